@@ -1,0 +1,53 @@
+"""Seeded synthetic inputs shared by the oracle tests and the GPU parity tests.
+
+This module holds no arithmetic of the method: it only draws vectors.  The
+method itself starts from the zero vector (Algorithm 2), so the random
+vectors here serve as arbitrary arguments of F and of the check, and as warm
+starts.  Values are fixed-point integers (units of 2^-K) of the magnitude the
+iterates reach (a few hundred units), spread over a few units like converged
+iterates, plus a random component that exercises every index.
+"""
+from __future__ import annotations
+
+import numpy as np
+
+K_DEFAULT = 44
+
+
+def n_states(sigma: int, d: int, h: int) -> int:
+    return sigma ** (d * h)
+
+
+def complement_index(n: int) -> np.ndarray:
+    """N-1-x for every x (the complement map of sigma = 2, paper section 3.3)."""
+    return np.arange(n - 1, -1, -1, dtype=np.int64)
+
+
+def random_fx(sigma, d, h, seed, base_units=200.0, spread_units=4.0, frac_bits=K_DEFAULT, symmetric=False):
+    """One random fixed-point vector over all states."""
+    rng = np.random.default_rng(seed)
+    n = n_states(sigma, d, h)
+    one = float(1 << frac_bits)
+    v = (base_units + spread_units * rng.random(n)) * one
+    v = v.astype(np.int64)
+    v += rng.integers(0, 1 << 20, size=n, dtype=np.int64)  # low-order noise below the unit
+    if symmetric:
+        if sigma != 2:
+            raise ValueError("complement symmetry needs sigma = 2")
+        v = np.minimum(v, v[complement_index(n)])
+    return v
+
+
+def random_history(sigma, d, h, seed, step_units=0.4, frac_bits=K_DEFAULT, symmetric=False):
+    """d vectors shaped like consecutive iterates: v[k] is k steps older than v[0]."""
+    base = random_fx(sigma, d, h, seed, frac_bits=frac_bits, symmetric=symmetric)
+    one = 1 << frac_bits
+    rng = np.random.default_rng(seed + 7919)
+    n = base.size
+    out = []
+    for k in range(d):
+        jitter = rng.integers(0, one // 16, size=n, dtype=np.int64)
+        if symmetric:
+            jitter = np.minimum(jitter, jitter[complement_index(n)])
+        out.append(base - int(k * step_units * one) - jitter)
+    return out

@@ -1,0 +1,73 @@
+"""Mutation test of the oracle's pins: every planted mistake must fail a pin.
+
+The oracle source has compile-time hooks (ORC_MUTANT = k) that plant one
+plausible mistake each -- a wrong shift direction, the arguments of F in
+reverse order, the wrong divisor, min instead of max, a dropped +1, a flipped
+increment, a check without the (d-k) R shift, transposed strings in the
+index.  The pins below are the same facts test_oracle_pins.py uses (printed
+values, closed forms, brute force, the encoding example); a mutant that passes
+all of them would mean the pins cannot see that mistake.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import load_golden
+import bruteforce as bf
+
+MUTANTS = {
+    1: "characters appended at the head instead of the end",
+    2: "F reads its arguments in reverse order",
+    3: "every mean divides by sigma^d",
+    4: "min over z instead of max",
+    5: "the +1 of equal heads dropped",
+    6: "increment taken as v_{t-1} - v_t",
+    7: "check evaluates F(u, .., u) without the (d-k) R shift",
+    8: "strings transposed inside each position of the index",
+}
+
+
+def _pins_hold(orc):
+    failures = []
+    (s, d, h, a, b, idx), = load_golden("encoding_example.txt")
+    digits = [[int(a[p]), int(b[p])] for p in range(int(h))]
+    if orc.encode(int(s), int(d), int(h), digits) != int(idx):
+        failures.append("encoding example")
+    for x in range(16):
+        if orc.encode(2, 2, 2, orc.decode(2, 2, 2, x)) != x:
+            failures.append("encode/decode")
+            break
+    for sigma in (2, 3, 5):
+        try:
+            bd = orc.run(sigma, 2, 1, 200, arith="fx")["bound_rd"]
+        except Exception:
+            bd = float("nan")
+        if not abs(bd - 2 / (sigma + 1)) < 1e-9:
+            failures.append(f"closed form sigma={sigma}")
+    for (s, d, h, val) in [(2, 2, 3, 0.747922), (3, 2, 2, 0.620690), (2, 3, 2, 0.673913)]:
+        try:
+            bd = orc.run(s, d, h, 300, arith="fx")["bound_rd"]
+        except Exception:
+            bd = float("nan")
+        if not abs(math.floor(bd * 1e6 + 1e-9) / 1e6 - val) < 1e-9 and not abs(round(bd * 1e6) / 1e6 - val) < 1e-9:
+            failures.append(f"table {s, d, h}")
+    W = bf.W_table(2, 2, 2, 4)
+    for n in range(2, 5):
+        vs = [np.array([float(W[n - k][x]) for x in range(16)]) for k in (1, 2)]
+        Fv = orc.F(2, 2, 2, vs, arith="f64")
+        Wn = np.array([float(w) for w in W[n]])
+        if not (np.all(Fv <= Wn) and np.any(Fv == Wn)):
+            failures.append(f"brute force n={n}")
+    return failures
+
+
+def test_unmutated_oracle_passes(orc):
+    assert _pins_hold(orc) == []
+
+
+@pytest.mark.parametrize("mutant", sorted(MUTANTS), ids=lambda m: MUTANTS[m])
+def test_mutant_is_caught(orc, mutant):
+    with orc.use_mutant(mutant):
+        failures = _pins_hold(orc)
+    assert failures, f"mutant {mutant} ({MUTANTS[mutant]}) passed every pin"
