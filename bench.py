@@ -1,0 +1,383 @@
+#!/usr/bin/env python3
+"""Benchmark of the GB300 feasible-triplet sweep (Heineman et al., arXiv 2407.10925).
+
+Workload (default): sigma = d = 2, h = 16 -- 2^32 states, the zero start of
+Algorithm 2, three resident fixed-point iterate vectors (complement-symmetric
+storage: 3 x 16 GiB).  One *step* is one check period of Algorithm 2 as the
+library runs it: C sweeps v_t = F(v_{t-1}, v_{t-2}) (the last one with the
+fused min/argmin of the increment), then the feasibility check of that
+iterate and the device-side keep test.  value = state-updates/s = (states x
+sweeps) / time over all ranks.
+
+Arms:
+  --impl ours (default)  the CUDA library through its C ABI
+  --impl reference       the CPU oracle as it stands, on a bounded sample of
+                         the same workload (no GPU work)
+
+Multi-GPU: the path has no exchange step across GPUs, so N ranks run N
+independent replicas (weak scaling); rank 0 prints the line.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+CONFIGS = {
+    "h16": dict(sigma=2, d=2, h=16),
+    "h14": dict(sigma=2, d=2, h=14),
+    "h12": dict(sigma=2, d=2, h=12),
+    "h8": dict(sigma=2, d=2, h=8),
+}
+METRIC = "state-updates/s"
+FALLBACK_HBM_GBS = 6800.0
+
+
+def parse():
+    ap = argparse.ArgumentParser(description=__doc__, formatter_class=argparse.RawDescriptionHelpFormatter)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--config", choices=sorted(CONFIGS), default="h16")
+    ap.add_argument("--check-every", type=int, default=10, help="sweeps per step (one check per step)")
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--symmetry", type=int, default=1)
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------------------
+# CPU side: the oracle on a bounded sample (spawned workers, before any CUDA use)
+
+
+def _oracle_chunk(args):
+    sigma, d, h, x0, count = args
+    import numpy as np
+
+    import oracle
+
+    seeds = [0x1234567 + k for k in range(d)]
+    one = 1 << oracle.DEFAULT_FRAC_BITS
+    bases = [(200 - k) * one for k in range(d)]
+    xs = np.arange(x0, x0 + count, dtype=np.uint64)
+    t = time.perf_counter()
+    oracle.F_generated(sigma, d, h, seeds, bases, 4 * one, xs)
+    return time.perf_counter() - t
+
+
+def oracle_sample(cfg, seconds_per_worker=1.5, workers=None, steps=1):
+    """Time the oracle's F on consecutive states of the workload; returns (states/s, cores, sample text)."""
+    import oracle
+
+    oracle.build()
+    sigma, d, h = cfg["sigma"], cfg["d"], cfg["h"]
+    n = sigma ** (d * h)
+    workers = workers or os.cpu_count() or 1
+    probe = min(1 << 14, n)
+    dt = _oracle_chunk((sigma, d, h, 0, probe))
+    per = max(1, min(n // workers, int(probe * seconds_per_worker / max(dt, 1e-6))))
+    ctx = mp.get_context("spawn")
+    rates = []
+    with ctx.Pool(workers) as pool:
+        pool.map(_oracle_chunk, [(sigma, d, h, 0, 16)] * workers)  # import + build in every worker
+        for s in range(steps):
+            chunks = [(sigma, d, h, (i * per + s * 7919) % max(1, n - per), per) for i in range(workers)]
+            t = time.perf_counter()
+            pool.map(_oracle_chunk, chunks)
+            rates.append(workers * per / (time.perf_counter() - t))
+    sample = (f"oracle F (fixed point) at {workers} x {per} consecutive states of sigma={sigma} d={d} h={h}, "
+              f"arguments from SplitMix64 (the sweep part of one iteration; {workers} spawned processes)")
+    return rates, workers, sample
+
+
+# ---------------------------------------------------------------------------
+# GPU helpers
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+
+    def __enter__(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=self.f, stderr=subprocess.DEVNULL)
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.f.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.path):
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in open(self.path):
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax = float(parts[2])
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def measured_peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+        return float(j["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+def kernel_source_hash():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2407_10925_gb300", "csrc")
+    for name in sorted(os.listdir(csrc)):
+        with open(os.path.join(csrc, name), "rb") as f:
+            h.update(name.encode())
+            h.update(f.read())
+    return h.hexdigest()[:16]
+
+
+def profiled_traffic(config_name, kernel):
+    """dram bytes per launch from the committed ncu summary, if it was taken on the current sources."""
+    p = os.path.join(ROOT, "profiles", "traffic.json")
+    try:
+        with open(p) as f:
+            j = json.load(f)
+    except (OSError, ValueError):
+        return None
+    entry = j.get(kernel, {}).get(config_name)
+    if not entry or entry.get("source_hash") != kernel_source_hash():
+        return None
+    return entry.get("dram_bytes_per_launch")
+
+
+# ---------------------------------------------------------------------------
+
+
+def run_reference(args, cfg, rank):
+    if rank != 0:
+        return
+    n = cfg["sigma"] ** (cfg["d"] * cfg["h"])
+    rates, cores, sample = oracle_sample(cfg, seconds_per_worker=1.0, steps=args.warmup + args.steps)
+    rates = rates[args.warmup:]
+    value = statistics.median(rates)
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "state-updates/s",
+        "n_gpus": args.gpus,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": 1e3 * n * args.check_every / value,
+        "higher_is_better": True,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "int64",
+        "data": "synthetic",
+        "config": {"workload": workload_name(cfg, args), "states": n, "sweeps_per_step": args.check_every},
+        "cpu_baseline": {"value": value, "unit": "state-updates/s", "cores": cores, "kind": "oracle",
+                         "sample": sample},
+        "e2e": {"value": value, "unit": "state-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_name(cfg, args):
+    return (f"feasible-triplet sweep sigma={cfg['sigma']} d={cfg['d']} h={cfg['h']} "
+            f"({cfg['sigma'] ** (cfg['d'] * cfg['h'])} states), zero start, fixed-point int64 iterates, "
+            f"{args.check_every} sweeps + 1 check per step")
+
+
+def main():
+    args = parse()
+    cfg = CONFIGS[args.config]
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        run_reference(args, cfg, rank)
+        return
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        rates, cores, sample = oracle_sample(cfg, seconds_per_worker=1.5, steps=1)
+        cpu = {"value": rates[0], "unit": "state-updates/s", "cores": cores, "kind": "oracle", "sample": sample}
+
+    import torch
+
+    import paper_2407_10925_gb300 as lb
+
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+
+    sigma, d, h = cfg["sigma"], cfg["d"], cfg["h"]
+    C = args.check_every
+    # a dedicated stream: every kernel of the library and the timing events go here
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    hnd = lb.LcsBound(sigma, d, h, check_every=C, timing=1, symmetry=args.symmetry, stream=stream.cuda_stream)
+    n = hnd.n_states
+    for _ in range(args.warmup):
+        hnd.iterate(C)
+    torch.cuda.synchronize()
+    hnd.stats(reset=True)
+
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        barrier()
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            hnd.iterate(C)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+        barrier()
+    ms = ev0.elapsed_time(ev1)
+    st = hnd.stats(reset=True)
+    if dist is not None:
+        t = torch.tensor([ms], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    bound, argmin, r, eps, at_iter = hnd.read()
+    rep = hnd.report()
+
+    sweeps = args.steps * C
+    value = world * n * sweeps / (ms / 1e3)
+    peak, peak_src = measured_peaks()
+    achieved = st["sweep_bytes"] / (st["sweep_ms"] / 1e3) / 1e9 if st["sweep_ms"] > 0 else None
+    per_launch_bytes = st["sweep_bytes"] / max(1, st["sweep_launches"])
+    traffic = profiled_traffic(args.config, "sweep")
+
+    # end to end through the public API from pinned host memory: set the start
+    # vectors from the host, run one check period, read the bound
+    e2e = None
+    if not args.no_e2e and args.e2e_steps > 0:
+        import numpy as np
+
+        start = hnd.export_fx(0, out=torch.empty(n, dtype=torch.int64, pin_memory=True))
+        e2e_ms = []
+        for i in range(args.e2e_steps + 1):
+            barrier()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            hnd.set_start_fx([start, start])
+            hnd.iterate(C)
+            hnd.read()
+            torch.cuda.synchronize()
+            dt = time.perf_counter() - t0
+            if i > 0:
+                e2e_ms.append(dt * 1e3)
+        e2e_ms_step = max(e2e_ms)
+        if dist is not None:
+            t = torch.tensor([e2e_ms_step], device="cuda")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            e2e_ms_step = float(t.item())
+        e2e = {"value": world * n * C / (e2e_ms_step / 1e3), "unit": "state-updates/s",
+               "h2d_bytes_per_step": d * n * 8, "d2h_bytes_per_step": 80,
+               "ms_per_step": e2e_ms_step,
+               "what": "lcs_bound_set_start_fx from pinned host (d vectors) + lcs_bound_iterate(C) + lcs_bound_read"}
+        del np
+
+    clocks = clk.summary()
+    if rank == 0:
+        line = {
+            "metric": METRIC,
+            "value": value,
+            "unit": "state-updates/s",
+            "n_gpus": world,
+            "steps": args.steps,
+            "warmup": args.warmup,
+            "ms_per_step": ms / args.steps,
+            "higher_is_better": True,
+            "scaling": "weak",
+            "vs_baseline": None,
+            "dtype": "int64",
+            "data": "synthetic",
+            "config": {
+                "workload": workload_name(cfg, args),
+                "states": n,
+                "stored_states": hnd.n_stored,
+                "sweeps_per_step": C,
+                "symmetry": bool(args.symmetry and hnd.n_stored < n),
+                "l2": "inputs larger than L2 (each iterate vector is %.1f GiB)" % (hnd.n_stored * 8 / 2 ** 30),
+                "parallelism": f"replicas x{world}",
+            },
+            "roofline": {
+                "bound": "hbm",
+                "kernel": "sweep",
+                "achieved": achieved,
+                "peak": peak,
+                "unit": "GB/s",
+                "frac": (achieved / peak) if achieved else None,
+                "peak_source": f"{peak_src} (MEASURED_PEAKS.json hbm_gbs)" if peak_src == "measured" else "fallback",
+                "traffic": traffic,
+                "algorithmic_bytes_per_launch": per_launch_bytes,
+                "sweep_ms_per_launch": st["sweep_ms"] / max(1, st["sweep_launches"]),
+                "check_ms_per_launch": st["check_ms"] / max(1, st["check_launches"]),
+            },
+            "cpu_baseline": cpu,
+            "e2e": e2e,
+            "gpu_launches": st["kernel_launches"],
+            "clocks": clocks,
+            "result": {"bound_rd": bound, "r": r, "eps": eps, "kept_iter": at_iter, "argmin_state": argmin,
+                       "iterations": rep["iters_done"]},
+        }
+        print(json.dumps(line), flush=True)
+    hnd.close()
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,219 @@
+/*
+ * lcs_bound.h -- C ABI of the GB300 feasible-triplet library.
+ *
+ * The library computes rigorous lower bounds on the Chvatal-Sankoff constants
+ * gamma_{sigma,d} with the feasible-triplet method of Heineman, Miller,
+ * Reichman, Salls, Sarkozy and Soiffer, "Improved Lower Bounds on the Expected
+ * Length of Longest Common Subsequences" (arXiv 2407.10925), section 2.1:
+ *
+ *   iterate   v_t = F(v_{t-1}, .., v_{t-d})        (Algorithm 2; F is Eq. ineq3
+ *                                                   built from Algorithm 1's F_z)
+ *   increment R_t = min_x (v_t - v_{t-1})[x]        (Algorithm 2; the text before it)
+ *   check     E_t = max(0, max_x W[x]),
+ *             W = v_t + dR - F(v_t + (d-1)R, .., v_t)    (Algorithm 2; Lemma 1)
+ *   keep      (u, r, eps) <- (v_t, R_t, E_t) when R_t - E_t >= r - eps
+ *   bound     gamma_{sigma,d} >= d (r - eps)         (Eq. lwrbound)
+ *
+ * STATE INDEX.  A state is a d-tuple of length-h strings over {0..sigma-1}.
+ * Its index is the paper's interleaved index (section 3.2) generalised to base
+ * sigma: the digit of string j (0-based) at position p (0 = head) has weight
+ * sigma^(d (h-1-p) + (d-1-j)).  For sigma = d = 2 the bits of a and b are
+ * interleaved starting with a: a = 1011, b = 0010 has index 142.  Every vector
+ * that crosses this interface uses that order, and the device buffers use it
+ * too.
+ *
+ * ARITHMETIC.  Iterates are stored as int64 fixed-point numbers: a stored
+ * integer q means q * 2^-K (K = frac_bits, default 44).  Sums are exact; each
+ * mean over sigma^k terms is rounded down (floor).  Because floor only lowers
+ * F, the same F serves the iteration and the check, and E computed this way
+ * is an upper bound of the exact E for the stored u and R: the reported
+ * bound d (r - eps) is rigorous.  Doubles crossing the interface are
+ * converted: inputs to fixed point rounding down, outputs to double rounding
+ * to nearest, except the bound, which is rounded down.
+ *
+ * STREAMS AND ERRORS.  All device work is enqueued on the handle's stream.
+ * Calls marked "asynchronous" return before the work ends; errors of the
+ * enqueued work surface at the next synchronising call.  Every call returns a
+ * status; lcs_bound_errstr() gives its text and lcs_bound_last_error() the
+ * message of the most recent failure on the calling thread.  Handles are not
+ * thread-safe: use one handle from one host thread at a time.
+ *
+ * OWNERSHIP.  The library owns every buffer it allocates (through the
+ * allocator in lcs_bound_opts if one is given) and frees them in
+ * lcs_bound_destroy().  Pointers passed in are borrowed for the duration of
+ * the call (for device pointers: until the enqueued work has read them).
+ */
+#ifndef LCS_BOUND_H
+#define LCS_BOUND_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct lcs_bound lcs_bound_t; /* opaque; library-owned */
+
+typedef enum {
+  LCS_OK = 0,
+  LCS_EINVAL = 1,       /* bad argument (shape, mode, pointer, size) */
+  LCS_ENOMEM = 2,       /* device or host allocation failed */
+  LCS_ECUDA = 3,        /* a CUDA call failed; see lcs_bound_last_error() */
+  LCS_ETIMEOUT = 4,     /* a bounded device-side wait gave up */
+  LCS_ENOBOUND = 5,     /* no feasibility check has run yet */
+  LCS_EOVERFLOW = 6,    /* fixed-point headroom would be exceeded */
+  LCS_EUNSUPPORTED = 7  /* (sigma, d, f_mode) has no kernel in this build */
+} lcs_status;
+
+typedef struct {
+  /* 0: check only at the last iteration of each lcs_bound_iterate() call;
+   * k > 0: check every k-th iteration (counted from creation) and at the last
+   * iteration of each call.  1 is Algorithm 2 as printed. */
+  int check_every;
+  /* 0: R = minimum increment (default).  1: R = maximum increment (the line of
+   * Algorithm 2 as printed).  E is evaluated for whichever R is taken. */
+  int r_mode;
+  /* 0: F as in the paper (max over z of F_z).  Other values: LCS_EUNSUPPORTED. */
+  int f_mode;
+  /* K, the number of fractional bits of the fixed-point iterates; 0 -> 44.
+   * Valid range 8..56. */
+  int frac_bits;
+  /* 1: keep a device copy of the kept u (one more vector of memory, and a
+   * copy at each check that keeps).  0: u is not retained. */
+  int keep_u;
+  /* 1 (default): for sigma = 2, store and compute only the states whose first
+   * string starts with 0, using the complement symmetry of the paper's
+   * section 3.3 (v[N-1-x] = v[x]).  The start vectors must then be symmetric.
+   * 0: store every state.  Ignored for sigma != 2. */
+  int symmetry;
+  /* 1: record CUDA events around each sweep and check launch; read them with
+   * lcs_bound_stats().  0 (default): no events. */
+  int timing;
+  /* Device allocator.  NULL alloc -> cudaMalloc / cudaFree.  alloc returns a
+   * device pointer aligned to at least 256 bytes, or NULL on failure. */
+  void* (*alloc)(size_t bytes, void* ctx);
+  void (*free)(void* ptr, void* ctx);
+  void* alloc_ctx;
+  /* cudaStream_t to enqueue on; NULL -> the library creates its own stream. */
+  void* stream;
+} lcs_bound_opts;
+
+/* Fill *opts with the defaults listed above. */
+lcs_status lcs_bound_default_opts(lcs_bound_opts* opts);
+
+/* Create a handle for the shape (sigma, d, h): sigma >= 2, d >= 2, h >= 1,
+ * sigma^(d h) < 2^40 states.  Allocates d+1 iterate vectors (d+2 with keep_u)
+ * on the current device and sets v_0 = .. = v_{d-1} = 0 (Algorithm 2's zero
+ * start).  opts may be NULL (defaults).  On failure *out is NULL.
+ * Synchronous. */
+lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts, lcs_bound_t** out);
+
+/* Number of states sigma^(d h) of the handle's shape, and the number the
+ * device stores (half of it under complement symmetry). */
+lcs_status lcs_bound_size(const lcs_bound_t* hnd, uint64_t* n_states, uint64_t* n_stored);
+
+/* Run n_iters >= 0 iterations of Algorithm 2: n_iters evaluations of F, the
+ * increment of each iteration that is checked, and the checks selected by
+ * check_every (always including the last of this call when n_iters > 0).
+ * Asynchronous.  LCS_EOVERFLOW if the iterates could leave the fixed-point
+ * range during the call (values grow by at most 1 per iteration). */
+lcs_status lcs_bound_iterate(lcs_bound_t* hnd, int64_t n_iters);
+
+/* The kept triplet and the bound.  Synchronises the stream.
+ *   bound_rd:     d (r - eps) rounded down to a double (rigorous)
+ *   argmin_state: index of a state attaining the increment R of the
+ *                 iteration last checked (smallest index among ties)
+ *   r, eps:       the kept R and E as doubles (rounded to nearest)
+ *   at_iter:      iteration count (since creation) of the kept u; -1 if no
+ *                 check has kept an iterate (the initial triplet (v_0, 0, 0))
+ * Any output pointer may be NULL.  LCS_ENOBOUND if no check has run. */
+lcs_status lcs_bound_read(lcs_bound_t* hnd, double* bound_rd, uint64_t* argmin_state, double* r, double* eps,
+                          int64_t* at_iter);
+
+/* Exact fixed-point form of the last results (all values in units of 2^-K). */
+typedef struct {
+  int64_t iters_done;  /* iterations run since creation (or since set_start) */
+  int64_t R;           /* increment of the last checked iteration */
+  uint64_t argmin;     /* state attaining R (smallest index among ties) */
+  int64_t E;           /* E of the last check */
+  int64_t r, eps;      /* kept triplet */
+  int64_t kept_iter;   /* -1: the initial triplet (v_0, 0, 0) */
+  int64_t have_check;  /* 1 once a check has run */
+  int frac_bits;       /* K */
+  int status;          /* sticky device-side error status (lcs_status) */
+} lcs_bound_report;
+
+/* Synchronises the stream. */
+lcs_status lcs_bound_read_report(lcs_bound_t* hnd, lcs_bound_report* out);
+
+/* Replace the d most recent iterates: v[k] (k = 0..d-1) becomes the iterate
+ * k steps older than the newest (v[0] newest), each a vector of
+ * sigma^(d h) doubles in state-index order, converted to fixed point rounding
+ * down.  on_device = 1: the pointers are device pointers; 0: host pointers
+ * (copied through a staging buffer).  Resets the iteration count and the kept
+ * triplet to the initial (v_oldest, 0, 0).  Under complement symmetry the
+ * vectors must satisfy v[N-1-x] = v[x] after conversion, else LCS_EINVAL.
+ * Synchronous for host pointers; asynchronous for device pointers. */
+lcs_status lcs_bound_set_start(lcs_bound_t* hnd, const double* const* v, int on_device);
+
+/* As lcs_bound_set_start with fixed-point values (units of 2^-K), exact. */
+lcs_status lcs_bound_set_start_fx(lcs_bound_t* hnd, const int64_t* const* v, int on_device);
+
+/* Copy the iterate k steps older than the newest (k = 0..d-1), or with
+ * k = -1 the kept u (needs keep_u), into dst: sigma^(d h) values in
+ * state-index order.  on_device selects the kind of dst.  Synchronises the
+ * stream when dst is a host pointer. */
+lcs_status lcs_bound_export(lcs_bound_t* hnd, int k, double* dst, int on_device);
+lcs_status lcs_bound_export_fx(lcs_bound_t* hnd, int k, int64_t* dst, int on_device);
+
+/* Evaluate the check of Algorithm 2 (Lemma 1) for an arbitrary vector u
+ * (sigma^(d h) fixed-point values, device pointer, state-index order; under
+ * complement symmetry only the stored half, the first n_stored values, is
+ * read and u must be symmetric) and increment R: writes
+ * E = max(0, max_x W[x]) to *E_out (host).  Does not touch the kept triplet.
+ * Synchronises the stream. */
+lcs_status lcs_bound_check_vector(lcs_bound_t* hnd, const int64_t* u_dev, int64_t R, int64_t* E_out);
+
+/* Timing of the enqueued sweep and check kernels (needs opts.timing = 1).
+ * Synchronises the stream.  Counts and milliseconds since creation or the
+ * last reset. */
+typedef struct {
+  int64_t sweep_launches;
+  double sweep_ms;
+  int64_t check_launches;
+  double check_ms;
+  int64_t kernel_launches; /* every kernel this handle enqueued */
+  uint64_t sweep_bytes;    /* algorithmic bytes of all sweeps: 8 (d+1) per stored state */
+  uint64_t check_bytes;    /* algorithmic bytes of all checks: 8 per stored state */
+} lcs_bound_stats_t;
+lcs_status lcs_bound_stats(lcs_bound_t* hnd, lcs_bound_stats_t* out, int reset);
+
+/* Free everything the handle owns (after the stream's pending work ends).
+ * NULL is ignored. */
+void lcs_bound_destroy(lcs_bound_t* hnd);
+
+/* Static text of a status code. */
+const char* lcs_bound_errstr(lcs_status st);
+
+/* Message of the most recent failure on the calling thread ("" if none). */
+const char* lcs_bound_last_error(void);
+
+/* ------------------------------------------------------------------------ */
+/* Stateless entry point.
+ *
+ * One evaluation of F (Eq. ineq3; Algorithm 2's first line in the loop):
+ * v_out = F(v_prev[0], .., v_prev[d-1]) where v_prev[k-1] is the iterate k
+ * steps older than the one being computed (the k-th argument v_k of F).
+ * All vectors are device pointers of sigma^(d h) fixed-point int64 values in
+ * state-index order (no symmetry).  v_out must not alias any input.
+ * f_mode and frac_bits as in lcs_bound_opts.  stream: cudaStream_t or NULL
+ * (legacy default stream).  Asynchronous; no allocation. */
+lcs_status lcs_sweep_fx(int sigma, int d, int h, int f_mode, int frac_bits, const int64_t* const* v_prev, int64_t* v_out,
+                        void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* LCS_BOUND_H */

@@ -83,6 +83,9 @@ def _load(path):
     for name in ("orc_add_dir", "orc_mul_dir", "orc_div_dir"):
         getattr(L, name).argtypes = [dbl, dbl, i32]
         getattr(L, name).restype = dbl
+    L.orc_F_fx_generated.argtypes = [i32, i32, i32, i32, vp, vp, u64, i32, vp, u64, vp]
+    L.orc_splitmix64_at.argtypes = [u64, u64]
+    L.orc_splitmix64_at.restype = u64
     L.orc_fx_to_double_rd.argtypes = [i64, i32]
     L.orc_fx_to_double_rd.restype = dbl
     if L.orc_result_size() != ctypes.sizeof(Result):
@@ -247,3 +250,22 @@ def div_dir(a, m, mode):
 
 def fx_to_double_rd(a: int, frac_bits: int = DEFAULT_FRAC_BITS) -> float:
     return lib().orc_fx_to_double_rd(int(a), frac_bits)
+
+
+def splitmix64_at(seed: int, i: int) -> int:
+    return int(lib().orc_splitmix64_at(seed, i))
+
+
+def F_generated(sigma: int, d: int, h: int, seeds, bases, spread: int, xs,
+                frac_bits: int = DEFAULT_FRAC_BITS, symmetric: bool = False) -> np.ndarray:
+    """F (fx) at the states xs, argument k being bases[k-1] + (SplitMix64(seeds[k-1], c(y)) mod spread).
+
+    c(y) = y, or min(y, N-1-y) with ``symmetric``.
+    """
+    seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
+    bases = np.ascontiguousarray(bases, dtype=np.int64)
+    xs = np.ascontiguousarray(xs, dtype=np.uint64)
+    out = np.empty(xs.size, dtype=np.int64)
+    _check(lib().orc_F_fx_generated(sigma, d, h, frac_bits, _ptr(seeds), _ptr(bases), int(spread),
+                                    1 if symmetric else 0, _ptr(xs), xs.size, _ptr(out)), "F_fx_generated")
+    return out

@@ -349,6 +349,68 @@ int orc_F_fx(int sigma, int d, int h, int f_mode, int frac_bits, const int64_t* 
   return ORC_OK;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Synthetic inputs defined by a counter-based generator, so that F can be
+ * evaluated at sampled states of shapes whose vectors would not fit in host
+ * memory.  gen_k[y] = base_k + (g(seed_k, y) mod spread) where g(seed, i) is
+ * the i-th output of SplitMix64 started at seed (Steele, Lea and Flood,
+ * "Fast splittable pseudorandom number generators", OOPSLA 2014): the state
+ * advances by 0x9e3779b97f4a7c15 per output and each output is the state
+ * after its increment passed through the published 64-bit finaliser. */
+
+static uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
+  uint64_t z = seed + (i + 1) * 0x9e3779b97f4a7c15ull;
+  z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+  z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
+  return z ^ (z >> 31);
+}
+
+uint64_t orc_splitmix64_at(uint64_t seed, uint64_t i) { return splitmix64_at(seed, i); }
+
+/* F (fx) at the states xs[0..m) with argument k (1-based) given by
+ * base[k-1] + (splitmix64_at(seed[k-1], c(y)) mod spread), where c(y) = y, or
+ * c(y) = min(y, N-1-y) when `symmetric` (inputs invariant under the
+ * complement map of sigma = 2).  Each state is evaluated exactly as
+ * F_state_fx does, reading through the generator. */
+int orc_F_fx_generated(int sigma, int d, int h, int frac_bits, const uint64_t* seed, const int64_t* base, uint64_t spread,
+                       int symmetric, const uint64_t* xs, uint64_t m, int64_t* out) {
+  shape_t s;
+  int st = make_shape(sigma, d, h, &s);
+  if (st) return st;
+  if (frac_bits < 0 || frac_bits > 60 || spread == 0) return ORC_EINVAL;
+  int X[ORC_MAXD * ORC_MAXH], Y[ORC_MAXD * ORC_MAXH];
+  int sets[ORC_MAXSETS][ORC_MAXD];
+  int sizes[ORC_MAXSETS];
+  int c[ORC_MAXD];
+  const int64_t one = (int64_t)1 << frac_bits;
+  for (uint64_t i = 0; i < m; ++i) {
+    if (xs[i] >= s.n) return ORC_EINVAL;
+    decode(&s, xs[i], X);
+    int b = heads_equal(&s, X);
+    int nsets = candidate_sets(&s, X, 0, sets, sizes);
+    __int128 best = 0;
+    int have = 0;
+    for (int q = 0; q < nsets; ++q) {
+      int k = sizes[q];
+      uint64_t terms = upow((uint64_t)s.sigma, k);
+      __int128 acc = 0;
+      for (uint64_t cc = 0; cc < terms; ++cc) {
+        tuple_of(s.sigma, k, cc, c);
+        advance(&s, X, sets[q], k, c, Y);
+        uint64_t y = encode(&s, Y);
+        if (symmetric && s.n - 1 - y < y) y = s.n - 1 - y;
+        acc += base[k - 1] + (int64_t)(splitmix64_at(seed[k - 1], y) % spread);
+      }
+      __int128 mean = floor_div128(acc, (int64_t)terms);
+      if (!have || mean > best) best = mean, have = 1;
+    }
+    if (b) best += one;
+    if (!fits64(best)) return ORC_EOVERFLOW;
+    out[i] = (int64_t)best;
+  }
+  return ORC_OK;
+}
+
 uint64_t orc_encode(int sigma, int d, int h, const int* X) {
   shape_t s;
   if (make_shape(sigma, d, h, &s)) return UINT64_MAX;

@@ -1,0 +1,346 @@
+"""Thin ctypes binding of ``include/lcs_bound.h`` (argument marshalling only).
+
+Every function keeps the C name and raises :class:`LcsError` when the C call
+returns a status other than ``LCS_OK``.  Vectors may be numpy arrays (host
+memory) or torch tensors (host or CUDA memory); nothing here computes on
+them.  The library is loaded from the package's ``_build`` directory and
+built there with nvcc when missing; if that is impossible the import fails
+loudly -- there is no CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import threading
+
+import numpy as np
+
+from . import build as _build
+
+LCS_OK, LCS_EINVAL, LCS_ENOMEM, LCS_ECUDA, LCS_ETIMEOUT, LCS_ENOBOUND, LCS_EOVERFLOW, LCS_EUNSUPPORTED = range(8)
+
+_ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+_FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class lcs_bound_opts(ctypes.Structure):
+    _fields_ = [
+        ("check_every", ctypes.c_int),
+        ("r_mode", ctypes.c_int),
+        ("f_mode", ctypes.c_int),
+        ("frac_bits", ctypes.c_int),
+        ("keep_u", ctypes.c_int),
+        ("symmetry", ctypes.c_int),
+        ("timing", ctypes.c_int),
+        ("alloc", _ALLOC),
+        ("free", _FREE),
+        ("alloc_ctx", ctypes.c_void_p),
+        ("stream", ctypes.c_void_p),
+    ]
+
+
+class lcs_bound_report(ctypes.Structure):
+    _fields_ = [
+        ("iters_done", ctypes.c_int64),
+        ("R", ctypes.c_int64),
+        ("argmin", ctypes.c_uint64),
+        ("E", ctypes.c_int64),
+        ("r", ctypes.c_int64),
+        ("eps", ctypes.c_int64),
+        ("kept_iter", ctypes.c_int64),
+        ("have_check", ctypes.c_int64),
+        ("frac_bits", ctypes.c_int),
+        ("status", ctypes.c_int),
+    ]
+
+
+class lcs_bound_stats_t(ctypes.Structure):
+    _fields_ = [
+        ("sweep_launches", ctypes.c_int64),
+        ("sweep_ms", ctypes.c_double),
+        ("check_launches", ctypes.c_int64),
+        ("check_ms", ctypes.c_double),
+        ("kernel_launches", ctypes.c_int64),
+        ("sweep_bytes", ctypes.c_uint64),
+        ("check_bytes", ctypes.c_uint64),
+    ]
+
+
+class LcsError(RuntimeError):
+    def __init__(self, status, message):
+        super().__init__(f"{message} (status {status})")
+        self.status = status
+
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib():
+    """The loaded CUDA library (built in-tree on first use)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            L = ctypes.CDLL(_build.build())
+            vp, i32, i64, u64, dbl = ctypes.c_void_p, ctypes.c_int, ctypes.c_int64, ctypes.c_uint64, ctypes.c_double
+            P = ctypes.POINTER
+            sig = {
+                "lcs_bound_default_opts": [P(lcs_bound_opts)],
+                "lcs_bound_create": [i32, i32, i32, P(lcs_bound_opts), P(vp)],
+                "lcs_bound_size": [vp, P(u64), P(u64)],
+                "lcs_bound_iterate": [vp, i64],
+                "lcs_bound_read": [vp, P(dbl), P(u64), P(dbl), P(dbl), P(i64)],
+                "lcs_bound_read_report": [vp, P(lcs_bound_report)],
+                "lcs_bound_set_start": [vp, vp, i32],
+                "lcs_bound_set_start_fx": [vp, vp, i32],
+                "lcs_bound_export": [vp, i32, vp, i32],
+                "lcs_bound_export_fx": [vp, i32, vp, i32],
+                "lcs_bound_check_vector": [vp, vp, i64, P(i64)],
+                "lcs_bound_stats": [vp, P(lcs_bound_stats_t), i32],
+                "lcs_sweep_fx": [i32, i32, i32, i32, i32, vp, vp, vp],
+            }
+            for name, args in sig.items():
+                fn = getattr(L, name)
+                fn.argtypes = args
+                fn.restype = ctypes.c_int
+            L.lcs_bound_destroy.argtypes = [vp]
+            L.lcs_bound_destroy.restype = None
+            L.lcs_bound_errstr.argtypes = [ctypes.c_int]
+            L.lcs_bound_errstr.restype = ctypes.c_char_p
+            L.lcs_bound_last_error.argtypes = []
+            L.lcs_bound_last_error.restype = ctypes.c_char_p
+            _lib = L
+    return _lib
+
+
+def lcs_bound_errstr(status: int) -> str:
+    return lib().lcs_bound_errstr(status).decode()
+
+
+def lcs_bound_last_error() -> str:
+    return lib().lcs_bound_last_error().decode()
+
+
+def _check(status: int, what: str):
+    if status != LCS_OK:
+        raise LcsError(status, f"{what}: {lcs_bound_errstr(status)}: {lcs_bound_last_error()}")
+
+
+# ---------------------------------------------------------------------------
+# pointers of numpy arrays / torch tensors
+
+
+def _ptr_and_kind(a, dtype):
+    """(address, on_device) of a contiguous vector of the given numpy dtype."""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        want = torch.float64 if dtype == np.float64 else torch.int64
+        if a.dtype != want or not a.is_contiguous():
+            raise TypeError(f"tensor must be contiguous {want}")
+        return a.data_ptr(), 1 if a.is_cuda else 0
+    if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
+        raise TypeError(f"array must be a contiguous numpy {np.dtype(dtype)} array")
+    return a.ctypes.data, 0
+
+
+class TorchAllocator:
+    """Device memory for the library from PyTorch's caching allocator."""
+
+    def __init__(self, device=None):
+        import torch
+
+        self._torch = torch
+        self._device = device if device is not None else torch.device("cuda", torch.cuda.current_device())
+        self._live = {}
+        self.alloc = _ALLOC(self._alloc)
+        self.free = _FREE(self._free)
+
+    def _alloc(self, nbytes, ctx):
+        try:
+            t = self._torch.empty(int(nbytes) + 256, dtype=self._torch.uint8, device=self._device)
+        except RuntimeError:
+            return None
+        p = t.data_ptr()
+        p = (p + 255) // 256 * 256
+        self._live[p] = t
+        return p
+
+    def _free(self, ptr, ctx):
+        self._live.pop(ptr, None)
+
+
+# ---------------------------------------------------------------------------
+# C functions, same names
+
+
+def lcs_bound_default_opts() -> lcs_bound_opts:
+    o = lcs_bound_opts()
+    _check(lib().lcs_bound_default_opts(ctypes.byref(o)), "lcs_bound_default_opts")
+    return o
+
+
+def lcs_bound_create(sigma: int, d: int, h: int, opts: lcs_bound_opts | None = None) -> ctypes.c_void_p:
+    hnd = ctypes.c_void_p()
+    _check(lib().lcs_bound_create(sigma, d, h, ctypes.byref(opts) if opts is not None else None, ctypes.byref(hnd)),
+           "lcs_bound_create")
+    return hnd
+
+
+def lcs_bound_size(hnd):
+    a, b = ctypes.c_uint64(), ctypes.c_uint64()
+    _check(lib().lcs_bound_size(hnd, ctypes.byref(a), ctypes.byref(b)), "lcs_bound_size")
+    return a.value, b.value
+
+
+def lcs_bound_iterate(hnd, n_iters: int):
+    _check(lib().lcs_bound_iterate(hnd, int(n_iters)), "lcs_bound_iterate")
+
+
+def lcs_bound_read(hnd):
+    """(bound_rd, argmin_state, r, eps, at_iter)."""
+    b, a, r, e, it = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(lib().lcs_bound_read(hnd, ctypes.byref(b), ctypes.byref(a), ctypes.byref(r), ctypes.byref(e),
+                                ctypes.byref(it)), "lcs_bound_read")
+    return b.value, a.value, r.value, e.value, it.value
+
+
+def lcs_bound_read_report(hnd) -> dict:
+    rep = lcs_bound_report()
+    _check(lib().lcs_bound_read_report(hnd, ctypes.byref(rep)), "lcs_bound_read_report")
+    return {f: getattr(rep, f) for f, _ in lcs_bound_report._fields_}
+
+
+def _vec_array(vs, dtype):
+    ptrs, kinds = zip(*[_ptr_and_kind(v, dtype) for v in vs])
+    if len(set(kinds)) != 1:
+        raise TypeError("start vectors must all be on the host or all on the device")
+    return (ctypes.c_void_p * len(ptrs))(*ptrs), kinds[0]
+
+
+def lcs_bound_set_start(hnd, vs):
+    """vs[k]: the iterate k steps older than the newest (float64, every state)."""
+    arr, on_dev = _vec_array(vs, np.float64)
+    _check(lib().lcs_bound_set_start(hnd, arr, on_dev), "lcs_bound_set_start")
+
+
+def lcs_bound_set_start_fx(hnd, vs):
+    arr, on_dev = _vec_array(vs, np.int64)
+    _check(lib().lcs_bound_set_start_fx(hnd, arr, on_dev), "lcs_bound_set_start_fx")
+
+
+def lcs_bound_export(hnd, k: int, out):
+    p, on_dev = _ptr_and_kind(out, np.float64)
+    _check(lib().lcs_bound_export(hnd, k, p, on_dev), "lcs_bound_export")
+    return out
+
+
+def lcs_bound_export_fx(hnd, k: int, out):
+    p, on_dev = _ptr_and_kind(out, np.int64)
+    _check(lib().lcs_bound_export_fx(hnd, k, p, on_dev), "lcs_bound_export_fx")
+    return out
+
+
+def lcs_bound_check_vector(hnd, u_dev, R: int) -> int:
+    p, on_dev = _ptr_and_kind(u_dev, np.int64)
+    if not on_dev:
+        raise TypeError("u must be a CUDA tensor")
+    E = ctypes.c_int64()
+    _check(lib().lcs_bound_check_vector(hnd, p, int(R), ctypes.byref(E)), "lcs_bound_check_vector")
+    return E.value
+
+
+def lcs_bound_stats(hnd, reset: bool = False) -> dict:
+    s = lcs_bound_stats_t()
+    _check(lib().lcs_bound_stats(hnd, ctypes.byref(s), 1 if reset else 0), "lcs_bound_stats")
+    return {f: getattr(s, f) for f, _ in lcs_bound_stats_t._fields_}
+
+
+def lcs_bound_destroy(hnd):
+    if hnd:
+        lib().lcs_bound_destroy(hnd)
+
+
+def lcs_sweep_fx(sigma, d, h, v_prev, v_out, f_mode=0, frac_bits=44, stream=None):
+    """v_out = F(v_prev[0], .., v_prev[d-1]) on the device (CUDA int64 tensors)."""
+    arr, on_dev = _vec_array(v_prev, np.int64)
+    po, od = _ptr_and_kind(v_out, np.int64)
+    if not (on_dev and od):
+        raise TypeError("lcs_sweep_fx takes CUDA tensors")
+    _check(lib().lcs_sweep_fx(sigma, d, h, f_mode, frac_bits, arr, po, stream), "lcs_sweep_fx")
+
+
+# ---------------------------------------------------------------------------
+# convenience object
+
+
+class LcsBound:
+    """Owns one handle; see ``include/lcs_bound.h`` for the semantics."""
+
+    def __init__(self, sigma, d, h, *, check_every=0, r_mode=0, f_mode=0, frac_bits=44, keep_u=0, symmetry=1,
+                 timing=0, stream=None, torch_alloc=False):
+        self.sigma, self.d, self.h = sigma, d, h
+        o = lcs_bound_default_opts()
+        o.check_every, o.r_mode, o.f_mode, o.frac_bits = check_every, r_mode, f_mode, frac_bits
+        o.keep_u, o.symmetry, o.timing = keep_u, symmetry, timing
+        self._alloc = None
+        if torch_alloc:
+            self._alloc = TorchAllocator()
+            o.alloc, o.free = self._alloc.alloc, self._alloc.free
+        if stream is not None:
+            if not stream:
+                raise ValueError("stream 0 means 'library-owned stream'; pass a non-default stream handle")
+            o.stream = stream
+        self.opts = o
+        self.frac_bits = frac_bits
+        self.hnd = lcs_bound_create(sigma, d, h, o)
+        self.n_states, self.n_stored = lcs_bound_size(self.hnd)
+
+    def close(self):
+        if self.hnd:
+            lcs_bound_destroy(self.hnd)
+            self.hnd = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def iterate(self, n):
+        lcs_bound_iterate(self.hnd, n)
+
+    def read(self):
+        return lcs_bound_read(self.hnd)
+
+    def report(self):
+        return lcs_bound_read_report(self.hnd)
+
+    def set_start(self, vs):
+        lcs_bound_set_start(self.hnd, vs)
+
+    def set_start_fx(self, vs):
+        lcs_bound_set_start_fx(self.hnd, vs)
+
+    def export(self, k=0, out=None):
+        if out is None:
+            out = np.empty(self.n_states, dtype=np.float64)
+        return lcs_bound_export(self.hnd, k, out)
+
+    def export_fx(self, k=0, out=None):
+        if out is None:
+            out = np.empty(self.n_states, dtype=np.int64)
+        return lcs_bound_export_fx(self.hnd, k, out)
+
+    def check_vector(self, u_dev, R):
+        return lcs_bound_check_vector(self.hnd, u_dev, R)
+
+    def stats(self, reset=False):
+        return lcs_bound_stats(self.hnd, reset)

@@ -1,0 +1,796 @@
+// lcs_bound.cu -- C ABI and host driver of the GB300 feasible-triplet library
+// (Heineman et al., arXiv 2407.10925, section 2.1, Algorithm 2).
+//
+// The handle owns a ring of d+1 fixed-point iterate vectors on the device.
+// One iteration launches the sweep (v_t = F(v_{t-1}, .., v_{t-d})); an
+// iteration that is checked fuses the increment reduction into the sweep and
+// then launches: the increment finalize (R, argmin), the check kernel (W, its
+// max) and the check finalize (E, and Algorithm 2's keep test).  The results
+// stay on the device (DevState) until lcs_bound_read synchronises.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <mutex>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "../../include/lcs_bound.h"
+#include "lcs_common.h"
+
+namespace lcs {
+
+// ---------------------------------------------------------------------------
+// Errors
+
+static thread_local std::string g_last_error;
+
+static lcs_status fail(lcs_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  g_last_error = buf;
+  return st;
+}
+
+#define LCS_CUDA(call)                                                                         \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return fail(LCS_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, \
+                  __LINE__);                                                                   \
+  } while (0)
+
+// ---------------------------------------------------------------------------
+// Small kernels: finalize reductions, conversions, copies.
+
+__device__ __forceinline__ bool better_arg(long long v, unsigned long long x, long long bv, unsigned long long bx,
+                                           int r_mode) {
+  if (v != bv) return r_mode ? (v > bv) : (v < bv);
+  return x < bx;
+}
+
+// R and its state from the per-CTA partials of a sweep (deterministic: fixed
+// assignment of partials to threads and a fixed reduction tree).
+__global__ void __launch_bounds__(kFinalBlock) finalize_incr_kernel(const RedPartial* parts, int n, int r_mode,
+                                                                     DevState* st, long long iter) {
+  long long v = r_mode ? LLONG_MIN : LLONG_MAX;
+  unsigned long long x = ULLONG_MAX;
+  for (int i = threadIdx.x; i < n; i += blockDim.x)
+    if (better_arg(parts[i].v, parts[i].x, v, x, r_mode)) v = parts[i].v, x = parts[i].x;
+  __shared__ long long sv[kFinalBlock / 32];
+  __shared__ unsigned long long sx[kFinalBlock / 32];
+  for (int o = 16; o > 0; o >>= 1) {
+    long long ov = __shfl_xor_sync(0xffffffffu, v, o);
+    unsigned long long ox = __shfl_xor_sync(0xffffffffu, x, o);
+    if (better_arg(ov, ox, v, x, r_mode)) v = ov, x = ox;
+  }
+  if ((threadIdx.x & 31) == 0) sv[threadIdx.x >> 5] = v, sx[threadIdx.x >> 5] = x;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x >> 5;
+    v = threadIdx.x < nw ? sv[threadIdx.x] : sv[0];
+    x = threadIdx.x < nw ? sx[threadIdx.x] : sx[0];
+    for (int o = 16; o > 0; o >>= 1) {
+      long long ov = __shfl_xor_sync(0xffffffffu, v, o);
+      unsigned long long ox = __shfl_xor_sync(0xffffffffu, x, o);
+      if (better_arg(ov, ox, v, x, r_mode)) v = ov, x = ox;
+    }
+    if (threadIdx.x == 0) {
+      st->R = v;
+      st->argmin = x;
+      st->R_iter = iter;
+    }
+  }
+}
+
+// E = max(0, max W) and Algorithm 2's keep test "R - E >= r - eps".
+__global__ void __launch_bounds__(kFinalBlock) finalize_check_kernel(const RedPartial* parts, int n, DevState* st,
+                                                                      long long iter) {
+  long long v = 0;  // E = max(0, ...)
+  for (int i = threadIdx.x; i < n; i += blockDim.x) v = max(v, parts[i].v);
+  __shared__ long long sv[kFinalBlock / 32];
+  for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+  if ((threadIdx.x & 31) == 0) sv[threadIdx.x >> 5] = v;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    const int nw = blockDim.x >> 5;
+    v = threadIdx.x < nw ? sv[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) {
+      const long long R = st->R, E = v;
+      st->E = E;
+      st->E_iter = iter;
+      st->have_check = 1;
+      // both sides are differences of int64 values far from the int64 limits
+      // (the host keeps every value below 2^62 in magnitude)
+      if (R - E >= st->r - st->eps) {
+        st->r = R;
+        st->eps = E;
+        st->kept_iter = iter;
+        st->kept_flag = 1;
+      } else {
+        st->kept_flag = 0;
+      }
+    }
+  }
+}
+
+__global__ void copy_if_kept_kernel(const long long* __restrict__ src, long long* __restrict__ dst,
+                                    unsigned long long n, const DevState* st) {
+  if (!st->kept_flag) return;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    dst[i] = src[i];
+}
+
+// Convert [off, off+len) of a full-length input vector (doubles rounded down to
+// multiples of 2^-K, or fixed-point values) into the stored vector.  Indices at
+// or above n_stored (complement-symmetric storage) are compared with their
+// mirror instead; a mismatch sets st->status.
+template <bool FROM_DOUBLE>
+__global__ void ingest_kernel(const void* __restrict__ src, unsigned long long off, unsigned long long len,
+                              long long* __restrict__ dst, unsigned long long n_stored, unsigned long long n_total,
+                              double scale, DevState* st) {
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    long long q;
+    if constexpr (FROM_DOUBLE) {
+      const double v = static_cast<const double*>(src)[i] * scale;  // exact: scale is a power of two
+      if (!(v >= -4.0e18 && v <= 4.0e18)) {                          // also catches NaN
+        atomicExch((unsigned long long*)&st->status, (unsigned long long)LCS_EOVERFLOW);
+        continue;
+      }
+      q = __double2ll_rd(v);
+    } else {
+      q = static_cast<const long long*>(src)[i];
+    }
+    const unsigned long long g = off + i;
+    if (g < n_stored) {
+      dst[g] = q;
+    } else if (dst[n_total - 1 - g] != q) {
+      atomicExch((unsigned long long*)&st->status, (unsigned long long)LCS_EINVAL);
+    }
+  }
+}
+
+// out[i] = value of state off+i (mirrored from the stored half when needed)
+template <bool TO_DOUBLE>
+__global__ void export_kernel(const long long* __restrict__ src, unsigned long long off, unsigned long long len,
+                              unsigned long long n_stored, unsigned long long n_total, double scale,
+                              void* __restrict__ out) {
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const unsigned long long g = off + i;
+    const long long q = src[g < n_stored ? g : n_total - 1 - g];
+    if constexpr (TO_DOUBLE)
+      static_cast<double*>(out)[i] = __ll2double_rn(q) * scale;
+    else
+      static_cast<long long*>(out)[i] = q;
+  }
+}
+
+__global__ void maxabs_kernel(const long long* __restrict__ v, unsigned long long n, DevState* st) {
+  long long m = 0;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const long long a = v[i];
+    m = max(m, a == LLONG_MIN ? LLONG_MAX : (a < 0 ? -a : a));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&st->maxabs, m);
+}
+
+__global__ void init_state_kernel(DevState* st) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) {
+    DevState z{};
+    z.kept_iter = -1;
+    *st = z;
+  }
+}
+
+}  // namespace lcs
+
+// ---------------------------------------------------------------------------
+// The handle.
+
+using namespace lcs;
+
+struct lcs_bound {
+  int sigma, d, h;
+  unsigned long long n_total, n_stored, n_tail;
+  int sym;
+  lcs_bound_opts opts;
+  cudaStream_t stream;
+  bool own_stream;
+  int device;
+  const KernelSet* ks;
+  long long* ring[kMaxD + 1];
+  int newest;  // ring slot of the newest iterate
+  long long* ubuf;
+  DevState* dstate;
+  RedPartial* partials;
+  int grid_sweep, grid_check, n_partials;
+  void* staging;  // device staging for host transfers
+  size_t staging_bytes;
+  long long iters_done;
+  double vbound;  // upper bound of max |v| over the live iterates, in units of 2^-K
+  long long one;
+  // timing
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sweep_ev, check_ev;
+  double sweep_ms, check_ms;
+  long long sweep_n, check_n, launches;
+  unsigned long long sweep_bytes, check_bytes;
+};
+
+static void* dev_alloc(lcs_bound* H, size_t bytes) {
+  if (H->opts.alloc) return H->opts.alloc(bytes, H->opts.alloc_ctx);
+  void* p = nullptr;
+  if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return p;
+}
+
+static void dev_free(lcs_bound* H, void* p) {
+  if (!p) return;
+  if (H->opts.alloc) {
+    if (H->opts.free) H->opts.free(p, H->opts.alloc_ctx);
+  } else {
+    cudaFree(p);
+  }
+}
+
+static int grid_for(const void* fn, int sms, unsigned long long work_items) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0) != cudaSuccess || per_sm < 1) {
+    cudaGetLastError();
+    per_sm = 1;
+  }
+  unsigned long long full = (unsigned long long)sms * (unsigned long long)per_sm;
+  unsigned long long need = (work_items + kBlock - 1) / kBlock;
+  if (need < 1) need = 1;
+  return (int)std::min(full, need);
+}
+
+// headroom: every intermediate of a sweep or check is at most sigma^d times the
+// largest |value| (plus lower-order terms); keep it below 2^62
+static bool headroom_ok(const lcs_bound* H, double vb) {
+  const double sd = std::pow((double)H->sigma, (double)H->d);
+  return sd * (vb + 4.0 * (double)H->one) * 2.0 < 4.6e18;
+}
+
+extern "C" {
+
+lcs_status lcs_bound_default_opts(lcs_bound_opts* o) {
+  if (!o) return fail(LCS_EINVAL, "opts is NULL");
+  std::memset(o, 0, sizeof *o);
+  o->check_every = 0;
+  o->r_mode = 0;
+  o->f_mode = 0;
+  o->frac_bits = 44;
+  o->keep_u = 0;
+  o->symmetry = 1;
+  o->timing = 0;
+  return LCS_OK;
+}
+
+const char* lcs_bound_errstr(lcs_status st) {
+  switch (st) {
+    case LCS_OK: return "ok";
+    case LCS_EINVAL: return "invalid argument";
+    case LCS_ENOMEM: return "out of memory";
+    case LCS_ECUDA: return "CUDA error";
+    case LCS_ETIMEOUT: return "device wait timed out";
+    case LCS_ENOBOUND: return "no feasibility check has run";
+    case LCS_EOVERFLOW: return "fixed-point range exceeded";
+    case LCS_EUNSUPPORTED: return "no kernel for this shape or mode";
+  }
+  return "unknown status";
+}
+
+const char* lcs_bound_last_error(void) { return g_last_error.c_str(); }
+
+void lcs_bound_destroy(lcs_bound_t* H) {
+  if (!H) return;
+  if (H->stream) cudaStreamSynchronize(H->stream);
+  for (auto& e : H->sweep_ev) cudaEventDestroy(e.first), cudaEventDestroy(e.second);
+  for (auto& e : H->check_ev) cudaEventDestroy(e.first), cudaEventDestroy(e.second);
+  for (int k = 0; k <= H->d; ++k) dev_free(H, H->ring[k]);
+  dev_free(H, H->ubuf);
+  dev_free(H, H->dstate);
+  dev_free(H, H->partials);
+  dev_free(H, H->staging);
+  if (H->own_stream && H->stream) cudaStreamDestroy(H->stream);
+  delete H;
+}
+
+lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_in, lcs_bound_t** out) {
+  if (!out) return fail(LCS_EINVAL, "out is NULL");
+  *out = nullptr;
+  lcs_bound_opts opts;
+  if (opts_in)
+    opts = *opts_in;
+  else
+    lcs_bound_default_opts(&opts);
+  if (opts.frac_bits == 0) opts.frac_bits = 44;
+  if (sigma < 2 || d < 2 || h < 1 || d > kMaxD) return fail(LCS_EINVAL, "bad shape sigma=%d d=%d h=%d", sigma, d, h);
+  if (opts.frac_bits < 8 || opts.frac_bits > 56) return fail(LCS_EINVAL, "frac_bits %d outside 8..56", opts.frac_bits);
+  if (opts.r_mode != 0 && opts.r_mode != 1) return fail(LCS_EINVAL, "r_mode %d", opts.r_mode);
+  if (opts.check_every < 0) return fail(LCS_EINVAL, "check_every %d", opts.check_every);
+  if (opts.f_mode != 0) return fail(LCS_EUNSUPPORTED, "f_mode %d has no GPU kernel", opts.f_mode);
+  if (opts.alloc && !opts.free) return fail(LCS_EINVAL, "alloc given without free");
+  // state count below 2^40
+  unsigned long long n = 1;
+  for (int i = 0; i < d * h; ++i) {
+    n *= (unsigned long long)sigma;
+    if (n >= (1ull << 40)) return fail(LCS_EINVAL, "sigma^(d h) must be below 2^40");
+  }
+  const int sym = (sigma == 2 && opts.symmetry && h >= 2) ? 1 : 0;
+  const KernelSet* ks = find_kernels(sigma, d, sym);
+  if (!ks) return fail(LCS_EUNSUPPORTED, "no kernel compiled for sigma=%d d=%d", sigma, d);
+
+  lcs_bound* H = new (std::nothrow) lcs_bound();
+  if (!H) return fail(LCS_ENOMEM, "host allocation");
+  H->sigma = sigma;
+  H->d = d;
+  H->h = h;
+  H->n_total = n;
+  H->sym = sym;
+  H->n_stored = sym ? n / 2 : n;
+  unsigned long long sd = 1;
+  for (int i = 0; i < d; ++i) sd *= (unsigned long long)sigma;
+  H->n_tail = n / sd;
+  H->opts = opts;
+  H->ks = ks;
+  H->one = 1ll << opts.frac_bits;
+  H->newest = d - 1;
+
+  cudaError_t e = cudaGetDevice(&H->device);
+  if (e != cudaSuccess) {
+    lcs_bound_destroy(H);
+    return fail(LCS_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
+  }
+  if (opts.stream) {
+    H->stream = (cudaStream_t)opts.stream;
+    H->own_stream = false;
+  } else {
+    e = cudaStreamCreateWithFlags(&H->stream, cudaStreamNonBlocking);
+    if (e != cudaSuccess) {
+      lcs_bound_destroy(H);
+      return fail(LCS_ECUDA, "cudaStreamCreate: %s", cudaGetErrorString(e));
+    }
+    H->own_stream = true;
+  }
+  int sms = 0;
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H->device);
+  if (sms < 1) sms = 1;
+  const unsigned long long thread_items = sym ? H->n_tail / 2 : H->n_tail;
+  H->grid_sweep = grid_for(ks->sweep_fn, sms, thread_items);
+  H->grid_check = grid_for(ks->check_fn, sms, thread_items);
+  H->n_partials = std::max(H->grid_sweep, H->grid_check);
+
+  const size_t vbytes = (size_t)H->n_stored * sizeof(long long);
+  for (int k = 0; k <= d; ++k) {
+    H->ring[k] = (long long*)dev_alloc(H, vbytes);
+    if (!H->ring[k]) {
+      lcs_bound_destroy(H);
+      return fail(LCS_ENOMEM, "iterate vector %d (%zu bytes)", k, vbytes);
+    }
+  }
+  if (opts.keep_u) {
+    H->ubuf = (long long*)dev_alloc(H, vbytes);
+    if (!H->ubuf) {
+      lcs_bound_destroy(H);
+      return fail(LCS_ENOMEM, "u vector (%zu bytes)", vbytes);
+    }
+  }
+  H->dstate = (DevState*)dev_alloc(H, sizeof(DevState));
+  H->partials = (RedPartial*)dev_alloc(H, sizeof(RedPartial) * (size_t)H->n_partials);
+  if (!H->dstate || !H->partials) {
+    lcs_bound_destroy(H);
+    return fail(LCS_ENOMEM, "state and reduction scratch");
+  }
+  // zero start (Algorithm 2: v <- 0)
+  for (int k = 0; k < d; ++k) {
+    e = cudaMemsetAsync(H->ring[k], 0, vbytes, H->stream);
+    if (e != cudaSuccess) {
+      lcs_bound_destroy(H);
+      return fail(LCS_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
+  }
+  if (H->ubuf) cudaMemsetAsync(H->ubuf, 0, vbytes, H->stream);
+  init_state_kernel<<<1, 32, 0, H->stream>>>(H->dstate);
+  e = cudaStreamSynchronize(H->stream);
+  if (e == cudaSuccess) e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    lcs_bound_destroy(H);
+    return fail(LCS_ECUDA, "create: %s", cudaGetErrorString(e));
+  }
+  H->vbound = 0.0;
+  *out = H;
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_size(const lcs_bound_t* H, uint64_t* n_states, uint64_t* n_stored) {
+  if (!H) return fail(LCS_EINVAL, "handle is NULL");
+  if (n_states) *n_states = H->n_total;
+  if (n_stored) *n_stored = H->n_stored;
+  return LCS_OK;
+}
+
+static void fold_events(lcs_bound* H) {
+  for (auto& e : H->sweep_ev) {
+    float ms = 0;
+    cudaEventSynchronize(e.second);
+    cudaEventElapsedTime(&ms, e.first, e.second);
+    H->sweep_ms += ms;
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  for (auto& e : H->check_ev) {
+    float ms = 0;
+    cudaEventSynchronize(e.second);
+    cudaEventElapsedTime(&ms, e.first, e.second);
+    H->check_ms += ms;
+    cudaEventDestroy(e.first);
+    cudaEventDestroy(e.second);
+  }
+  H->sweep_ev.clear();
+  H->check_ev.clear();
+}
+
+static lcs_status timed_begin(lcs_bound* H, cudaEvent_t* a) {
+  if (!H->opts.timing) return LCS_OK;
+  LCS_CUDA(cudaEventCreate(a));
+  LCS_CUDA(cudaEventRecord(*a, H->stream));
+  return LCS_OK;
+}
+
+static lcs_status timed_end(lcs_bound* H, cudaEvent_t a, bool sweep) {
+  if (!H->opts.timing) return LCS_OK;
+  cudaEvent_t b;
+  LCS_CUDA(cudaEventCreate(&b));
+  LCS_CUDA(cudaEventRecord(b, H->stream));
+  (sweep ? H->sweep_ev : H->check_ev).emplace_back(a, b);
+  if (H->sweep_ev.size() + H->check_ev.size() > 8192) fold_events(H);
+  return LCS_OK;
+}
+
+static lcs_status run_check(lcs_bound* H, const long long* u, bool R_from_state, long long R, long long iter,
+                            bool finalize) {
+  CheckParams c{};
+  c.u = u;
+  c.n_tail = H->n_tail;
+  c.n_stored = H->n_stored;
+  c.h = H->h;
+  c.one = H->one;
+  c.state = H->dstate;
+  c.R_from_state = R_from_state ? 1 : 0;
+  c.R = R;
+  c.partials = H->partials;
+  cudaEvent_t a = nullptr;
+  lcs_status st = timed_begin(H, &a);
+  if (st) return st;
+  H->ks->check(c, H->grid_check, H->stream);
+  LCS_CUDA(cudaGetLastError());
+  st = timed_end(H, a, false);
+  if (st) return st;
+  H->check_n++;
+  H->check_bytes += 8ull * H->n_stored;
+  H->launches++;
+  if (finalize) {
+    finalize_check_kernel<<<1, kFinalBlock, 0, H->stream>>>(H->partials, H->grid_check, H->dstate, iter);
+    LCS_CUDA(cudaGetLastError());
+    H->launches++;
+  }
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_iterate(lcs_bound_t* H, int64_t n_iters) {
+  if (!H) return fail(LCS_EINVAL, "handle is NULL");
+  if (n_iters < 0) return fail(LCS_EINVAL, "n_iters < 0");
+  if (n_iters == 0) return LCS_OK;
+  const double vb_after = H->vbound + (double)n_iters * (double)H->one;
+  if (!headroom_ok(H, vb_after))
+    return fail(LCS_EOVERFLOW, "iterates could exceed the fixed-point range (max |v| up to %.3g)",
+                vb_after / (double)H->one);
+  const int rows = H->d + 1;
+  for (int64_t i = 0; i < n_iters; ++i) {
+    const long long it = H->iters_done + 1;
+    const bool check = (H->opts.check_every > 0 && it % H->opts.check_every == 0) || i == n_iters - 1;
+    const int out_slot = (H->newest + 1) % rows;
+    SweepParams p{};
+    for (int k = 1; k <= H->d; ++k) p.prev[k - 1] = H->ring[(H->newest - (k - 1) + rows) % rows];
+    p.out = H->ring[out_slot];
+    p.n_tail = H->n_tail;
+    p.n_stored = H->n_stored;
+    p.h = H->h;
+    p.incr = check ? 1 : 0;
+    p.r_mode = H->opts.r_mode;
+    p.one = H->one;
+    p.partials = H->partials;
+    cudaEvent_t a = nullptr;
+    lcs_status st = timed_begin(H, &a);
+    if (st) return st;
+    H->ks->sweep(p, H->grid_sweep, H->stream);
+    LCS_CUDA(cudaGetLastError());
+    st = timed_end(H, a, true);
+    if (st) return st;
+    H->sweep_n++;
+    H->sweep_bytes += 8ull * (unsigned long long)(H->d + 1) * H->n_stored;
+    H->launches++;
+    if (check) {
+      finalize_incr_kernel<<<1, kFinalBlock, 0, H->stream>>>(H->partials, H->grid_sweep, H->opts.r_mode, H->dstate,
+                                                              it);
+      LCS_CUDA(cudaGetLastError());
+      H->launches++;
+      st = run_check(H, p.out, true, 0, it, true);
+      if (st) return st;
+      if (H->ubuf) {
+        copy_if_kept_kernel<<<H->grid_sweep, kBlock, 0, H->stream>>>(p.out, H->ubuf, H->n_stored, H->dstate);
+        LCS_CUDA(cudaGetLastError());
+        H->launches++;
+      }
+    }
+    H->newest = out_slot;
+    H->iters_done = it;
+  }
+  H->vbound = vb_after;
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_read_report(lcs_bound_t* H, lcs_bound_report* out) {
+  if (!H || !out) return fail(LCS_EINVAL, "NULL argument");
+  DevState s;
+  LCS_CUDA(cudaMemcpyAsync(&s, H->dstate, sizeof s, cudaMemcpyDeviceToHost, H->stream));
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
+  out->iters_done = H->iters_done;
+  out->R = s.R;
+  out->argmin = s.argmin;
+  out->E = s.E;
+  out->r = s.r;
+  out->eps = s.eps;
+  out->kept_iter = s.kept_iter;
+  out->have_check = s.have_check;
+  out->frac_bits = H->opts.frac_bits;
+  out->status = (int)s.status;
+  return LCS_OK;
+}
+
+// round-down conversion of a fixed-point value to double
+static double fx_to_double_rd(long long a, int frac_bits) {
+  double x = (double)a;  // round to nearest
+  if (x >= 9223372036854775808.0)
+    x = std::nextafter(x, -INFINITY);
+  else if ((long double)x > (long double)a && (long long)x > a)
+    x = std::nextafter(x, -INFINITY);
+  return std::ldexp(x, -frac_bits);
+}
+
+lcs_status lcs_bound_read(lcs_bound_t* H, double* bound_rd, uint64_t* argmin_state, double* r, double* eps,
+                          int64_t* at_iter) {
+  lcs_bound_report rep;
+  lcs_status st = lcs_bound_read_report(H, &rep);
+  if (st) return st;
+  if (rep.status) return fail((lcs_status)rep.status, "device status %d", rep.status);
+  if (!rep.have_check) return fail(LCS_ENOBOUND, "no feasibility check has run");
+  const int K = H->opts.frac_bits;
+  const long long B = (long long)H->d * (rep.r - rep.eps);  // |r|, |eps| < 2^62 / d by the headroom rule
+  if (bound_rd) *bound_rd = fx_to_double_rd(B, K);
+  if (argmin_state) *argmin_state = rep.argmin;
+  if (r) *r = std::ldexp((double)rep.r, -K);
+  if (eps) *eps = std::ldexp((double)rep.eps, -K);
+  if (at_iter) *at_iter = rep.kept_iter;
+  return LCS_OK;
+}
+
+static lcs_status ensure_staging(lcs_bound* H, size_t bytes) {
+  if (H->staging_bytes >= bytes) return LCS_OK;
+  dev_free(H, H->staging);
+  H->staging = dev_alloc(H, bytes);
+  H->staging_bytes = H->staging ? bytes : 0;
+  if (!H->staging) return fail(LCS_ENOMEM, "staging buffer (%zu bytes)", bytes);
+  return LCS_OK;
+}
+
+static const size_t kChunk = (size_t)32 << 20;  // elements per host transfer chunk (256 MiB)
+
+// Ingest [off, off+len) of an input vector.  Under complement-symmetric
+// storage the part below n_stored is written before the part above it is
+// compared with its mirror: two launches, ordered on the stream.
+static lcs_status ingest_range(lcs_bound* H, const void* src, unsigned long long off, unsigned long long len,
+                               long long* dst, bool from_double, double scale) {
+  const unsigned long long split = std::min(std::max(H->n_stored, off), off + len);
+  const unsigned long long parts[2][2] = {{off, split - off}, {split, off + len - split}};
+  for (const auto& pr : parts) {
+    if (pr[1] == 0) continue;
+    const void* s = (const char*)src + (pr[0] - off) * 8;
+    const int grid = (int)std::min<unsigned long long>(4096, (pr[1] + kBlock - 1) / kBlock);
+    if (from_double)
+      ingest_kernel<true><<<grid, kBlock, 0, H->stream>>>(s, pr[0], pr[1], dst, H->n_stored, H->n_total, scale,
+                                                          H->dstate);
+    else
+      ingest_kernel<false><<<grid, kBlock, 0, H->stream>>>(s, pr[0], pr[1], dst, H->n_stored, H->n_total, scale,
+                                                           H->dstate);
+    LCS_CUDA(cudaGetLastError());
+    H->launches++;
+  }
+  return LCS_OK;
+}
+
+static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_device, bool from_double) {
+  if (!H) return fail(LCS_EINVAL, "handle is NULL");
+  if (!v) return fail(LCS_EINVAL, "NULL argument");
+  const double scale = std::ldexp(1.0, H->opts.frac_bits);
+  LCS_CUDA(cudaMemsetAsync(H->dstate, 0, sizeof(DevState), H->stream));
+  for (int k = 0; k < H->d; ++k) {
+    if (!v[k]) return fail(LCS_EINVAL, "start vector %d is NULL", k);
+    long long* dst = H->ring[H->d - 1 - k];
+    if (on_device) {
+      lcs_status st = ingest_range(H, v[k], 0, H->n_total, dst, from_double, scale);
+      if (st) return st;
+    } else {
+      lcs_status st = ensure_staging(H, kChunk * 8);
+      if (st) return st;
+      for (unsigned long long off = 0; off < H->n_total; off += kChunk) {
+        const unsigned long long len = std::min<unsigned long long>(kChunk, H->n_total - off);
+        LCS_CUDA(cudaMemcpyAsync(H->staging, (const char*)v[k] + off * 8, len * 8, cudaMemcpyHostToDevice, H->stream));
+        st = ingest_range(H, H->staging, off, len, dst, from_double, scale);
+        if (st) return st;
+      }
+    }
+    const int grid = (int)std::min<unsigned long long>(4096, (H->n_stored + kBlock - 1) / kBlock);
+    maxabs_kernel<<<grid, kBlock, 0, H->stream>>>(dst, H->n_stored, H->dstate);
+    LCS_CUDA(cudaGetLastError());
+    H->launches++;
+  }
+  DevState s;
+  LCS_CUDA(cudaMemcpyAsync(&s, H->dstate, sizeof s, cudaMemcpyDeviceToHost, H->stream));
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
+  // reset the results: the kept triplet returns to the initial (v_0, 0, 0)
+  init_state_kernel<<<1, 32, 0, H->stream>>>(H->dstate);
+  LCS_CUDA(cudaGetLastError());
+  if (H->ubuf) LCS_CUDA(cudaMemcpyAsync(H->ubuf, H->ring[0], H->n_stored * 8, cudaMemcpyDeviceToDevice, H->stream));
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
+  H->newest = H->d - 1;
+  H->iters_done = 0;
+  if (s.status == LCS_EINVAL)
+    return fail(LCS_EINVAL, "start vectors are not complement-symmetric (v[N-1-x] != v[x])");
+  if (s.status == LCS_EOVERFLOW) return fail(LCS_EOVERFLOW, "start values outside the fixed-point range");
+  H->vbound = (double)s.maxabs;
+  if (!headroom_ok(H, H->vbound)) return fail(LCS_EOVERFLOW, "start values too large for the fixed-point headroom");
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_set_start(lcs_bound_t* H, const double* const* v, int on_device) {
+  return set_start_checked(H, (const void* const*)v, on_device, true);
+}
+
+lcs_status lcs_bound_set_start_fx(lcs_bound_t* H, const int64_t* const* v, int on_device) {
+  return set_start_checked(H, (const void* const*)v, on_device, false);
+}
+
+static lcs_status export_impl(lcs_bound* H, int k, void* dst, int on_device, bool to_double) {
+  if (!H || !dst) return fail(LCS_EINVAL, "NULL argument");
+  if (k < -1 || k >= H->d) return fail(LCS_EINVAL, "k=%d outside -1..d-1", k);
+  const long long* src;
+  if (k == -1) {
+    if (!H->ubuf) return fail(LCS_EINVAL, "u is not retained (opts.keep_u = 0)");
+    src = H->ubuf;
+  } else {
+    const int rows = H->d + 1;
+    src = H->ring[(H->newest - k + rows) % rows];
+  }
+  const double scale = std::ldexp(1.0, -H->opts.frac_bits);
+  if (on_device) {
+    const int grid = (int)std::min<unsigned long long>(4096, (H->n_total + kBlock - 1) / kBlock);
+    if (to_double)
+      export_kernel<true><<<grid, kBlock, 0, H->stream>>>(src, 0, H->n_total, H->n_stored, H->n_total, scale, dst);
+    else
+      export_kernel<false><<<grid, kBlock, 0, H->stream>>>(src, 0, H->n_total, H->n_stored, H->n_total, scale, dst);
+    LCS_CUDA(cudaGetLastError());
+    H->launches++;
+    return LCS_OK;
+  }
+  lcs_status st = ensure_staging(H, kChunk * 8);
+  if (st) return st;
+  for (unsigned long long off = 0; off < H->n_total; off += kChunk) {
+    const unsigned long long len = std::min<unsigned long long>(kChunk, H->n_total - off);
+    const int grid = (int)std::min<unsigned long long>(4096, (len + kBlock - 1) / kBlock);
+    if (to_double)
+      export_kernel<true><<<grid, kBlock, 0, H->stream>>>(src, off, len, H->n_stored, H->n_total, scale, H->staging);
+    else
+      export_kernel<false><<<grid, kBlock, 0, H->stream>>>(src, off, len, H->n_stored, H->n_total, scale, H->staging);
+    LCS_CUDA(cudaGetLastError());
+    H->launches++;
+    LCS_CUDA(cudaMemcpyAsync((char*)dst + off * 8, H->staging, len * 8, cudaMemcpyDeviceToHost, H->stream));
+  }
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_export(lcs_bound_t* H, int k, double* dst, int on_device) {
+  return export_impl(H, k, dst, on_device, true);
+}
+
+lcs_status lcs_bound_export_fx(lcs_bound_t* H, int k, int64_t* dst, int on_device) {
+  return export_impl(H, k, dst, on_device, false);
+}
+
+lcs_status lcs_bound_check_vector(lcs_bound_t* H, const int64_t* u_dev, int64_t R, int64_t* E_out) {
+  if (!H || !u_dev || !E_out) return fail(LCS_EINVAL, "NULL argument");
+  lcs_status st = run_check(H, (const long long*)u_dev, false, R, 0, false);
+  if (st) return st;
+  std::vector<RedPartial> parts((size_t)H->grid_check);
+  LCS_CUDA(cudaMemcpyAsync(parts.data(), H->partials, sizeof(RedPartial) * parts.size(), cudaMemcpyDeviceToHost,
+                           H->stream));
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
+  long long E = 0;
+  for (const auto& q : parts) E = std::max(E, q.v);
+  *E_out = E;
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_stats(lcs_bound_t* H, lcs_bound_stats_t* out, int reset) {
+  if (!H || !out) return fail(LCS_EINVAL, "NULL argument");
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
+  fold_events(H);
+  out->sweep_launches = H->sweep_n;
+  out->sweep_ms = H->sweep_ms;
+  out->check_launches = H->check_n;
+  out->check_ms = H->check_ms;
+  out->kernel_launches = H->launches;
+  out->sweep_bytes = H->sweep_bytes;
+  out->check_bytes = H->check_bytes;
+  if (reset) {
+    H->sweep_n = H->check_n = H->launches = 0;
+    H->sweep_ms = H->check_ms = 0;
+    H->sweep_bytes = H->check_bytes = 0;
+  }
+  return LCS_OK;
+}
+
+lcs_status lcs_sweep_fx(int sigma, int d, int h, int f_mode, int frac_bits, const int64_t* const* v_prev,
+                        int64_t* v_out, void* stream) {
+  if (sigma < 2 || d < 2 || h < 1 || d > kMaxD) return fail(LCS_EINVAL, "bad shape");
+  if (f_mode != 0) return fail(LCS_EUNSUPPORTED, "f_mode %d", f_mode);
+  if (frac_bits == 0) frac_bits = 44;
+  if (frac_bits < 8 || frac_bits > 56) return fail(LCS_EINVAL, "frac_bits");
+  if (!v_prev || !v_out) return fail(LCS_EINVAL, "NULL argument");
+  unsigned long long n = 1, sd = 1;
+  for (int i = 0; i < d * h; ++i) {
+    n *= (unsigned long long)sigma;
+    if (n >= (1ull << 40)) return fail(LCS_EINVAL, "sigma^(d h) must be below 2^40");
+  }
+  for (int i = 0; i < d; ++i) sd *= (unsigned long long)sigma;
+  const KernelSet* ks = find_kernels(sigma, d, 0);
+  if (!ks) return fail(LCS_EUNSUPPORTED, "no kernel for sigma=%d d=%d", sigma, d);
+  SweepParams p{};
+  for (int k = 0; k < d; ++k) {
+    if (!v_prev[k]) return fail(LCS_EINVAL, "v_prev[%d] is NULL", k);
+    if ((const void*)v_prev[k] == (const void*)v_out) return fail(LCS_EINVAL, "v_out aliases an input");
+    p.prev[k] = (const long long*)v_prev[k];
+  }
+  p.out = (long long*)v_out;
+  p.n_tail = n / sd;
+  p.n_stored = n;
+  p.h = h;
+  p.incr = 0;
+  p.one = 1ll << frac_bits;
+  int dev = 0, sms = 1;
+  LCS_CUDA(cudaGetDevice(&dev));
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = grid_for(ks->sweep_fn, std::max(sms, 1), p.n_tail);
+  ks->sweep(p, grid, (cudaStream_t)stream);
+  LCS_CUDA(cudaGetLastError());
+  return LCS_OK;
+}
+
+}  // extern "C"

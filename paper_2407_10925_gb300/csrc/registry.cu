@@ -1,0 +1,19 @@
+// Lookup of the kernels compiled for an alphabet size, string count and
+// storage mode.
+#include "lcs_common.h"
+
+namespace lcs {
+
+const KernelSet* kernels_sigma2(int d, int sym);
+const KernelSet* kernels_sigma3(int d);
+const KernelSet* kernels_sigma45(int sigma, int d);
+
+const KernelSet* find_kernels(int sigma, int d, int sym) {
+  if (sigma == 2) return kernels_sigma2(d, sym);
+  if (sym) return nullptr;
+  if (sigma == 3) return kernels_sigma3(d);
+  if (sigma == 4 || sigma == 5) return kernels_sigma45(sigma, d);
+  return nullptr;
+}
+
+}  // namespace lcs

@@ -1,0 +1,87 @@
+"""The C-ABI library builds, loads and exports every entry point include/lcs_bound.h declares.
+
+No GPU: only calls that need no device (status strings, defaults, argument
+validation that happens before any CUDA call).
+"""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+HEADER = os.path.join(ROOT, "include", "lcs_bound.h")
+
+
+def declared_functions():
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    names = re.findall(r"^\s*(?:const\s+)?[\w]+\s*\*?\s*(lcs_\w+)\s*\(", text, flags=re.M)
+    return sorted(set(names))
+
+
+@pytest.fixture(scope="module")
+def L():
+    from paper_2407_10925_gb300 import binding
+
+    return binding.lib()
+
+
+def test_header_declares_the_documented_api():
+    names = declared_functions()
+    for required in ["lcs_bound_create", "lcs_bound_iterate", "lcs_bound_read", "lcs_bound_destroy",
+                     "lcs_bound_set_start", "lcs_bound_export", "lcs_bound_errstr", "lcs_sweep_fx"]:
+        assert required in names
+
+
+def test_every_declared_symbol_is_exported(L):
+    missing = [n for n in declared_functions() if not hasattr(L, n)]
+    assert missing == []
+
+
+def test_status_strings(L):
+    from paper_2407_10925_gb300 import binding
+
+    for st in range(8):
+        assert binding.lcs_bound_errstr(st)
+    assert binding.lcs_bound_errstr(0) == "ok"
+
+
+def test_default_opts(L):
+    from paper_2407_10925_gb300 import binding
+
+    o = binding.lcs_bound_default_opts()
+    assert (o.check_every, o.r_mode, o.f_mode, o.frac_bits, o.symmetry) == (0, 0, 0, 44, 1)
+
+
+@pytest.mark.parametrize("shape", [(1, 2, 3), (2, 1, 3), (2, 2, 0), (2, 9, 1), (2, 2, 20)])
+def test_bad_shapes_rejected_before_any_device_call(L, shape):
+    from paper_2407_10925_gb300 import binding
+
+    with pytest.raises(binding.LcsError) as e:
+        binding.lcs_bound_create(*shape)
+    assert e.value.status == binding.LCS_EINVAL
+
+
+def test_bad_options_rejected(L):
+    from paper_2407_10925_gb300 import binding
+
+    o = binding.lcs_bound_default_opts()
+    o.frac_bits = 70
+    with pytest.raises(binding.LcsError) as e:
+        binding.lcs_bound_create(2, 2, 3, o)
+    assert e.value.status == binding.LCS_EINVAL
+    o = binding.lcs_bound_default_opts()
+    o.f_mode = 1
+    with pytest.raises(binding.LcsError) as e:
+        binding.lcs_bound_create(2, 2, 3, o)
+    assert e.value.status == binding.LCS_EUNSUPPORTED
+
+
+def test_null_handle_calls_fail_cleanly(L):
+    from paper_2407_10925_gb300 import binding
+
+    assert L.lcs_bound_iterate(None, 1) == binding.LCS_EINVAL
+    assert L.lcs_bound_read(None, None, None, None, None, None) == binding.LCS_EINVAL
+    L.lcs_bound_destroy(None)
