@@ -193,6 +193,18 @@ def profiled_traffic(config_name, kernel):
 
 
 # ---------------------------------------------------------------------------
+# ranks: replicas only; the slowest rank's time is the job's time
+
+
+def reduce_max(x: float, dist=None, device=None) -> float:
+    """max of x over all ranks (x itself without a process group)."""
+    if dist is None or not dist.is_initialized():
+        return x
+    import torch
+
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
 
 
 def run_reference(args, cfg, rank):
@@ -283,12 +295,8 @@ def main():
         ev1.record(stream)
         torch.cuda.synchronize()
         barrier()
-    ms = ev0.elapsed_time(ev1)
+    ms = reduce_max(ev0.elapsed_time(ev1), dist, "cuda")
     st = hnd.stats(reset=True)
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
     bound, argmin, r, eps, at_iter = hnd.read()
     rep = hnd.report()
 
@@ -318,11 +326,7 @@ def main():
             dt = time.perf_counter() - t0
             if i > 0:
                 e2e_ms.append(dt * 1e3)
-        e2e_ms_step = max(e2e_ms)
-        if dist is not None:
-            t = torch.tensor([e2e_ms_step], device="cuda")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            e2e_ms_step = float(t.item())
+        e2e_ms_step = reduce_max(max(e2e_ms), dist, "cuda")
         e2e = {"value": world * n * C / (e2e_ms_step / 1e3), "unit": "state-updates/s",
                "h2d_bytes_per_step": d * n * 8, "d2h_bytes_per_step": 80,
                "ms_per_step": e2e_ms_step,
