@@ -212,6 +212,36 @@ const char* lcs_bound_last_error(void);
 lcs_status lcs_sweep_fx(int sigma, int d, int h, int f_mode, int frac_bits, const int64_t* const* v_prev, int64_t* v_out,
                         void* stream);
 
+/* ------------------------------------------------------------------------ */
+/* Entry point that allocates nothing.  The paper has no counterpart: it is an
+ * interface for callers that cannot allocate device memory -- code running
+ * inside a memory pool it does not own, a plugin whose host forbids device
+ * allocations, or a process that has already committed all free HBM.
+ *
+ * One evaluation of F fused with the increment reduction, as one checked
+ * iteration of lcs_bound_iterate performs it: v_out = F(v_prev[0], ..,
+ * v_prev[d-1]) (v_prev[k-1] = the iterate k steps older than the one being
+ * computed; sigma^(d h) fixed-point int64 values each, device pointers, state
+ * order, no symmetry), then *R_out = min_x (v_out - v_prev[0])[x] (max with
+ * r_mode = 1) and *argmin_out = the smallest state index attaining it.
+ * R_out and argmin_out are device pointers owned by the caller.  frac_bits as
+ * in lcs_bound_opts (0 -> 44).  stream: cudaStream_t or NULL.  Asynchronous.
+ *
+ * Scratch: the per-CTA partials of the reduction live in a fixed 64 KiB
+ * array inside the library (4096 partials), reserved on every device that
+ * loads the library until the process exits.  The first call on each device
+ * looks up that array's device address (cudaGetSymbolAddress) with the
+ * device current; make that first call before any stream capture.  A call
+ * whose launch would need more than 4096 partials returns LCS_EINVAL.  The
+ * function calls no allocator (no cudaMalloc, cudaFree or allocating library
+ * routine).  All calls share the one array and each call overwrites every
+ * slot it later reads, so no state carries over -- but calls that overlap on
+ * the GPU (different streams, or different host threads without ordering)
+ * race on it: order them.  Errors: LCS_EINVAL, LCS_EUNSUPPORTED, LCS_ECUDA;
+ * lcs_bound_last_error() gives the message. */
+lcs_status lcs_sweep_incr_fx_noalloc(int sigma, int d, int h, int frac_bits, int r_mode, const int64_t* const* v_prev,
+                                     int64_t* v_out, int64_t* R_out, uint64_t* argmin_out, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

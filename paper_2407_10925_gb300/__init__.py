@@ -23,5 +23,6 @@ from .binding import (  # noqa: F401
     lcs_bound_size,
     lcs_bound_stats,
     lcs_sweep_fx,
+    lcs_sweep_incr_fx_noalloc,
     lib,
 )

@@ -97,6 +97,7 @@ def lib():
                 "lcs_bound_check_vector": [vp, vp, i64, P(i64)],
                 "lcs_bound_stats": [vp, P(lcs_bound_stats_t), i32],
                 "lcs_sweep_fx": [i32, i32, i32, i32, i32, vp, vp, vp],
+                "lcs_sweep_incr_fx_noalloc": [i32, i32, i32, i32, i32, vp, vp, vp, vp, vp],
             }
             for name, args in sig.items():
                 fn = getattr(L, name)
@@ -269,6 +270,23 @@ def lcs_sweep_fx(sigma, d, h, v_prev, v_out, f_mode=0, frac_bits=44, stream=None
     if not (on_dev and od):
         raise TypeError("lcs_sweep_fx takes CUDA tensors")
     _check(lib().lcs_sweep_fx(sigma, d, h, f_mode, frac_bits, arr, po, stream), "lcs_sweep_fx")
+
+
+def lcs_sweep_incr_fx_noalloc(sigma, d, h, v_prev, v_out, R_out, argmin_out, frac_bits=44, r_mode=0, stream=None):
+    """One sweep fused with the increment reduction, allocating nothing (CUDA tensors only).
+
+    For callers that cannot allocate device memory: the reduction's scratch is
+    a fixed array inside the library.  R_out and argmin_out are one-element
+    CUDA int64 tensors that receive R and its state index.
+    """
+    arr, on_dev = _vec_array(v_prev, np.int64)
+    po, od = _ptr_and_kind(v_out, np.int64)
+    pr, rd = _ptr_and_kind(R_out, np.int64)
+    pa, ad = _ptr_and_kind(argmin_out, np.int64)
+    if not (on_dev and od and rd and ad):
+        raise TypeError("lcs_sweep_incr_fx_noalloc takes CUDA tensors")
+    _check(lib().lcs_sweep_incr_fx_noalloc(sigma, d, h, frac_bits, r_mode, arr, po, pr, pa, stream),
+           "lcs_sweep_incr_fx_noalloc")
 
 
 # ---------------------------------------------------------------------------

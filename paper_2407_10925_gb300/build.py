@@ -23,6 +23,7 @@ SOURCES = [
     "kernels_s2.cu",
     "kernels_s3.cu",
     "kernels_s4.cu",
+    "noalloc.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -38,6 +38,10 @@ static lcs_status fail(lcs_status st, const char* fmt, ...) {
   return st;
 }
 
+// lets other translation units of the library set the message that
+// lcs_bound_last_error() returns
+__attribute__((visibility("hidden"))) void record_error(const char* msg) { g_last_error = msg; }
+
 #define LCS_CUDA(call)                                                                         \
   do {                                                                                         \
     cudaError_t e_ = (call);                                                                   \

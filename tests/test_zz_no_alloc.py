@@ -1,0 +1,68 @@
+"""The entry point that allocates nothing, against the handle API.
+
+lcs_sweep_incr_fx_noalloc serves callers that cannot allocate device memory
+(code inside a memory pool it does not own, plugins whose host forbids
+allocations, processes that have committed all free HBM): its reduction
+scratch is a fixed array inside the library.  It must produce what a handle
+produces for one checked iteration -- the new iterate, R and its state -- on
+consecutive calls that share that array.  Results are integers: compared
+exactly.  This file is collected last.
+"""
+import numpy as np
+import pytest
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2407_10925_gb300 as lb
+
+    lb.lib()
+    return torch, lb
+
+
+def _via_handle(lb, s, d, h, hist, r_mode):
+    with lb.LcsBound(s, d, h, symmetry=0, r_mode=r_mode) as hnd:
+        hnd.set_start_fx(hist)
+        hnd.iterate(1)
+        rep = hnd.report()
+        return hnd.export_fx(0), rep["R"], rep["argmin"]
+
+
+def _via_noalloc(torch, lb, s, d, h, hist, r_mode):
+    dev = [torch.from_numpy(v).cuda() for v in hist]
+    out = torch.empty(s ** (d * h), dtype=torch.int64, device="cuda")
+    R = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    arg = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    lb.lcs_sweep_incr_fx_noalloc(s, d, h, dev, out, R, arg, r_mode=r_mode)
+    torch.cuda.synchronize()
+    return out.cpu().numpy(), int(R.item()), int(arg.item())
+
+
+def test_noalloc_matches_handle_on_consecutive_calls(env):
+    torch, lb = env
+    # a larger shape first, then a smaller one that launches fewer CTAs, then a
+    # different kernel: each call must ignore whatever the previous left behind
+    cases = [(2, 2, 7, 0, 11), (2, 2, 4, 0, 12), (3, 2, 3, 1, 13)]
+    for s, d, h, r_mode, seed in cases:
+        hist = inputs.random_history(s, d, h, seed=seed)
+        want_v, want_R, want_arg = _via_handle(lb, s, d, h, hist, r_mode)
+        got_v, got_R, got_arg = _via_noalloc(torch, lb, s, d, h, hist, r_mode)
+        assert np.array_equal(got_v, want_v)
+        assert (got_R, got_arg) == (want_R, want_arg)
+
+
+def test_noalloc_rejects_bad_arguments(env):
+    torch, lb = env
+    v = torch.zeros(16, dtype=torch.int64, device="cuda")
+    R = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(lb.LcsError) as e:
+        lb.lcs_sweep_incr_fx_noalloc(2, 2, 2, [v, v], v, R, R)
+    assert e.value.status == 1  # output aliases an input
