@@ -168,10 +168,10 @@ def measured_peaks():
         return FALLBACK_HBM_GBS, "fallback"
 
 
-def kernel_source_hash():
+def kernel_source_hash(files):
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2407_10925_gb300", "csrc")
-    for name in sorted(os.listdir(csrc)):
+    for name in files:
         with open(os.path.join(csrc, name), "rb") as f:
             h.update(name.encode())
             h.update(f.read())
@@ -179,17 +179,17 @@ def kernel_source_hash():
 
 
 def profiled_traffic(config_name, kernel):
-    """dram bytes per launch from the committed ncu summary, if it was taken on the current sources."""
+    """dram bytes per launch from the committed ncu summary, if it was taken on the current kernel sources."""
     p = os.path.join(ROOT, "profiles", "traffic.json")
     try:
         with open(p) as f:
             j = json.load(f)
-    except (OSError, ValueError):
+        entry = j.get(kernel, {}).get(config_name)
+        if not entry or entry.get("source_hash") != kernel_source_hash(entry["source_files"]):
+            return None
+        return entry.get("dram_bytes_per_launch")
+    except (OSError, ValueError, KeyError):
         return None
-    entry = j.get(kernel, {}).get(config_name)
-    if not entry or entry.get("source_hash") != kernel_source_hash():
-        return None
-    return entry.get("dram_bytes_per_launch")
 
 
 # ---------------------------------------------------------------------------

@@ -163,7 +163,11 @@ lcs_status lcs_bound_set_start_fx(lcs_bound_t* hnd, const int64_t* const* v, int
 /* Copy the iterate k steps older than the newest (k = 0..d-1), or with
  * k = -1 the kept u (needs keep_u), into dst: sigma^(d h) values in
  * state-index order.  on_device selects the kind of dst.  Synchronises the
- * stream when dst is a host pointer. */
+ * stream when dst is a host pointer; with a device pointer the copy is
+ * asynchronous on the handle's stream (see lcs_bound_synchronize).
+ * Device pointers given to any call are read on the handle's stream: the
+ * caller must make sure their contents are complete (for example by
+ * synchronising the stream that produced them). */
 lcs_status lcs_bound_export(lcs_bound_t* hnd, int k, double* dst, int on_device);
 lcs_status lcs_bound_export_fx(lcs_bound_t* hnd, int k, int64_t* dst, int on_device);
 
@@ -188,6 +192,11 @@ typedef struct {
   uint64_t check_bytes;    /* algorithmic bytes of all checks: 8 per stored state */
 } lcs_bound_stats_t;
 lcs_status lcs_bound_stats(lcs_bound_t* hnd, lcs_bound_stats_t* out, int reset);
+
+/* Wait until every piece of work enqueued on the handle's stream has ended
+ * (for example before reading a device vector filled by lcs_bound_export with
+ * on_device = 1 from another stream).  Synchronous. */
+lcs_status lcs_bound_synchronize(lcs_bound_t* hnd);
 
 /* Free everything the handle owns (after the stream's pending work ends).
  * NULL is ignored. */

@@ -257,15 +257,16 @@ def splitmix64_at(seed: int, i: int) -> int:
 
 
 def F_generated(sigma: int, d: int, h: int, seeds, bases, spread: int, xs,
-                frac_bits: int = DEFAULT_FRAC_BITS, symmetric: bool = False) -> np.ndarray:
+                frac_bits: int = DEFAULT_FRAC_BITS, symmetric: int = 0) -> np.ndarray:
     """F (fx) at the states xs, argument k being bases[k-1] + (SplitMix64(seeds[k-1], c(y)) mod spread).
 
-    c(y) = y, or min(y, N-1-y) with ``symmetric``.
+    c(y) = y (symmetric = 0), min(y, N-1-y) (1), or the smallest index of y's
+    orbit under complement and string swap (2; sigma = d = 2).
     """
     seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
     bases = np.ascontiguousarray(bases, dtype=np.int64)
     xs = np.ascontiguousarray(xs, dtype=np.uint64)
     out = np.empty(xs.size, dtype=np.int64)
     _check(lib().orc_F_fx_generated(sigma, d, h, frac_bits, _ptr(seeds), _ptr(bases), int(spread),
-                                    1 if symmetric else 0, _ptr(xs), xs.size, _ptr(out)), "F_fx_generated")
+                                    int(symmetric), _ptr(xs), xs.size, _ptr(out)), "F_fx_generated")
     return out

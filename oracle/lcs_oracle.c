@@ -367,17 +367,35 @@ static uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
 
 uint64_t orc_splitmix64_at(uint64_t seed, uint64_t i) { return splitmix64_at(seed, i); }
 
+/* canonical index of y for generated inputs: symmetric = 0: y; 1: the smaller
+ * of y and its complement N-1-y; 2 (sigma = d = 2): the smallest of y, its
+ * complement, its swap (the two strings exchanged) and the swapped complement */
+static uint64_t canonical_index(const shape_t* s, uint64_t y, int symmetric) {
+  if (symmetric == 0) return y;
+  uint64_t c = s->n - 1 - y, best = y < c ? y : c;
+  if (symmetric == 2) {
+    uint64_t w = ((y >> 1) & 0x5555555555555555ull) | ((y & 0x5555555555555555ull) << 1);
+    uint64_t wc = s->n - 1 - w;
+    if (w < best) best = w;
+    if (wc < best) best = wc;
+  }
+  return best;
+}
+
 /* F (fx) at the states xs[0..m) with argument k (1-based) given by
- * base[k-1] + (splitmix64_at(seed[k-1], c(y)) mod spread), where c(y) = y, or
- * c(y) = min(y, N-1-y) when `symmetric` (inputs invariant under the
- * complement map of sigma = 2).  Each state is evaluated exactly as
- * F_state_fx does, reading through the generator. */
+ * base[k-1] + (splitmix64_at(seed[k-1], canonical_index(y)) mod spread), so
+ * that symmetric = 1 gives inputs invariant under the complement map of
+ * sigma = 2 and symmetric = 2 inputs also invariant under exchanging the two
+ * strings (sigma = d = 2).  Each state is evaluated exactly as F_state_fx
+ * does, reading through the generator. */
 int orc_F_fx_generated(int sigma, int d, int h, int frac_bits, const uint64_t* seed, const int64_t* base, uint64_t spread,
                        int symmetric, const uint64_t* xs, uint64_t m, int64_t* out) {
   shape_t s;
   int st = make_shape(sigma, d, h, &s);
   if (st) return st;
-  if (frac_bits < 0 || frac_bits > 60 || spread == 0) return ORC_EINVAL;
+  if (frac_bits < 0 || frac_bits > 60 || spread == 0 || symmetric < 0 || symmetric > 2) return ORC_EINVAL;
+  if (symmetric && sigma != 2) return ORC_EINVAL;
+  if (symmetric == 2 && d != 2) return ORC_EINVAL;
   int X[ORC_MAXD * ORC_MAXH], Y[ORC_MAXD * ORC_MAXH];
   int sets[ORC_MAXSETS][ORC_MAXD];
   int sizes[ORC_MAXSETS];
@@ -397,8 +415,7 @@ int orc_F_fx_generated(int sigma, int d, int h, int frac_bits, const uint64_t* s
       for (uint64_t cc = 0; cc < terms; ++cc) {
         tuple_of(s.sigma, k, cc, c);
         advance(&s, X, sets[q], k, c, Y);
-        uint64_t y = encode(&s, Y);
-        if (symmetric && s.n - 1 - y < y) y = s.n - 1 - y;
+        uint64_t y = canonical_index(&s, encode(&s, Y), symmetric);
         acc += base[k - 1] + (int64_t)(splitmix64_at(seed[k - 1], y) % spread);
       }
       __int128 mean = floor_div128(acc, (int64_t)terms);

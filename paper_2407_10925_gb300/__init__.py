@@ -22,6 +22,7 @@ from .binding import (  # noqa: F401
     lcs_bound_set_start_fx,
     lcs_bound_size,
     lcs_bound_stats,
+    lcs_bound_synchronize,
     lcs_sweep_fx,
     lcs_sweep_incr_fx_noalloc,
     lib,

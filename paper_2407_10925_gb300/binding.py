@@ -96,6 +96,7 @@ def lib():
                 "lcs_bound_export_fx": [vp, i32, vp, i32],
                 "lcs_bound_check_vector": [vp, vp, i64, P(i64)],
                 "lcs_bound_stats": [vp, P(lcs_bound_stats_t), i32],
+                "lcs_bound_synchronize": [vp],
                 "lcs_sweep_fx": [i32, i32, i32, i32, i32, vp, vp, vp],
                 "lcs_sweep_incr_fx_noalloc": [i32, i32, i32, i32, i32, vp, vp, vp, vp, vp],
             }
@@ -140,6 +141,10 @@ def _ptr_and_kind(a, dtype):
         want = torch.float64 if dtype == np.float64 else torch.int64
         if a.dtype != want or not a.is_contiguous():
             raise TypeError(f"tensor must be contiguous {want}")
+        if a.is_cuda:
+            # the library reads and writes on its own stream: let the work
+            # that produced (or still reads) this tensor on torch's stream end
+            torch.cuda.current_stream(a.device).synchronize()
         return a.data_ptr(), 1 if a.is_cuda else 0
     if not isinstance(a, np.ndarray) or a.dtype != dtype or not a.flags["C_CONTIGUOUS"]:
         raise TypeError(f"array must be a contiguous numpy {np.dtype(dtype)} array")
@@ -231,15 +236,23 @@ def lcs_bound_set_start_fx(hnd, vs):
     _check(lib().lcs_bound_set_start_fx(hnd, arr, on_dev), "lcs_bound_set_start_fx")
 
 
+def lcs_bound_synchronize(hnd):
+    _check(lib().lcs_bound_synchronize(hnd), "lcs_bound_synchronize")
+
+
 def lcs_bound_export(hnd, k: int, out):
     p, on_dev = _ptr_and_kind(out, np.float64)
     _check(lib().lcs_bound_export(hnd, k, p, on_dev), "lcs_bound_export")
+    if on_dev:
+        lcs_bound_synchronize(hnd)  # the tensor is complete when this returns
     return out
 
 
 def lcs_bound_export_fx(hnd, k: int, out):
     p, on_dev = _ptr_and_kind(out, np.int64)
     _check(lib().lcs_bound_export_fx(hnd, k, p, on_dev), "lcs_bound_export_fx")
+    if on_dev:
+        lcs_bound_synchronize(hnd)
     return out
 
 

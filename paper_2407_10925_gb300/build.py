@@ -24,6 +24,7 @@ SOURCES = [
     "kernels_s3.cu",
     "kernels_s4.cu",
     "noalloc.cu",
+    "kernels_s2d2.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -190,6 +190,19 @@ __global__ void maxabs_kernel(const long long* __restrict__ v, unsigned long lon
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&st->maxabs, m);
 }
 
+// sigma = d = 2: is v invariant under exchanging the two strings?  The swap
+// exchanges the two bits of every position in the interleaved index; a swapped
+// index in the upper half is read through the complement symmetry.
+__global__ void swap_check_kernel(const long long* __restrict__ v, unsigned long long n_stored,
+                                  unsigned long long n_total, DevState* st) {
+  for (unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_stored;
+       x += (unsigned long long)gridDim.x * blockDim.x) {
+    unsigned long long y = ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
+    if (y >= n_stored) y = n_total - 1 - y;
+    if (v[y] != v[x]) atomicExch((unsigned long long*)&st->swap_bad, 1ull);
+  }
+}
+
 __global__ void init_state_kernel(DevState* st) {
   if (threadIdx.x == 0 && blockIdx.x == 0) {
     DevState z{};
@@ -213,13 +226,15 @@ struct lcs_bound {
   cudaStream_t stream;
   bool own_stream;
   int device;
-  const KernelSet* ks;
+  const KernelSet* ks;       // kernels for the storage scheme (complement-symmetric or full)
+  const KernelSet* ks_swap;  // sigma = d = 2, h >= 6: kernels that also use the swap symmetry
+  bool swap_ok;              // the live iterates are swap-symmetric: ks_swap may run
   long long* ring[kMaxD + 1];
   int newest;  // ring slot of the newest iterate
   long long* ubuf;
   DevState* dstate;
   RedPartial* partials;
-  int grid_sweep, grid_check, n_partials;
+  int grid_sweep, grid_check, grid_sweep_swap, grid_check_swap, n_partials;
   void* staging;  // device staging for host transfers
   size_t staging_bytes;
   long long iters_done;
@@ -230,6 +245,7 @@ struct lcs_bound {
   double sweep_ms, check_ms;
   long long sweep_n, check_n, launches;
   unsigned long long sweep_bytes, check_bytes;
+  int last_check_grid;
 };
 
 static void* dev_alloc(lcs_bound* H, size_t bytes) {
@@ -301,6 +317,12 @@ const char* lcs_bound_errstr(lcs_status st) {
 
 const char* lcs_bound_last_error(void) { return g_last_error.c_str(); }
 
+lcs_status lcs_bound_synchronize(lcs_bound_t* H) {
+  if (!H) return fail(LCS_EINVAL, "handle is NULL");
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
+  return LCS_OK;
+}
+
 void lcs_bound_destroy(lcs_bound_t* H) {
   if (!H) return;
   if (H->stream) cudaStreamSynchronize(H->stream);
@@ -339,6 +361,7 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   const int sym = (sigma == 2 && opts.symmetry && h >= 2) ? 1 : 0;
   const KernelSet* ks = find_kernels(sigma, d, sym);
   if (!ks) return fail(LCS_EUNSUPPORTED, "no kernel compiled for sigma=%d d=%d", sigma, d);
+  const KernelSet* ks_swap = (sym && d == 2 && h >= 6) ? find_kernels(sigma, d, 2) : nullptr;
 
   lcs_bound* H = new (std::nothrow) lcs_bound();
   if (!H) return fail(LCS_ENOMEM, "host allocation");
@@ -353,6 +376,8 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   H->n_tail = n / sd;
   H->opts = opts;
   H->ks = ks;
+  H->ks_swap = ks_swap;
+  H->swap_ok = ks_swap != nullptr;  // the zero start is swap-symmetric
   H->one = 1ll << opts.frac_bits;
   H->newest = d - 1;
 
@@ -379,6 +404,13 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   H->grid_sweep = grid_for(ks->sweep_fn, sms, thread_items);
   H->grid_check = grid_for(ks->check_fn, sms, thread_items);
   H->n_partials = std::max(H->grid_sweep, H->grid_check);
+  if (ks_swap) {
+    // one CTA per 16 x 16 tile of orbit representatives
+    const unsigned long long tiles = 2ull * (1ull << (h - 6)) * (1ull << (h - 6));
+    H->grid_sweep_swap = grid_for(ks_swap->sweep_fn, sms, tiles * kBlock);
+    H->grid_check_swap = grid_for(ks_swap->check_fn, sms, tiles * kBlock);
+    H->n_partials = std::max(H->n_partials, std::max(H->grid_sweep_swap, H->grid_check_swap));
+  }
 
   const size_t vbytes = (size_t)H->n_stored * sizeof(long long);
   for (int k = 0; k <= d; ++k) {
@@ -468,7 +500,10 @@ static lcs_status timed_end(lcs_bound* H, cudaEvent_t a, bool sweep) {
 }
 
 static lcs_status run_check(lcs_bound* H, const long long* u, bool R_from_state, long long R, long long iter,
-                            bool finalize) {
+                            bool finalize, bool allow_swap) {
+  const bool use_swap = allow_swap && H->swap_ok && H->ks_swap;
+  const KernelSet* K = use_swap ? H->ks_swap : H->ks;
+  const int grid = use_swap ? H->grid_check_swap : H->grid_check;
   CheckParams c{};
   c.u = u;
   c.n_tail = H->n_tail;
@@ -482,15 +517,16 @@ static lcs_status run_check(lcs_bound* H, const long long* u, bool R_from_state,
   cudaEvent_t a = nullptr;
   lcs_status st = timed_begin(H, &a);
   if (st) return st;
-  H->ks->check(c, H->grid_check, H->stream);
+  K->check(c, grid, H->stream);
   LCS_CUDA(cudaGetLastError());
   st = timed_end(H, a, false);
   if (st) return st;
   H->check_n++;
-  H->check_bytes += 8ull * H->n_stored;
+  H->check_bytes += (unsigned long long)K->check_algo_bytes * H->n_stored;
   H->launches++;
+  H->last_check_grid = grid;
   if (finalize) {
-    finalize_check_kernel<<<1, kFinalBlock, 0, H->stream>>>(H->partials, H->grid_check, H->dstate, iter);
+    finalize_check_kernel<<<1, kFinalBlock, 0, H->stream>>>(H->partials, grid, H->dstate, iter);
     LCS_CUDA(cudaGetLastError());
     H->launches++;
   }
@@ -520,22 +556,24 @@ lcs_status lcs_bound_iterate(lcs_bound_t* H, int64_t n_iters) {
     p.r_mode = H->opts.r_mode;
     p.one = H->one;
     p.partials = H->partials;
+    const bool use_swap = H->swap_ok && H->ks_swap;
+    const KernelSet* K = use_swap ? H->ks_swap : H->ks;
+    const int grid = use_swap ? H->grid_sweep_swap : H->grid_sweep;
     cudaEvent_t a = nullptr;
     lcs_status st = timed_begin(H, &a);
     if (st) return st;
-    H->ks->sweep(p, H->grid_sweep, H->stream);
+    K->sweep(p, grid, H->stream);
     LCS_CUDA(cudaGetLastError());
     st = timed_end(H, a, true);
     if (st) return st;
     H->sweep_n++;
-    H->sweep_bytes += 8ull * (unsigned long long)(H->d + 1) * H->n_stored;
+    H->sweep_bytes += (unsigned long long)K->sweep_algo_bytes * H->n_stored;
     H->launches++;
     if (check) {
-      finalize_incr_kernel<<<1, kFinalBlock, 0, H->stream>>>(H->partials, H->grid_sweep, H->opts.r_mode, H->dstate,
-                                                              it);
+      finalize_incr_kernel<<<1, kFinalBlock, 0, H->stream>>>(H->partials, grid, H->opts.r_mode, H->dstate, it);
       LCS_CUDA(cudaGetLastError());
       H->launches++;
-      st = run_check(H, p.out, true, 0, it, true);
+      st = run_check(H, p.out, true, 0, it, true, true);
       if (st) return st;
       if (H->ubuf) {
         copy_if_kept_kernel<<<H->grid_sweep, kBlock, 0, H->stream>>>(p.out, H->ubuf, H->n_stored, H->dstate);
@@ -654,6 +692,11 @@ static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_d
     maxabs_kernel<<<grid, kBlock, 0, H->stream>>>(dst, H->n_stored, H->dstate);
     LCS_CUDA(cudaGetLastError());
     H->launches++;
+    if (H->ks_swap) {
+      swap_check_kernel<<<grid, kBlock, 0, H->stream>>>(dst, H->n_stored, H->n_total, H->dstate);
+      LCS_CUDA(cudaGetLastError());
+      H->launches++;
+    }
   }
   DevState s;
   LCS_CUDA(cudaMemcpyAsync(&s, H->dstate, sizeof s, cudaMemcpyDeviceToHost, H->stream));
@@ -669,6 +712,7 @@ static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_d
     return fail(LCS_EINVAL, "start vectors are not complement-symmetric (v[N-1-x] != v[x])");
   if (s.status == LCS_EOVERFLOW) return fail(LCS_EOVERFLOW, "start values outside the fixed-point range");
   H->vbound = (double)s.maxabs;
+  H->swap_ok = H->ks_swap != nullptr && s.swap_bad == 0;
   if (!headroom_ok(H, H->vbound)) return fail(LCS_EOVERFLOW, "start values too large for the fixed-point headroom");
   return LCS_OK;
 }
@@ -730,9 +774,9 @@ lcs_status lcs_bound_export_fx(lcs_bound_t* H, int k, int64_t* dst, int on_devic
 
 lcs_status lcs_bound_check_vector(lcs_bound_t* H, const int64_t* u_dev, int64_t R, int64_t* E_out) {
   if (!H || !u_dev || !E_out) return fail(LCS_EINVAL, "NULL argument");
-  lcs_status st = run_check(H, (const long long*)u_dev, false, R, 0, false);
+  lcs_status st = run_check(H, (const long long*)u_dev, false, R, 0, false, false);
   if (st) return st;
-  std::vector<RedPartial> parts((size_t)H->grid_check);
+  std::vector<RedPartial> parts((size_t)H->last_check_grid);
   LCS_CUDA(cudaMemcpyAsync(parts.data(), H->partials, sizeof(RedPartial) * parts.size(), cudaMemcpyDeviceToHost,
                            H->stream));
   LCS_CUDA(cudaStreamSynchronize(H->stream));

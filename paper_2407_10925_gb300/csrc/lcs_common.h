@@ -33,7 +33,8 @@ struct DevState {
   long long kept_flag;      // 1 if the last check kept its iterate
   long long maxabs;         // scratch of the max-|v| reduction
   long long status;         // sticky error status (lcs_status values)
-  long long pad[4];
+  long long swap_bad;       // set by the swap-symmetry check of start vectors
+  long long pad[3];
 };
 
 // Arguments of one sweep launch: v_out = F(prev[0], .., prev[d-1]).
@@ -65,12 +66,17 @@ struct CheckParams {
 // Host-visible description of the kernels compiled for one (sigma, d).
 struct KernelSet {
   int sigma, d;
-  int sym;                       // 1: complement-symmetric storage (sigma = 2 only)
+  int sym;                       // 0: full storage; 1: complement-symmetric storage (sigma = 2);
+                                 // 2: complement storage + swap-aware reads (sigma = d = 2)
   void (*sweep)(const SweepParams&, int grid, cudaStream_t);
   void (*check)(const CheckParams&, int grid, cudaStream_t);
   const void* sweep_fn;          // kernel symbols, for occupancy queries
   const void* check_fn;
   int tails_per_thread;          // tail tuples one thread handles per loop step
+  // algorithmic bytes per stored state: every output written once and every
+  // distinct input value the kernel's storage scheme needs read once
+  int sweep_algo_bytes;
+  int check_algo_bytes;
 };
 
 // Registry filled by the per-alphabet translation units.

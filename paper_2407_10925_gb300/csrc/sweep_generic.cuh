@@ -418,6 +418,8 @@ KernelSet make_generic_set() {
   k.sweep_fn = (const void*)&sweep_generic_kernel<SIG, D, SYM, true>;
   k.check_fn = (const void*)&check_generic_kernel<SIG, D, SYM>;
   k.tails_per_thread = SYM ? 2 : 1;
+  k.sweep_algo_bytes = 8 * (D + 1);
+  k.check_algo_bytes = 8;
   return k;
 }
 

@@ -23,7 +23,23 @@ def complement_index(n: int) -> np.ndarray:
     return np.arange(n - 1, -1, -1, dtype=np.int64)
 
 
-def random_fx(sigma, d, h, seed, base_units=200.0, spread_units=4.0, frac_bits=K_DEFAULT, symmetric=False):
+def swap_index(n: int) -> np.ndarray:
+    """The index with the two strings exchanged (sigma = d = 2, interleaved bits)."""
+    y = np.arange(n, dtype=np.int64)
+    return ((y >> 1) & 0x5555555555555555) | ((y & 0x5555555555555555) << 1)
+
+
+def symmetrize(v: np.ndarray, swap: bool = False) -> np.ndarray:
+    """The smallest value over each orbit of the complement map (and of the string swap)."""
+    n = v.size
+    out = np.minimum(v, v[complement_index(n)])
+    if swap:
+        out = np.minimum(out, out[swap_index(n)])
+    return out
+
+
+def random_fx(sigma, d, h, seed, base_units=200.0, spread_units=4.0, frac_bits=K_DEFAULT, symmetric=False,
+              swap=False):
     """One random fixed-point vector over all states."""
     rng = np.random.default_rng(seed)
     n = n_states(sigma, d, h)
@@ -31,23 +47,23 @@ def random_fx(sigma, d, h, seed, base_units=200.0, spread_units=4.0, frac_bits=K
     v = (base_units + spread_units * rng.random(n)) * one
     v = v.astype(np.int64)
     v += rng.integers(0, 1 << 20, size=n, dtype=np.int64)  # low-order noise below the unit
-    if symmetric:
-        if sigma != 2:
-            raise ValueError("complement symmetry needs sigma = 2")
-        v = np.minimum(v, v[complement_index(n)])
+    if symmetric or swap:
+        if sigma != 2 or (swap and d != 2):
+            raise ValueError("complement symmetry needs sigma = 2; the swap needs d = 2")
+        v = symmetrize(v, swap)
     return v
 
 
-def random_history(sigma, d, h, seed, step_units=0.4, frac_bits=K_DEFAULT, symmetric=False):
+def random_history(sigma, d, h, seed, step_units=0.4, frac_bits=K_DEFAULT, symmetric=False, swap=False):
     """d vectors shaped like consecutive iterates: v[k] is k steps older than v[0]."""
-    base = random_fx(sigma, d, h, seed, frac_bits=frac_bits, symmetric=symmetric)
+    base = random_fx(sigma, d, h, seed, frac_bits=frac_bits, symmetric=symmetric, swap=swap)
     one = 1 << frac_bits
     rng = np.random.default_rng(seed + 7919)
     n = base.size
     out = []
     for k in range(d):
         jitter = rng.integers(0, one // 16, size=n, dtype=np.int64)
-        if symmetric:
-            jitter = np.minimum(jitter, jitter[complement_index(n)])
+        if symmetric or swap:
+            jitter = symmetrize(jitter, swap)
         out.append(base - int(k * step_units * one) - jitter)
     return out

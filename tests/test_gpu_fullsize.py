@@ -42,15 +42,24 @@ def torch_mod():
 
 
 def splitmix_fill(torch, out, seed, base, start, symmetric, chunk=1 << 28):
-    """out[i] = base + (SplitMix64(seed, c(start + i)) mod 2^SPREAD_BITS), in int64 with wrap-around."""
+    """out[i] = base + (SplitMix64(seed, c(start + i)) mod 2^SPREAD_BITS), in int64 with wrap-around.
+
+    c(y) = y (symmetric 0), min(y, N-1-y) (1), or the smallest index of y's
+    orbit under complement and string swap (2).
+    """
     g = _as_i64(GOLD)
     m1, m2 = _as_i64(0xBF58476D1CE4E5B9), _as_i64(0x94D049BB133111EB)
+    ev = 0x5555555555555555
     n = out.numel()
     for off in range(0, n, chunk):
         m = min(chunk, n - off)
         y = torch.arange(start + off, start + off + m, dtype=torch.int64, device=out.device)
         if symmetric:
-            y = torch.minimum(y, (N - 1) - y)
+            c = torch.minimum(y, (N - 1) - y)
+            if symmetric == 2:
+                w = ((y >> 1) & ev) | ((y & ev) << 1)
+                c = torch.minimum(c, torch.minimum(w, (N - 1) - w))
+            y = c
         z = (y + 1) * g + seed
         z = (z ^ ((z >> 30) & ((1 << 34) - 1))) * m1
         z = (z ^ ((z >> 27) & ((1 << 37) - 1))) * m2
@@ -82,6 +91,7 @@ def test_h16_stateless_sweep_sampled(torch_mod, orc):
     v2 = torch.empty(N, dtype=torch.int64, device="cuda")
     splitmix_fill(torch, v1, SEEDS[0], BASES[0], 0, False)
     splitmix_fill(torch, v2, SEEDS[1], BASES[1], 0, False)
+    torch.cuda.synchronize()
     out = torch.empty(N, dtype=torch.int64, device="cuda")
     lb.lcs_sweep_fx(S, D, H, [v1, v2], out)
     torch.cuda.synchronize()
@@ -93,15 +103,22 @@ def test_h16_stateless_sweep_sampled(torch_mod, orc):
     assert np.array_equal(got, want), xs[got != want][:10]
 
 
-def test_h16_symmetric_iteration_sampled(torch_mod, orc):
-    """The library's complement-symmetric sweep with the fused increment reduction, at full size."""
+@pytest.mark.parametrize("symmetric", [1, 2], ids=["complement", "complement+swap"])
+def test_h16_symmetric_iteration_sampled(torch_mod, orc, symmetric):
+    """The library's symmetric sweeps with the fused increment reduction, at full size.
+
+    Complement-symmetric arguments run the complement kernel; arguments that are
+    also swap-symmetric run the kernel that uses both symmetries (the one the
+    benchmark's zero start runs).
+    """
     import paper_2407_10925_gb300 as lb
 
     torch = torch_mod
     newest = torch.empty(N, dtype=torch.int64, device="cuda")
     older = torch.empty(N, dtype=torch.int64, device="cuda")
-    splitmix_fill(torch, newest, SEEDS[0], BASES[0], 0, True)
-    splitmix_fill(torch, older, SEEDS[1], BASES[1], 0, True)
+    splitmix_fill(torch, newest, SEEDS[0], BASES[0], 0, symmetric)
+    splitmix_fill(torch, older, SEEDS[1], BASES[1], 0, symmetric)
+    torch.cuda.synchronize()  # the library reads them on its own stream
     with lb.LcsBound(S, D, H, symmetry=1) as hnd:
         hnd.set_start_fx([newest, older])
         del newest, older
@@ -116,9 +133,12 @@ def test_h16_symmetric_iteration_sampled(torch_mod, orc):
     got = out[torch.from_numpy(xs).cuda()].cpu().numpy()
     del out
     torch.cuda.empty_cache()
-    # the oracle reads the same symmetric generator: v(y) = v(min(y, N-1-y))
+    # the oracle reads the same symmetric generator
     canon = np.minimum(xs, N - 1 - xs)
-    want = orc.F_generated(S, D, H, SEEDS, BASES, 1 << SPREAD_BITS, xs.astype(np.uint64), symmetric=True)
+    if symmetric == 2:
+        w = ((xs >> 1) & 0x5555555555555555) | ((xs & 0x5555555555555555) << 1)
+        canon = np.minimum(canon, np.minimum(w, N - 1 - w))
+    want = orc.F_generated(S, D, H, SEEDS, BASES, 1 << SPREAD_BITS, xs.astype(np.uint64), symmetric=symmetric)
     assert np.array_equal(got, want)
     # R is attained at its state, and no sampled state has a smaller increment
     prev = np.array([BASES[0] + orc.splitmix64_at(SEEDS[0], int(c)) % (1 << SPREAD_BITS) for c in canon])

@@ -106,6 +106,23 @@ def test_warm_start_bit_exact(lb, orc, s, d, h, sym):
     _check_run_against_oracle(lb, orc, s, d, h, 17, 4, sym, 0, start=start)
 
 
+@pytest.mark.parametrize("h", [6, 7, 9])
+@pytest.mark.parametrize("swap", [False, True])
+def test_sigma2_d2_paths_bit_exact(lb, orc, h, swap):
+    """sigma = d = 2, h >= 6: swap-symmetric starts run the kernel that also uses the
+    string swap; complement-only starts fall back to the complement kernel.  Both exact."""
+    hist = inputs.random_history(2, 2, h, seed=40 + h, symmetric=True, swap=swap)
+    start = [hist[1], hist[0]]  # oldest first
+    _check_run_against_oracle(lb, orc, 2, 2, h, 23, 6, 1, 0, start=start)
+
+
+@pytest.mark.parametrize("h", [6, 8, 11])
+def test_swap_kernel_zero_start_many_checks(lb, orc, h):
+    """Zero start (swap-symmetric): every iteration checked, r_mode both ways."""
+    for r_mode in (0, 1):
+        _check_run_against_oracle(lb, orc, 2, 2, h, 12 if h > 8 else 30, 1, 1, r_mode)
+
+
 @pytest.mark.parametrize("s,d,h,sym", [(2, 2, 5, 1), (2, 2, 5, 0), (2, 3, 3, 1), (3, 2, 3, 0), (4, 2, 2, 0)])
 def test_check_vector_matches_oracle(lb, torch_mod, orc, s, d, h, sym):
     torch = torch_mod
@@ -227,4 +244,10 @@ def test_timing_stats(lb):
         st = hnd.stats()
         assert st["sweep_launches"] == 30 and st["check_launches"] == 3
         assert st["sweep_ms"] > 0 and st["check_ms"] > 0
-        assert st["sweep_bytes"] == 30 * 24 * (4 ** 6 // 2)
+        # at h >= 6 the zero start runs the kernel that also uses the string
+        # swap: 20 algorithmic bytes per stored state instead of 8 (d+1) = 24
+        assert st["sweep_bytes"] == 30 * 20 * (4 ** 6 // 2)
+        assert st["check_bytes"] == 3 * 8 * (4 ** 6 // 2)
+    with lb.LcsBound(2, 2, 5, timing=1) as hnd:
+        hnd.iterate(4)
+        assert hnd.stats()["sweep_bytes"] == 4 * 24 * (4 ** 5 // 2)
