@@ -32,7 +32,9 @@ import time
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+BATCH_SHAPES = [(2, 2, 10), (2, 2, 12), (3, 2, 6), (3, 2, 7), (4, 2, 5), (2, 3, 6), (2, 3, 7), (2, 4, 5)]
 CONFIGS = {
+    "batch": dict(sigma=0, d=0, h=0, shapes=BATCH_SHAPES),
     "h16": dict(sigma=2, d=2, h=16),
     "h14": dict(sigma=2, d=2, h=14),
     "h12": dict(sigma=2, d=2, h=12),
@@ -242,6 +244,72 @@ def workload_name(cfg, args):
             f"{args.check_every} sweeps + 1 check per step")
 
 
+def run_batch(args, cfg, world, rank, local_rank):
+    """Config 3: the eight instances in one persistent launch vs one after another."""
+    import torch
+
+    import paper_2407_10925_gb300 as lb
+
+    torch.cuda.set_device(local_rank)
+    shapes = cfg["shapes"]
+    n_states = [s ** (d * h) for s, d, h in shapes]
+    C = args.check_every
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    total_iters = 1000
+
+    # wall time to the rigorous bounds, batched: create (with autotuning) .. read
+    torch.cuda.synchronize()
+    t0_batch = time.perf_counter()
+    b = lb.LcsBatch(shapes, check_every=C, stream=stream.cuda_stream)
+    t_created = time.perf_counter()
+    b.iterate(total_iters)
+    bounds_batch = [b.read(i)[0] for i in range(len(shapes))]
+    t_batch = time.perf_counter() - t0_batch
+    info = b.info()
+
+    # the timed steady state: steps of C iterations after warm-up
+    for _ in range(args.warmup):
+        b.iterate(C)
+    torch.cuda.synchronize()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    with ClockSampler(local_rank) as clk:
+        torch.cuda.synchronize()
+        ev0.record(stream)
+        for _ in range(args.steps):
+            b.iterate(C)
+        ev1.record(stream)
+        torch.cuda.synchronize()
+    ms = reduce_max(ev0.elapsed_time(ev1), None)
+    b.close()
+
+    # the plain path: each instance alone through the single-instance API
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    bounds_plain = []
+    for s_, d_, h_ in shapes:
+        with lb.LcsBound(s_, d_, h_, check_every=C, stream=stream.cuda_stream) as one:
+            one.iterate(total_iters)
+            bounds_plain.append(one.read()[0])
+    t_plain = time.perf_counter() - t0
+    value = world * sum(n_states) * C * args.steps / (ms / 1e3)
+    line = {
+        "metric": METRIC, "value": value, "unit": "state-updates/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "config": {"workload": "8 instances (sigma,d,h) " + str(shapes) + f" in one persistent launch, "
+                   f"{C} iterations per step", "states": sum(n_states), "sweeps_per_step": C,
+                   "l2": "working set of the batch (about 0.6 GB) is larger than L2"},
+        "batch": {"time_to_bounds_s": t_batch, "create_and_tune_s": t_created - t0_batch,
+                  "plain_sequential_time_to_bounds_s": t_plain, "speedup_vs_plain": t_plain / t_batch,
+                  "iterations": total_iters, "bounds_equal_plain": bounds_batch == bounds_plain,
+                  "bounds": dict(zip([str(s) for s in shapes], bounds_batch)), "tuning": info},
+        "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     cfg = CONFIGS[args.config]
@@ -251,6 +319,9 @@ def main():
 
     if args.impl == "reference":
         run_reference(args, cfg, rank)
+        return
+    if args.config == "batch":
+        run_batch(args, cfg, world, rank, local_rank)
         return
 
     cpu = None

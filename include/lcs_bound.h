@@ -209,6 +209,84 @@ const char* lcs_bound_errstr(lcs_status st);
 const char* lcs_bound_last_error(void);
 
 /* ------------------------------------------------------------------------ */
+/* Batches: many small instances of uneven size in one persistent launch.
+ *
+ * lcs_bound_batch_create makes a handle for n instances (1 <= n <= 16),
+ * shapes[i] = {sigma, d, h} (each below 2^36 states; kernels exist for
+ * (2,2,h), (2,3,h), (2,4,h) with complement symmetry, (3,2,h), (4,2,h)).
+ * Every instance runs Algorithm 2 from the zero start; lcs_bound_iterate(hnd,
+ * n) advances all of them by n iterations in lockstep, in ONE cooperative
+ * persistent kernel launch that walks a work list of (instance, item) pairs
+ * and meets at a grid barrier between phases (sweep; on checked iterations
+ * the increment reduction, the check and the keep test).  The launch of each
+ * distinct n is captured once in a CUDA graph and replayed.  opts as for
+ * lcs_bound_create (keep_u unsupported).  At creation an autotuner times a few
+ * iterations for each candidate grid size and item size and keeps the
+ * fastest, then returns every vector to the zero start.
+ *
+ * The grid barrier waits with a clock budget (about 2 s by default); if it
+ * runs out the launch ends and the status LCS_ETIMEOUT is reported by the
+ * next read, instead of a hang.  lcs_bound_destroy and lcs_bound_synchronize
+ * apply; lcs_bound_read/export/set_start/check_vector return LCS_EINVAL on a
+ * batch handle: use the calls below, which take the instance index i. */
+lcs_status lcs_bound_batch_create(int n, const int (*shapes)[3], const lcs_bound_opts* opts, lcs_bound_t** out);
+lcs_status lcs_bound_batch_read(lcs_bound_t* hnd, int i, double* bound_rd, uint64_t* argmin_state, double* r,
+                                double* eps, int64_t* at_iter);
+lcs_status lcs_bound_batch_report(lcs_bound_t* hnd, int i, lcs_bound_report* out);
+/* the newest iterate (k = 0) or an older one (k < d) of instance i, every state, fixed point */
+lcs_status lcs_bound_batch_export_fx(lcs_bound_t* hnd, int i, int k, int64_t* dst, int on_device);
+
+typedef struct {
+  int n_instances;
+  int grid;               /* CTAs of the persistent launch chosen by the autotuner */
+  int units_per_item;     /* tiles per work item chosen by the autotuner */
+  int graph;              /* 1: launches replay a captured CUDA graph */
+  double tuned_ms_per_iter;
+  int64_t launches;       /* persistent launches or graph replays so far */
+} lcs_bound_batch_info_t;
+lcs_status lcs_bound_batch_info(lcs_bound_t* hnd, lcs_bound_batch_info_t* out);
+
+/* Set the grid barrier's clock budget in cycles (testing the timeout path);
+ * also clears a previous LCS_ETIMEOUT status. */
+lcs_status lcs_bound_batch_set_spin_budget(lcs_bound_t* hnd, int64_t cycles);
+
+/* ------------------------------------------------------------------------ */
+/* Learned warm start (sigma = d = 2).  Not part of the paper's method, whose
+ * iteration starts from the zero vector; Lemma 1 makes any start legitimate
+ * because the bound comes only from a triplet whose feasibility the check
+ * verifies, so a warm start changes the work, never the rigor.
+ *
+ * A 3-layer MLP (49 -> 256 -> 256 -> 1, GELU, FP32 weights on the device)
+ * predicts the relative value v[x] - v[0] of a converged iterate.  Inputs: a
+ * one-hot of the letters at the first 12 positions of each string (zero
+ * beyond h) and h / 16, computed from the smallest index of the state's orbit
+ * under complement and string swap (so predictions are symmetric).  Parameters
+ * are a flat float array of lcs_mlp_param_count() values: W1 (256 x 49), b1,
+ * W2 (256 x 256, out x in), b2, w3, b3.  Handles are not thread-safe. */
+typedef struct lcs_mlp lcs_mlp_t;
+int64_t lcs_mlp_param_count(void);
+/* random initialisation (uniform +-1/sqrt(fan-in), SplitMix64 stream `seed`) */
+lcs_status lcs_mlp_create(uint64_t seed, lcs_mlp_t** out);
+lcs_status lcs_mlp_get_params(lcs_mlp_t* m, float* host_out);
+lcs_status lcs_mlp_set_params(lcs_mlp_t* m, const float* host_in);
+/* mean squared error over n host rows (states, their h, targets) and its
+ * gradient (host, lcs_mlp_param_count() floats) -- the forward and backward
+ * kernels the training uses, for checking them.  Synchronous. */
+lcs_status lcs_mlp_gradient(lcs_mlp_t* m, int n, const int64_t* states, const int* hs, const float* targets,
+                            float* loss_out, float* grad_out);
+/* Adam steps on batches drawn from converged iterates: vectors[i] is a
+ * full-length fixed-point device vector (units of 2^-frac_bits) of the shape
+ * (2, 2, hs[i]); targets are v[x] - v[0] in units.  Synchronous. */
+lcs_status lcs_mlp_train(lcs_mlp_t* m, int n_sets, const int64_t* const* vectors, const int* hs, int64_t steps,
+                         int batch, float lr, uint64_t seed, int frac_bits, float* last_loss);
+/* predictions (units) for n device states of length h into out_dev (device) */
+lcs_status lcs_mlp_predict(lcs_mlp_t* m, int h, int64_t n, const int64_t* states_dev, float* out_dev);
+/* a start for lcs_bound_set_start (device doubles, 4^h values each):
+ * older = u_hat, newest = u_hat + r_hat.  Synchronous. */
+lcs_status lcs_mlp_start_vectors(lcs_mlp_t* m, int h, double r_hat, double* newest_dev, double* older_dev);
+void lcs_mlp_destroy(lcs_mlp_t* m);
+
+/* ------------------------------------------------------------------------ */
 /* Stateless entry point.
  *
  * One evaluation of F (Eq. ineq3; Algorithm 2's first line in the loop):

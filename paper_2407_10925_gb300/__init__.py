@@ -5,8 +5,16 @@ The product is the CUDA library built from ``csrc/`` behind the C ABI in
 ``include/lcs_bound.h``; ``binding`` is its thin ctypes binding.
 """
 from .binding import (  # noqa: F401
+    LcsBatch,
     LcsBound,
     LcsError,
+    LcsMlp,
+    lcs_bound_batch_create,
+    lcs_bound_batch_export_fx,
+    lcs_bound_batch_info,
+    lcs_bound_batch_read,
+    lcs_bound_batch_report,
+    lcs_bound_batch_set_spin_budget,
     lcs_bound_check_vector,
     lcs_bound_create,
     lcs_bound_default_opts,

@@ -65,6 +65,17 @@ class lcs_bound_stats_t(ctypes.Structure):
     ]
 
 
+class lcs_bound_batch_info_t(ctypes.Structure):
+    _fields_ = [
+        ("n_instances", ctypes.c_int),
+        ("grid", ctypes.c_int),
+        ("units_per_item", ctypes.c_int),
+        ("graph", ctypes.c_int),
+        ("tuned_ms_per_iter", ctypes.c_double),
+        ("launches", ctypes.c_int64),
+    ]
+
+
 class LcsError(RuntimeError):
     def __init__(self, status, message):
         super().__init__(f"{message} (status {status})")
@@ -97,6 +108,19 @@ def lib():
                 "lcs_bound_check_vector": [vp, vp, i64, P(i64)],
                 "lcs_bound_stats": [vp, P(lcs_bound_stats_t), i32],
                 "lcs_bound_synchronize": [vp],
+                "lcs_bound_batch_create": [i32, vp, P(lcs_bound_opts), P(vp)],
+                "lcs_bound_batch_read": [vp, i32, P(dbl), P(u64), P(dbl), P(dbl), P(i64)],
+                "lcs_bound_batch_report": [vp, i32, P(lcs_bound_report)],
+                "lcs_bound_batch_export_fx": [vp, i32, i32, vp, i32],
+                "lcs_bound_batch_info": [vp, P(lcs_bound_batch_info_t)],
+                "lcs_bound_batch_set_spin_budget": [vp, i64],
+                "lcs_mlp_create": [u64, P(vp)],
+                "lcs_mlp_get_params": [vp, vp],
+                "lcs_mlp_set_params": [vp, vp],
+                "lcs_mlp_gradient": [vp, i32, vp, vp, vp, P(ctypes.c_float), vp],
+                "lcs_mlp_train": [vp, i32, vp, vp, i64, i32, ctypes.c_float, u64, i32, P(ctypes.c_float)],
+                "lcs_mlp_predict": [vp, i32, i64, vp, vp],
+                "lcs_mlp_start_vectors": [vp, i32, dbl, vp, vp],
                 "lcs_sweep_fx": [i32, i32, i32, i32, i32, vp, vp, vp],
                 "lcs_sweep_incr_fx_noalloc": [i32, i32, i32, i32, i32, vp, vp, vp, vp, vp],
             }
@@ -104,6 +128,10 @@ def lib():
                 fn = getattr(L, name)
                 fn.argtypes = args
                 fn.restype = ctypes.c_int
+            L.lcs_mlp_param_count.argtypes = []
+            L.lcs_mlp_param_count.restype = i64
+            L.lcs_mlp_destroy.argtypes = [vp]
+            L.lcs_mlp_destroy.restype = None
             L.lcs_bound_destroy.argtypes = [vp]
             L.lcs_bound_destroy.restype = None
             L.lcs_bound_errstr.argtypes = [ctypes.c_int]
@@ -300,6 +328,173 @@ def lcs_sweep_incr_fx_noalloc(sigma, d, h, v_prev, v_out, R_out, argmin_out, fra
         raise TypeError("lcs_sweep_incr_fx_noalloc takes CUDA tensors")
     _check(lib().lcs_sweep_incr_fx_noalloc(sigma, d, h, frac_bits, r_mode, arr, po, pr, pa, stream),
            "lcs_sweep_incr_fx_noalloc")
+
+
+def lcs_bound_batch_create(shapes, opts: lcs_bound_opts | None = None):
+    arr = (ctypes.c_int * (3 * len(shapes)))(*[int(v) for sh in shapes for v in sh])
+    hnd = ctypes.c_void_p()
+    _check(lib().lcs_bound_batch_create(len(shapes), arr, ctypes.byref(opts) if opts is not None else None,
+                                        ctypes.byref(hnd)), "lcs_bound_batch_create")
+    return hnd
+
+
+def lcs_bound_batch_read(hnd, i: int):
+    b, a, r, e, it = ctypes.c_double(), ctypes.c_uint64(), ctypes.c_double(), ctypes.c_double(), ctypes.c_int64()
+    _check(lib().lcs_bound_batch_read(hnd, i, ctypes.byref(b), ctypes.byref(a), ctypes.byref(r), ctypes.byref(e),
+                                      ctypes.byref(it)), "lcs_bound_batch_read")
+    return b.value, a.value, r.value, e.value, it.value
+
+
+def lcs_bound_batch_report(hnd, i: int) -> dict:
+    rep = lcs_bound_report()
+    _check(lib().lcs_bound_batch_report(hnd, i, ctypes.byref(rep)), "lcs_bound_batch_report")
+    return {f: getattr(rep, f) for f, _ in lcs_bound_report._fields_}
+
+
+def lcs_bound_batch_export_fx(hnd, i: int, k: int, out):
+    p, on_dev = _ptr_and_kind(out, np.int64)
+    _check(lib().lcs_bound_batch_export_fx(hnd, i, k, p, on_dev), "lcs_bound_batch_export_fx")
+    if on_dev:
+        lcs_bound_synchronize(hnd)
+    return out
+
+
+def lcs_bound_batch_info(hnd) -> dict:
+    info = lcs_bound_batch_info_t()
+    _check(lib().lcs_bound_batch_info(hnd, ctypes.byref(info)), "lcs_bound_batch_info")
+    return {f: getattr(info, f) for f, _ in lcs_bound_batch_info_t._fields_}
+
+
+def lcs_bound_batch_set_spin_budget(hnd, cycles: int):
+    _check(lib().lcs_bound_batch_set_spin_budget(hnd, int(cycles)), "lcs_bound_batch_set_spin_budget")
+
+
+class LcsBatch:
+    """Owns one batch handle (lcs_bound_batch_create); instances are indexed 0..n-1."""
+
+    def __init__(self, shapes, *, check_every=0, r_mode=0, frac_bits=44, symmetry=1, stream=None):
+        self.shapes = [tuple(s) for s in shapes]
+        o = lcs_bound_default_opts()
+        o.check_every, o.r_mode, o.frac_bits, o.symmetry = check_every, r_mode, frac_bits, symmetry
+        if stream is not None:
+            if not stream:
+                raise ValueError("stream 0 means 'library-owned stream'; pass a non-default stream handle")
+            o.stream = stream
+        self.hnd = lcs_bound_batch_create(self.shapes, o)
+
+    def close(self):
+        if self.hnd:
+            lcs_bound_destroy(self.hnd)
+            self.hnd = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def iterate(self, n):
+        lcs_bound_iterate(self.hnd, n)
+
+    def read(self, i):
+        return lcs_bound_batch_read(self.hnd, i)
+
+    def report(self, i):
+        return lcs_bound_batch_report(self.hnd, i)
+
+    def export_fx(self, i, k=0, out=None):
+        s, d, h = self.shapes[i]
+        if out is None:
+            out = np.empty(s ** (d * h), dtype=np.int64)
+        return lcs_bound_batch_export_fx(self.hnd, i, k, out)
+
+    def info(self):
+        return lcs_bound_batch_info(self.hnd)
+
+    def set_spin_budget(self, cycles):
+        lcs_bound_batch_set_spin_budget(self.hnd, cycles)
+
+
+def lcs_mlp_param_count() -> int:
+    return int(lib().lcs_mlp_param_count())
+
+
+class LcsMlp:
+    """The warm-start network (lcs_mlp_*); every computation runs in the library's kernels."""
+
+    def __init__(self, seed=1):
+        self.hnd = ctypes.c_void_p()
+        _check(lib().lcs_mlp_create(seed, ctypes.byref(self.hnd)), "lcs_mlp_create")
+        self.n_params = lcs_mlp_param_count()
+
+    def close(self):
+        if self.hnd:
+            lib().lcs_mlp_destroy(self.hnd)
+            self.hnd = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def get_params(self):
+        out = np.empty(self.n_params, dtype=np.float32)
+        _check(lib().lcs_mlp_get_params(self.hnd, out.ctypes.data), "lcs_mlp_get_params")
+        return out
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        _check(lib().lcs_mlp_set_params(self.hnd, flat.ctypes.data), "lcs_mlp_set_params")
+
+    def gradient(self, states, hs, targets):
+        states = np.ascontiguousarray(states, dtype=np.int64)
+        hs = np.ascontiguousarray(hs, dtype=np.int32)
+        targets = np.ascontiguousarray(targets, dtype=np.float32)
+        g = np.empty(self.n_params, dtype=np.float32)
+        loss = ctypes.c_float()
+        _check(lib().lcs_mlp_gradient(self.hnd, states.size, states.ctypes.data, hs.ctypes.data, targets.ctypes.data,
+                                      ctypes.byref(loss), g.ctypes.data), "lcs_mlp_gradient")
+        return loss.value, g
+
+    def train(self, vectors, hs, steps, batch=4096, lr=1e-3, seed=7, frac_bits=44):
+        arr, on_dev = _vec_array(vectors, np.int64)
+        if not on_dev:
+            raise TypeError("training vectors must be CUDA tensors")
+        hs_arr = (ctypes.c_int * len(hs))(*hs)
+        loss = ctypes.c_float()
+        _check(lib().lcs_mlp_train(self.hnd, len(hs), arr, hs_arr, steps, batch, lr, seed, frac_bits,
+                                   ctypes.byref(loss)), "lcs_mlp_train")
+        return loss.value
+
+    def predict(self, h, states_dev, out_dev):
+        ps, sd = _ptr_and_kind(states_dev, np.int64)
+        if not sd or not out_dev.is_cuda:
+            raise TypeError("predict takes CUDA tensors")
+        import torch
+
+        torch.cuda.current_stream().synchronize()
+        _check(lib().lcs_mlp_predict(self.hnd, h, states_dev.numel(), ps, out_dev.data_ptr()), "lcs_mlp_predict")
+        return out_dev
+
+    def start_vectors(self, h, r_hat, newest_dev, older_dev):
+        pn, dn = _ptr_and_kind(newest_dev, np.float64)
+        po, do = _ptr_and_kind(older_dev, np.float64)
+        if not (dn and do):
+            raise TypeError("start vectors must be CUDA tensors")
+        _check(lib().lcs_mlp_start_vectors(self.hnd, h, float(r_hat), pn, po), "lcs_mlp_start_vectors")
 
 
 # ---------------------------------------------------------------------------

@@ -25,6 +25,8 @@ SOURCES = [
     "kernels_s4.cu",
     "noalloc.cu",
     "kernels_s2d2.cu",
+    "batch.cu",
+    "mlp.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

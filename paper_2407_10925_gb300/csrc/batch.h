@@ -1,0 +1,28 @@
+// batch.h -- internal interface between the handle (lcs_bound.cu) and the
+// batched persistent launch (batch.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "../../include/lcs_bound.h"
+#include "lcs_common.h"
+
+namespace lcs {
+
+constexpr int kMaxBatch = 16;
+
+struct BatchState;
+
+lcs_status batch_create(int n, const int (*shapes)[3], const lcs_bound_opts& o, cudaStream_t s, BatchState** out);
+lcs_status batch_iterate(BatchState* B, cudaStream_t s, long long n_iters);
+lcs_status batch_report(BatchState* B, cudaStream_t s, int i, lcs_bound_report* out);
+const long long* batch_vector(BatchState* B, cudaStream_t s, int i, int k, unsigned long long* n_stored,
+                              unsigned long long* n_total, lcs_status* err);
+lcs_status batch_set_spin_budget(BatchState* B, cudaStream_t s, long long cycles);
+lcs_status batch_clear_status(BatchState* B, cudaStream_t s);
+void batch_tuning(const BatchState* B, int* grid, int* units, double* ms, long long* launches, int* graph);
+int batch_size(const BatchState* B);
+int batch_d(const BatchState* B, int i);
+void batch_destroy(BatchState* B);
+
+}  // namespace lcs

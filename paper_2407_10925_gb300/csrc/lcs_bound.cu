@@ -19,6 +19,7 @@
 #include <vector>
 
 #include "../../include/lcs_bound.h"
+#include "batch.h"
 #include "lcs_common.h"
 
 namespace lcs {
@@ -240,12 +241,14 @@ struct lcs_bound {
   long long iters_done;
   double vbound;  // upper bound of max |v| over the live iterates, in units of 2^-K
   long long one;
+  BatchState* batch;  // non-null: a batch of instances (lcs_bound_batch_create)
   // timing
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sweep_ev, check_ev;
   double sweep_ms, check_ms;
   long long sweep_n, check_n, launches;
   unsigned long long sweep_bytes, check_bytes;
   int last_check_grid;
+  int d_batch_worst;  // batch handles: d of the instance with the largest sigma^d
 };
 
 static void* dev_alloc(lcs_bound* H, size_t bytes) {
@@ -282,7 +285,7 @@ static int grid_for(const void* fn, int sms, unsigned long long work_items) {
 // headroom: every intermediate of a sweep or check is at most sigma^d times the
 // largest |value| (plus lower-order terms); keep it below 2^62
 static bool headroom_ok(const lcs_bound* H, double vb) {
-  const double sd = std::pow((double)H->sigma, (double)H->d);
+  const double sd = std::pow((double)H->sigma, (double)(H->batch ? H->d_batch_worst : H->d));
   return sd * (vb + 4.0 * (double)H->one) * 2.0 < 4.6e18;
 }
 
@@ -328,6 +331,7 @@ void lcs_bound_destroy(lcs_bound_t* H) {
   if (H->stream) cudaStreamSynchronize(H->stream);
   for (auto& e : H->sweep_ev) cudaEventDestroy(e.first), cudaEventDestroy(e.second);
   for (auto& e : H->check_ev) cudaEventDestroy(e.first), cudaEventDestroy(e.second);
+  if (H->batch) batch_destroy(H->batch);
   for (int k = 0; k <= H->d; ++k) dev_free(H, H->ring[k]);
   dev_free(H, H->ubuf);
   dev_free(H, H->dstate);
@@ -537,6 +541,15 @@ lcs_status lcs_bound_iterate(lcs_bound_t* H, int64_t n_iters) {
   if (!H) return fail(LCS_EINVAL, "handle is NULL");
   if (n_iters < 0) return fail(LCS_EINVAL, "n_iters < 0");
   if (n_iters == 0) return LCS_OK;
+  if (H->batch) {
+    const double vb_after = H->vbound + (double)n_iters * (double)H->one;
+    if (!headroom_ok(H, vb_after)) return fail(LCS_EOVERFLOW, "iterates could exceed the fixed-point range");
+    lcs_status st = batch_iterate(H->batch, H->stream, n_iters);
+    if (st) return st;
+    H->vbound = vb_after;
+    H->iters_done += n_iters;
+    return LCS_OK;
+  }
   const double vb_after = H->vbound + (double)n_iters * (double)H->one;
   if (!headroom_ok(H, vb_after))
     return fail(LCS_EOVERFLOW, "iterates could exceed the fixed-point range (max |v| up to %.3g)",
@@ -590,6 +603,7 @@ lcs_status lcs_bound_iterate(lcs_bound_t* H, int64_t n_iters) {
 
 lcs_status lcs_bound_read_report(lcs_bound_t* H, lcs_bound_report* out) {
   if (!H || !out) return fail(LCS_EINVAL, "NULL argument");
+  if (H->batch) return fail(LCS_EINVAL, "a batch handle: use the lcs_bound_batch_* calls");
   DevState s;
   LCS_CUDA(cudaMemcpyAsync(&s, H->dstate, sizeof s, cudaMemcpyDeviceToHost, H->stream));
   LCS_CUDA(cudaStreamSynchronize(H->stream));
@@ -669,6 +683,7 @@ static lcs_status ingest_range(lcs_bound* H, const void* src, unsigned long long
 
 static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_device, bool from_double) {
   if (!H) return fail(LCS_EINVAL, "handle is NULL");
+  if (H->batch) return fail(LCS_EINVAL, "a batch handle: use the lcs_bound_batch_* calls");
   if (!v) return fail(LCS_EINVAL, "NULL argument");
   const double scale = std::ldexp(1.0, H->opts.frac_bits);
   LCS_CUDA(cudaMemsetAsync(H->dstate, 0, sizeof(DevState), H->stream));
@@ -727,6 +742,7 @@ lcs_status lcs_bound_set_start_fx(lcs_bound_t* H, const int64_t* const* v, int o
 
 static lcs_status export_impl(lcs_bound* H, int k, void* dst, int on_device, bool to_double) {
   if (!H || !dst) return fail(LCS_EINVAL, "NULL argument");
+  if (H->batch) return fail(LCS_EINVAL, "a batch handle: use the lcs_bound_batch_* calls");
   if (k < -1 || k >= H->d) return fail(LCS_EINVAL, "k=%d outside -1..d-1", k);
   const long long* src;
   if (k == -1) {
@@ -774,6 +790,7 @@ lcs_status lcs_bound_export_fx(lcs_bound_t* H, int k, int64_t* dst, int on_devic
 
 lcs_status lcs_bound_check_vector(lcs_bound_t* H, const int64_t* u_dev, int64_t R, int64_t* E_out) {
   if (!H || !u_dev || !E_out) return fail(LCS_EINVAL, "NULL argument");
+  if (H->batch) return fail(LCS_EINVAL, "a batch handle: use the lcs_bound_batch_* calls");
   lcs_status st = run_check(H, (const long long*)u_dev, false, R, 0, false, false);
   if (st) return st;
   std::vector<RedPartial> parts((size_t)H->last_check_grid);
@@ -803,6 +820,122 @@ lcs_status lcs_bound_stats(lcs_bound_t* H, lcs_bound_stats_t* out, int reset) {
     H->sweep_bytes = H->check_bytes = 0;
   }
   return LCS_OK;
+}
+
+lcs_status lcs_bound_batch_create(int n, const int (*shapes)[3], const lcs_bound_opts* opts_in, lcs_bound_t** out) {
+  if (!out || !shapes) return fail(LCS_EINVAL, "NULL argument");
+  *out = nullptr;
+  lcs_bound_opts opts;
+  if (opts_in)
+    opts = *opts_in;
+  else
+    lcs_bound_default_opts(&opts);
+  if (opts.frac_bits == 0) opts.frac_bits = 44;
+  if (opts.frac_bits < 8 || opts.frac_bits > 56) return fail(LCS_EINVAL, "frac_bits %d outside 8..56", opts.frac_bits);
+  if (opts.r_mode != 0 && opts.r_mode != 1) return fail(LCS_EINVAL, "r_mode %d", opts.r_mode);
+  if (opts.check_every < 0) return fail(LCS_EINVAL, "check_every %d", opts.check_every);
+  if (opts.f_mode != 0) return fail(LCS_EUNSUPPORTED, "f_mode %d has no GPU kernel", opts.f_mode);
+  if (opts.alloc && !opts.free) return fail(LCS_EINVAL, "alloc given without free");
+  lcs_bound* H = new (std::nothrow) lcs_bound();
+  if (!H) return fail(LCS_ENOMEM, "host allocation");
+  H->opts = opts;
+  H->one = 1ll << opts.frac_bits;
+  H->d = 0;  // the handle owns no ring of its own
+  cudaError_t e = cudaGetDevice(&H->device);
+  if (e == cudaSuccess) {
+    if (opts.stream) {
+      H->stream = (cudaStream_t)opts.stream;
+    } else {
+      e = cudaStreamCreateWithFlags(&H->stream, cudaStreamNonBlocking);
+      H->own_stream = e == cudaSuccess;
+    }
+  }
+  if (e != cudaSuccess) {
+    lcs_bound_destroy(H);
+    return fail(LCS_ECUDA, "batch stream: %s", cudaGetErrorString(e));
+  }
+  // headroom is checked against the largest sigma^d of the batch
+  int worst_sigma = 2, worst_d = 2;
+  double worst = 0;
+  for (int i = 0; i < n && i < kMaxBatch; ++i) {
+    const double sd = std::pow((double)shapes[i][0], (double)shapes[i][1]);
+    if (sd > worst) worst = sd, worst_sigma = shapes[i][0], worst_d = shapes[i][1];
+  }
+  H->sigma = worst_sigma;
+  H->d_batch_worst = worst_d;
+  lcs_status st = batch_create(n, shapes, opts, H->stream, &H->batch);
+  if (st) {
+    lcs_bound_destroy(H);
+    return st;
+  }
+  *out = H;
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_batch_report(lcs_bound_t* H, int i, lcs_bound_report* out) {
+  if (!H || !out) return fail(LCS_EINVAL, "NULL argument");
+  if (!H->batch) return fail(LCS_EINVAL, "not a batch handle");
+  return batch_report(H->batch, H->stream, i, out);
+}
+
+lcs_status lcs_bound_batch_read(lcs_bound_t* H, int i, double* bound_rd, uint64_t* argmin_state, double* r,
+                                double* eps, int64_t* at_iter) {
+  lcs_bound_report rep;
+  lcs_status st = lcs_bound_batch_report(H, i, &rep);
+  if (st) return st;
+  if (rep.status) return fail((lcs_status)rep.status, "device status %d", rep.status);
+  if (!rep.have_check) return fail(LCS_ENOBOUND, "no feasibility check has run");
+  const int K = H->opts.frac_bits;
+  const long long B = (long long)batch_d(H->batch, i) * (rep.r - rep.eps);
+  if (bound_rd) *bound_rd = fx_to_double_rd(B, K);
+  if (argmin_state) *argmin_state = rep.argmin;
+  if (r) *r = std::ldexp((double)rep.r, -K);
+  if (eps) *eps = std::ldexp((double)rep.eps, -K);
+  if (at_iter) *at_iter = rep.kept_iter;
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_batch_export_fx(lcs_bound_t* H, int i, int k, int64_t* dst, int on_device) {
+  if (!H || !dst) return fail(LCS_EINVAL, "NULL argument");
+  if (!H->batch) return fail(LCS_EINVAL, "not a batch handle");
+  unsigned long long n_stored = 0, n_total = 0;
+  lcs_status st = LCS_OK;
+  const long long* src = batch_vector(H->batch, H->stream, i, k, &n_stored, &n_total, &st);
+  if (!src) return st;
+  if (on_device) {
+    const int grid = (int)std::min<unsigned long long>(4096, (n_total + kBlock - 1) / kBlock);
+    export_kernel<false><<<grid, kBlock, 0, H->stream>>>(src, 0, n_total, n_stored, n_total, 1.0, dst);
+    LCS_CUDA(cudaGetLastError());
+    return LCS_OK;
+  }
+  st = ensure_staging(H, kChunk * 8);
+  if (st) return st;
+  for (unsigned long long off = 0; off < n_total; off += kChunk) {
+    const unsigned long long len = std::min<unsigned long long>(kChunk, n_total - off);
+    const int grid = (int)std::min<unsigned long long>(4096, (len + kBlock - 1) / kBlock);
+    export_kernel<false><<<grid, kBlock, 0, H->stream>>>(src, off, len, n_stored, n_total, 1.0, H->staging);
+    LCS_CUDA(cudaGetLastError());
+    LCS_CUDA(cudaMemcpyAsync((char*)dst + off * 8, H->staging, len * 8, cudaMemcpyDeviceToHost, H->stream));
+  }
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_batch_info(lcs_bound_t* H, lcs_bound_batch_info_t* out) {
+  if (!H || !out) return fail(LCS_EINVAL, "NULL argument");
+  if (!H->batch) return fail(LCS_EINVAL, "not a batch handle");
+  long long launches = 0;
+  batch_tuning(H->batch, &out->grid, &out->units_per_item, &out->tuned_ms_per_iter, &launches, &out->graph);
+  out->launches = launches;
+  out->n_instances = batch_size(H->batch);
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_batch_set_spin_budget(lcs_bound_t* H, int64_t cycles) {
+  if (!H) return fail(LCS_EINVAL, "NULL argument");
+  if (!H->batch) return fail(LCS_EINVAL, "not a batch handle");
+  if (cycles < 0) return fail(LCS_EINVAL, "negative budget");
+  return batch_set_spin_budget(H->batch, H->stream, cycles);
 }
 
 lcs_status lcs_sweep_fx(int sigma, int d, int h, int f_mode, int frac_bits, const int64_t* const* v_prev,

@@ -59,6 +59,17 @@ __device__ __forceinline__ long long floor_div(long long a) {
   }
 }
 
+// Loads of iterate vectors.  Standalone launches read vectors that no thread
+// of the launch writes: the read-only path.  A persistent launch that runs
+// several iterations reads what other CTAs wrote earlier in the same launch:
+// L2-coherent loads that bypass L1 (CG = true).
+template <bool CG = false>
+__device__ __forceinline__ long long ld_vec(const long long* p) {
+  if constexpr (CG)
+    return __ldcg(p);
+  else
+    return __ldg(p);
+}
 __device__ __forceinline__ long long ld_stream(const long long* p) { return __ldg(p); }
 
 // ---------------------------------------------------------------------------
@@ -72,7 +83,7 @@ __device__ __forceinline__ bool red_better(long long v, unsigned long long x, lo
   return x < bx;
 }
 
-__device__ __forceinline__ void block_reduce_arg(long long& v, unsigned long long& x, int r_mode, RedPartial* out) {
+__device__ __forceinline__ void block_reduce_arg_to(long long& v, unsigned long long& x, int r_mode, RedPartial* slot) {
   __shared__ long long sv[kBlock / 32];
   __shared__ unsigned long long sx[kBlock / 32];
 #pragma unroll
@@ -94,11 +105,16 @@ __device__ __forceinline__ void block_reduce_arg(long long& v, unsigned long lon
       unsigned long long ox = __shfl_xor_sync(0xffffffffu, x, o);
       if (red_better(ov, ox, v, x, r_mode)) v = ov, x = ox;
     }
-    if (l == 0) out[blockIdx.x] = RedPartial{v, x};
+    if (l == 0) *slot = RedPartial{v, x};
   }
+  __syncthreads();  // the shared scratch may be reused by a following reduction
 }
 
-__device__ __forceinline__ void block_reduce_max(long long v, RedPartial* out) {
+__device__ __forceinline__ void block_reduce_arg(long long& v, unsigned long long& x, int r_mode, RedPartial* out) {
+  block_reduce_arg_to(v, x, r_mode, out + blockIdx.x);
+}
+
+__device__ __forceinline__ void block_reduce_max_to(long long v, RedPartial* slot) {
   __shared__ long long sv[kBlock / 32];
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
@@ -110,9 +126,12 @@ __device__ __forceinline__ void block_reduce_max(long long v, RedPartial* out) {
     v = l < nw ? sv[l] : sv[0];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (l == 0) out[blockIdx.x] = RedPartial{v, 0ull};
+    if (l == 0) *slot = RedPartial{v, 0ull};
   }
+  __syncthreads();
 }
+
+__device__ __forceinline__ void block_reduce_max(long long v, RedPartial* out) { block_reduce_max_to(v, out + blockIdx.x); }
 
 // ---------------------------------------------------------------------------
 // Index algebra for compile-time (SIG, D).
@@ -193,7 +212,7 @@ __device__ __forceinline__ void tail_fields(unsigned long long t, int h, unsigne
 // the strings of N (appending every tuple of letters) while the others keep
 // head Z.  REFLECT: the addresses lie in the upper half and are read through
 // the complement symmetry (only with SYM).
-template <int SIG, int D, unsigned N, int Z, bool REFLECT>
+template <int SIG, int D, unsigned N, int Z, bool REFLECT, bool CG = false>
 __device__ __forceinline__ long long partial_sum(const long long* const* prev, const unsigned long long (&S)[D],
                                                  unsigned long long n_tail, unsigned long long n_total) {
   using G = Geo<SIG, D>;
@@ -211,7 +230,7 @@ __device__ __forceinline__ long long partial_sum(const long long* const* prev, c
   static_for<0, (int)cpow(SIG, K)>([&](auto cc) {
     constexpr unsigned long long off = G::coff(N, decltype(cc)::value);
     const unsigned long long y = base + off;
-    acc += ld_stream(v + (REFLECT ? (n_total - 1 - y) : y));
+    acc += ld_vec<CG>(v + (REFLECT ? (n_total - 1 - y) : y));
   });
   return acc;
 }
@@ -219,7 +238,7 @@ __device__ __forceinline__ long long partial_sum(const long long* const* prev, c
 // Every partial sum a head tuple of the thread may need.  With SYM only heads
 // with H_0 = 0 are computed: then z = 0 goes with sets N without string 0 and
 // z = 1 with sets containing it; UPPER marks the reflected tail of the pair.
-template <int SIG, int D, bool SYM, bool UPPER>
+template <int SIG, int D, bool SYM, bool UPPER, bool CG = false>
 __device__ __forceinline__ void all_partials(const long long* const* prev, const unsigned long long (&S)[D],
                                              unsigned long long n_tail, unsigned long long n_total,
                                              long long (&P)[Geo<SIG, D>::NP > 0 ? Geo<SIG, D>::NP : 1]) {
@@ -229,13 +248,13 @@ __device__ __forceinline__ void all_partials(const long long* const* prev, const
     constexpr unsigned N = (unsigned)(i / SIG) + 1;
     constexpr int Z = i % SIG;
     if constexpr (!SYM) {
-      P[i] = partial_sum<SIG, D, N, Z, false>(prev, S, n_tail, n_total);
+      P[i] = partial_sum<SIG, D, N, Z, false, CG>(prev, S, n_tail, n_total);
     } else {
       constexpr bool has0 = (N & 1u) != 0;
       if constexpr ((Z == 0 && !has0) || (Z == 1 && has0)) {
         // sets without string 0 keep its head z = 0 (lower half); sets with it
         // take string 0's second digit, which is 1 exactly for the upper tail
-        P[i] = partial_sum<SIG, D, N, Z, UPPER && has0>(prev, S, n_tail, n_total);
+        P[i] = partial_sum<SIG, D, N, Z, UPPER && has0, CG>(prev, S, n_tail, n_total);
       } else {
         P[i] = 0;
       }
@@ -302,95 +321,113 @@ __device__ __forceinline__ long long state_w(long long u, long long s_all,
 // ---------------------------------------------------------------------------
 // Kernels.
 
-template <int SIG, int D, bool SYM, bool INCR>
-__global__ void __launch_bounds__(kBlock) sweep_generic_kernel(SweepParams p) {
+// One thread's share of a sweep: tail tuple t (with SYM also its complement)
+// and every head tuple stored for it.  INCR folds the increment of each state
+// into (best_v, best_x).
+template <int SIG, int D, bool SYM, bool INCR, bool CG = false>
+__device__ __forceinline__ void generic_sweep_thread(const SweepParams& p, unsigned long long t, long long& best_v,
+                                                     unsigned long long& best_x) {
   using G = Geo<SIG, D>;
   const unsigned long long nt = p.n_tail;
   const unsigned long long n_total = nt * G::SD;
-  const unsigned long long n_threads = SYM ? nt / 2 : nt;
+  unsigned long long S[D];
+  tail_fields<SIG, D>(t, p.h, S);
+  long long s_all = 0;
+  {
+    const long long* vd = p.prev[D - 1];
+    const unsigned long long b = t * G::SD;
+    static_for<0, (int)G::SD>([&](auto c) { s_all += ld_vec<CG>(vd + b + decltype(c)::value); });
+  }
+  long long P[G::NP > 0 ? G::NP : 1];
+  all_partials<SIG, D, SYM, false, CG>(p.prev, S, nt, n_total, P);
+
+  auto emit = [&](auto Hc, unsigned long long tt, const long long(&PP)[G::NP > 0 ? G::NP : 1]) {
+    constexpr int H = decltype(Hc)::value;
+    const long long val = state_value<SIG, D, H>(s_all, PP, p.one);
+    const unsigned long long x = (unsigned long long)H * nt + tt;
+    if constexpr (INCR) {
+      const long long inc = val - ld_vec<CG>(p.prev[0] + x);
+      if (red_better(inc, x, best_v, best_x, p.r_mode)) best_v = inc, best_x = x;
+    }
+    p.out[x] = val;
+  };
+  constexpr int NH = SYM ? (int)(G::SD / SIG) : (int)G::SD;  // SYM: heads with H_0 = 0
+  static_for<0, NH>([&](auto Hc) { emit(Hc, t, P); });
+  if constexpr (SYM) {
+    const unsigned long long tu = nt - 1 - t;  // the complementary tail
+    unsigned long long SU[D];
+    tail_fields<SIG, D>(tu, p.h, SU);
+    long long PU[G::NP > 0 ? G::NP : 1];
+    all_partials<SIG, D, true, true, CG>(p.prev, SU, nt, n_total, PU);
+    // equal heads of the upper tail read the reflection of t's block: same sum
+    static_for<0, NH>([&](auto Hc) { emit(Hc, tu, PU); });
+  }
+}
+
+// One thread's share of a check: max of W over the states it owns.
+template <int SIG, int D, bool SYM, bool CG = false>
+__device__ __forceinline__ void generic_check_thread(const CheckParams& p, long long R, unsigned long long t,
+                                                     long long& best) {
+  using G = Geo<SIG, D>;
+  const unsigned long long nt = p.n_tail;
+  const unsigned long long n_total = nt * G::SD;
+  const long long* prev[kMaxD];
+#pragma unroll
+  for (int k = 0; k < D; ++k) prev[k] = p.u;
+  unsigned long long S[D];
+  tail_fields<SIG, D>(t, p.h, S);
+  long long s_all = 0;
+  {
+    const unsigned long long b = t * G::SD;
+    static_for<0, (int)G::SD>([&](auto c) { s_all += ld_vec<CG>(p.u + b + decltype(c)::value); });
+  }
+  long long P[G::NP > 0 ? G::NP : 1];
+  all_partials<SIG, D, SYM, false, CG>(prev, S, nt, n_total, P);
+  constexpr int NH = SYM ? (int)(G::SD / SIG) : (int)G::SD;
+  static_for<0, NH>([&](auto Hc) {
+    constexpr int H = decltype(Hc)::value;
+    const unsigned long long x = (unsigned long long)H * nt + t;
+    best = max(best, state_w<SIG, D, H>(ld_vec<CG>(p.u + x), s_all, P, p.one, R));
+  });
+  if constexpr (SYM) {
+    const unsigned long long tu = nt - 1 - t;
+    unsigned long long SU[D];
+    tail_fields<SIG, D>(tu, p.h, SU);
+    long long PU[G::NP > 0 ? G::NP : 1];
+    all_partials<SIG, D, true, true, CG>(prev, SU, nt, n_total, PU);
+    static_for<0, NH>([&](auto Hc) {
+      constexpr int H = decltype(Hc)::value;
+      const unsigned long long x = (unsigned long long)H * nt + tu;
+      best = max(best, state_w<SIG, D, H>(ld_vec<CG>(p.u + x), s_all, PU, p.one, R));
+    });
+  }
+}
+
+// threads a sweep or check of this kind runs: one per tail tuple (SYM: per pair)
+template <int SIG, int D, bool SYM>
+__host__ __device__ inline unsigned long long generic_threads(unsigned long long n_tail) {
+  return SYM ? n_tail / 2 : n_tail;
+}
+
+template <int SIG, int D, bool SYM, bool INCR>
+__global__ void __launch_bounds__(kBlock) sweep_generic_kernel(SweepParams p) {
+  const unsigned long long n_threads = generic_threads<SIG, D, SYM>(p.n_tail);
   long long best_v = p.r_mode ? LLONG_MIN : LLONG_MAX;
   unsigned long long best_x = ULLONG_MAX;
-
   for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < n_threads;
-       t += (unsigned long long)gridDim.x * blockDim.x) {
-    unsigned long long S[D];
-    tail_fields<SIG, D>(t, p.h, S);
-    long long s_all = 0;
-    {
-      const long long* vd = p.prev[D - 1];
-      const unsigned long long b = t * G::SD;
-      static_for<0, (int)G::SD>([&](auto c) { s_all += ld_stream(vd + b + decltype(c)::value); });
-    }
-    long long P[G::NP > 0 ? G::NP : 1];
-    all_partials<SIG, D, SYM, false>(p.prev, S, nt, n_total, P);
-
-    auto emit = [&](auto Hc, unsigned long long tt, const long long(&PP)[G::NP > 0 ? G::NP : 1]) {
-      constexpr int H = decltype(Hc)::value;
-      const long long val = state_value<SIG, D, H>(s_all, PP, p.one);
-      const unsigned long long x = (unsigned long long)H * nt + tt;
-      if constexpr (INCR) {
-        const long long inc = val - ld_stream(p.prev[0] + x);
-        if (red_better(inc, x, best_v, best_x, p.r_mode)) best_v = inc, best_x = x;
-      }
-      p.out[x] = val;
-    };
-    constexpr int NH = SYM ? (int)(G::SD / SIG) : (int)G::SD;  // SYM: heads with H_0 = 0
-    static_for<0, NH>([&](auto Hc) { emit(Hc, t, P); });
-    if constexpr (SYM) {
-      const unsigned long long tu = nt - 1 - t;  // the complementary tail
-      unsigned long long SU[D];
-      tail_fields<SIG, D>(tu, p.h, SU);
-      long long PU[G::NP > 0 ? G::NP : 1];
-      all_partials<SIG, D, true, true>(p.prev, SU, nt, n_total, PU);
-      // equal heads of the upper tail read the reflection of t's block: same sum
-      static_for<0, NH>([&](auto Hc) { emit(Hc, tu, PU); });
-    }
-  }
+       t += (unsigned long long)gridDim.x * blockDim.x)
+    generic_sweep_thread<SIG, D, SYM, INCR>(p, t, best_v, best_x);
   if constexpr (INCR) block_reduce_arg(best_v, best_x, p.r_mode, p.partials);
 }
 
 template <int SIG, int D, bool SYM>
 __global__ void __launch_bounds__(kBlock) check_generic_kernel(CheckParams p) {
-  using G = Geo<SIG, D>;
-  const unsigned long long nt = p.n_tail;
-  const unsigned long long n_total = nt * G::SD;
-  const unsigned long long n_threads = SYM ? nt / 2 : nt;
+  const unsigned long long n_threads = generic_threads<SIG, D, SYM>(p.n_tail);
   const long long R = p.R_from_state ? p.state->R : p.R;
-  const long long* prev[kMaxD];
-#pragma unroll
-  for (int k = 0; k < D; ++k) prev[k] = p.u;
   long long best = LLONG_MIN;
-
   for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < n_threads;
-       t += (unsigned long long)gridDim.x * blockDim.x) {
-    unsigned long long S[D];
-    tail_fields<SIG, D>(t, p.h, S);
-    long long s_all = 0;
-    {
-      const unsigned long long b = t * G::SD;
-      static_for<0, (int)G::SD>([&](auto c) { s_all += ld_stream(p.u + b + decltype(c)::value); });
-    }
-    long long P[G::NP > 0 ? G::NP : 1];
-    all_partials<SIG, D, SYM, false>(prev, S, nt, n_total, P);
-    constexpr int NH = SYM ? (int)(G::SD / SIG) : (int)G::SD;
-    static_for<0, NH>([&](auto Hc) {
-      constexpr int H = decltype(Hc)::value;
-      const unsigned long long x = (unsigned long long)H * nt + t;
-      best = max(best, state_w<SIG, D, H>(ld_stream(p.u + x), s_all, P, p.one, R));
-    });
-    if constexpr (SYM) {
-      const unsigned long long tu = nt - 1 - t;
-      unsigned long long SU[D];
-      tail_fields<SIG, D>(tu, p.h, SU);
-      long long PU[G::NP > 0 ? G::NP : 1];
-      all_partials<SIG, D, true, true>(prev, SU, nt, n_total, PU);
-      static_for<0, NH>([&](auto Hc) {
-        constexpr int H = decltype(Hc)::value;
-        const unsigned long long x = (unsigned long long)H * nt + tu;
-        best = max(best, state_w<SIG, D, H>(ld_stream(p.u + x), s_all, PU, p.one, R));
-      });
-    }
-  }
+       t += (unsigned long long)gridDim.x * blockDim.x)
+    generic_check_thread<SIG, D, SYM>(p, R, t, best);
   block_reduce_max(best, p.partials);
 }
 

@@ -88,98 +88,139 @@ __device__ __forceinline__ bool s2d2_orbit(unsigned long long k, unsigned tn, in
   return true;
 }
 
+template <bool CG>
+__device__ __forceinline__ longlong2 ld_pair(const long long* v, unsigned long long y) {
+  const longlong2* q = reinterpret_cast<const longlong2*>(v + y);  // y is even: 16-byte aligned
+  if constexpr (CG)
+    return __ldcg(q);
+  else
+    return __ldg(q);
+}
+
+template <bool CG = false>
 __device__ __forceinline__ long long pair_sum(const long long* v, unsigned long long y) {
-  const longlong2 q = __ldg(reinterpret_cast<const longlong2*>(v + y));  // y is even: 16-byte aligned
+  const longlong2 q = ld_pair<CG>(v, y);
   return q.x + q.y;
 }
 
+template <bool CG = false>
 __device__ __forceinline__ long long quad_sum(const long long* v, unsigned long long y) {
-  const longlong2 q0 = __ldg(reinterpret_cast<const longlong2*>(v + y));
-  const longlong2 q1 = __ldg(reinterpret_cast<const longlong2*>(v + y + 2));
+  const longlong2 q0 = ld_pair<CG>(v, y);
+  const longlong2 q1 = ld_pair<CG>(v, y + 2);
   return q0.x + q0.y + q1.x + q1.y;
+}
+
+// geometry of the orbit tiles for one h
+struct S2D2Geo {
+  int L;                     // h - 1: length of a tail string
+  unsigned tn;               // tiles per side: 2^(L-1) / 16
+  unsigned long long nt;     // tail tuples: 4^L
+  unsigned long long maskE;  // spread of L one-bits
+};
+
+__device__ __forceinline__ S2D2Geo s2d2_geo(int h, unsigned long long n_tail) {
+  S2D2Geo g;
+  g.L = h - 1;
+  g.tn = (1u << (g.L - 1)) / kS2D2Tile;
+  g.nt = n_tail;
+  g.maskE = spread_bits((1ull << g.L) - 1);
+  return g;
+}
+
+// One thread's orbit of tile k: the 8 stored outputs; INCR folds one
+// increment candidate per class of equal values into (best_v, best_x).
+template <bool INCR, bool CG = false>
+__device__ __forceinline__ void s2d2_sweep_orbit(const SweepParams& p, const S2D2Geo& g, unsigned long long k,
+                                                 long long& best_v, unsigned long long& best_x) {
+  S2D2Orbit o;
+  if (!s2d2_orbit(k, g.tn, g.L, g.nt, g.maskE, threadIdx.x, o)) return;
+  const unsigned long long nt = g.nt;
+  const long long* v1 = p.prev[0];
+  const long long* v2 = p.prev[1];
+  const long long s00 = quad_sum<CG>(v2, 4 * o.t);
+  const long long sb_t = pair_sum<CG>(v1, o.yb[0]);
+  const long long sb_tc = pair_sum<CG>(v1, o.yb[1]);
+  const long long sb_tp = pair_sum<CG>(v1, o.yb[2]);
+  const long long sb_sw = pair_sum<CG>(v1, o.yb[3]);
+  const long long e00 = p.one + (s00 >> 2);
+  const long long u_t = max(sb_t, sb_tp) >> 1;    // heads 01 at t and t'
+  const long long u_tc = max(sb_tc, sb_sw) >> 1;  // heads 01 at ~t and ~t'
+  long long* out = p.out;
+  out[o.t] = e00;
+  out[o.tc] = e00;
+  out[o.tp] = e00;
+  out[o.sw] = e00;
+  out[nt + o.t] = u_t;
+  out[nt + o.tp] = u_t;
+  out[nt + o.tc] = u_tc;
+  out[nt + o.sw] = u_tc;
+  if constexpr (INCR) {
+    // equal values have equal increments (v_{t-1} has the same symmetries):
+    // one candidate per class, at the class's smallest index
+    const unsigned long long m00 = min(min(o.t, o.tc), min(o.tp, o.sw));
+    const long long i00 = e00 - ld_vec<CG>(v1 + o.t);
+    const long long i01 = u_t - ld_vec<CG>(v1 + nt + o.t);
+    const long long i01c = u_tc - ld_vec<CG>(v1 + nt + o.tc);
+    if (red_better(i00, m00, best_v, best_x, p.r_mode)) best_v = i00, best_x = m00;
+    if (red_better(i01, nt + min(o.t, o.tp), best_v, best_x, p.r_mode)) best_v = i01, best_x = nt + min(o.t, o.tp);
+    if (red_better(i01c, nt + min(o.tc, o.sw), best_v, best_x, p.r_mode)) best_v = i01c, best_x = nt + min(o.tc, o.sw);
+  }
+}
+
+// W = u + 2R - F(u + R, u) at the 8 stored states of one orbit (3 distinct).
+template <bool CG = false>
+__device__ __forceinline__ void s2d2_check_orbit(const CheckParams& p, const S2D2Geo& g, long long R,
+                                                 unsigned long long k, long long& best) {
+  S2D2Orbit o;
+  if (!s2d2_orbit(k, g.tn, g.L, g.nt, g.maskE, threadIdx.x, o)) return;
+  const unsigned long long nt = g.nt;
+  const long long* u = p.u;
+  const long long s00 = quad_sum<CG>(u, 4 * o.t);
+  const long long sb_t = pair_sum<CG>(u, o.yb[0]);
+  const long long sb_tc = pair_sum<CG>(u, o.yb[1]);
+  const long long sb_tp = pair_sum<CG>(u, o.yb[2]);
+  const long long sb_sw = pair_sum<CG>(u, o.yb[3]);
+  // equal heads: only the all-advance candidate, shifted by (d - d) R = 0;
+  // heads 01: both candidates advance one string, shifted by (d - 1) R = R
+  const long long w00 = ld_vec<CG>(u + o.t) + 2 * R - (p.one + (s00 >> 2));
+  const long long w01 = ld_vec<CG>(u + nt + o.t) + 2 * R - ((max(sb_t, sb_tp) >> 1) + R);
+  const long long w01c = ld_vec<CG>(u + nt + o.tc) + 2 * R - ((max(sb_tc, sb_sw) >> 1) + R);
+  best = max(best, max(w00, max(w01, w01c)));
+}
+
+// the upper-triangle tile index q (A <= B) of one s-half as (A, B)
+__device__ __forceinline__ void tri_decode(unsigned long long q, unsigned& A, unsigned& B) {
+  unsigned long long b = (unsigned long long)((sqrt(8.0 * (double)q + 1.0) - 1.0) * 0.5);
+  while (b * (b + 1) / 2 > q) --b;
+  while ((b + 1) * (b + 2) / 2 <= q) ++b;
+  B = (unsigned)b;
+  A = (unsigned)(q - b * (b + 1) / 2);
 }
 
 template <bool INCR>
 __global__ void __launch_bounds__(kBlock) sweep_s2d2_kernel(SweepParams p) {
-  const int L = p.h - 1;
-  const unsigned long long nt = p.n_tail;
-  const unsigned long long maskE = spread_bits((1ull << L) - 1);
-  const unsigned tn = (1u << (L - 1)) / kS2D2Tile;
-  const unsigned long long n_tiles = 2ull * tn * tn;
-  const long long* v1 = p.prev[0];
-  const long long* v2 = p.prev[1];
+  const S2D2Geo g = s2d2_geo(p.h, p.n_tail);
+  const unsigned long long n_tiles = 2ull * g.tn * g.tn;
   long long best_v = p.r_mode ? LLONG_MIN : LLONG_MAX;
   unsigned long long best_x = ULLONG_MAX;
-
   for (unsigned long long k = blockIdx.x; k < n_tiles; k += gridDim.x) {
-    {
-      const unsigned long long rem = k % ((unsigned long long)tn * tn);
-      if (rem / tn > rem % tn) continue;  // tile below the diagonal: the whole CTA skips it
-    }
-    S2D2Orbit o;
-    if (!s2d2_orbit(k, tn, L, nt, maskE, threadIdx.x, o)) continue;
-    const long long s00 = quad_sum(v2, 4 * o.t);
-    const long long sb_t = pair_sum(v1, o.yb[0]);
-    const long long sb_tc = pair_sum(v1, o.yb[1]);
-    const long long sb_tp = pair_sum(v1, o.yb[2]);
-    const long long sb_sw = pair_sum(v1, o.yb[3]);
-    const long long e00 = p.one + (s00 >> 2);
-    const long long u_t = max(sb_t, sb_tp) >> 1;    // heads 01 at t and t'
-    const long long u_tc = max(sb_tc, sb_sw) >> 1;  // heads 01 at ~t and ~t'
-    long long* out = p.out;
-    out[o.t] = e00;
-    out[o.tc] = e00;
-    out[o.tp] = e00;
-    out[o.sw] = e00;
-    out[nt + o.t] = u_t;
-    out[nt + o.tp] = u_t;
-    out[nt + o.tc] = u_tc;
-    out[nt + o.sw] = u_tc;
-    if constexpr (INCR) {
-      // equal values have equal increments (v_{t-1} has the same symmetries):
-      // one candidate per class, at the class's smallest index
-      const unsigned long long m00 = min(min(o.t, o.tc), min(o.tp, o.sw));
-      const long long i00 = e00 - __ldg(v1 + o.t);
-      const long long i01 = u_t - __ldg(v1 + nt + o.t);
-      const long long i01c = u_tc - __ldg(v1 + nt + o.tc);
-      if (red_better(i00, m00, best_v, best_x, p.r_mode)) best_v = i00, best_x = m00;
-      if (red_better(i01, nt + min(o.t, o.tp), best_v, best_x, p.r_mode)) best_v = i01, best_x = nt + min(o.t, o.tp);
-      if (red_better(i01c, nt + min(o.tc, o.sw), best_v, best_x, p.r_mode))
-        best_v = i01c, best_x = nt + min(o.tc, o.sw);
-    }
+    const unsigned long long rem = k % ((unsigned long long)g.tn * g.tn);
+    if (rem / g.tn > rem % g.tn) continue;  // tile below the diagonal: the whole CTA skips it
+    s2d2_sweep_orbit<INCR>(p, g, k, best_v, best_x);
   }
   if constexpr (INCR) block_reduce_arg(best_v, best_x, p.r_mode, p.partials);
 }
 
-// W = u + 2R - F(u + R, u) at the 8 stored states of each orbit (3 distinct).
+template <int UNUSED = 0>
 __global__ void __launch_bounds__(kBlock) check_s2d2_kernel(CheckParams p) {
-  const int L = p.h - 1;
-  const unsigned long long nt = p.n_tail;
-  const unsigned long long maskE = spread_bits((1ull << L) - 1);
-  const unsigned tn = (1u << (L - 1)) / kS2D2Tile;
-  const unsigned long long n_tiles = 2ull * tn * tn;
+  const S2D2Geo g = s2d2_geo(p.h, p.n_tail);
+  const unsigned long long n_tiles = 2ull * g.tn * g.tn;
   const long long R = p.R_from_state ? p.state->R : p.R;
-  const long long* u = p.u;
   long long best = LLONG_MIN;
-
   for (unsigned long long k = blockIdx.x; k < n_tiles; k += gridDim.x) {
-    {
-      const unsigned long long rem = k % ((unsigned long long)tn * tn);
-      if (rem / tn > rem % tn) continue;
-    }
-    S2D2Orbit o;
-    if (!s2d2_orbit(k, tn, L, nt, maskE, threadIdx.x, o)) continue;
-    const long long s00 = quad_sum(u, 4 * o.t);
-    const long long sb_t = pair_sum(u, o.yb[0]);
-    const long long sb_tc = pair_sum(u, o.yb[1]);
-    const long long sb_tp = pair_sum(u, o.yb[2]);
-    const long long sb_sw = pair_sum(u, o.yb[3]);
-    // equal heads: only the all-advance candidate, shifted by (d - d) R = 0;
-    // heads 01: both candidates advance one string, shifted by (d - 1) R = R
-    const long long w00 = __ldg(u + o.t) + 2 * R - (p.one + (s00 >> 2));
-    const long long w01 = __ldg(u + nt + o.t) + 2 * R - ((max(sb_t, sb_tp) >> 1) + R);
-    const long long w01c = __ldg(u + nt + o.tc) + 2 * R - ((max(sb_tc, sb_sw) >> 1) + R);
-    best = max(best, max(w00, max(w01, w01c)));
+    const unsigned long long rem = k % ((unsigned long long)g.tn * g.tn);
+    if (rem / g.tn > rem % g.tn) continue;
+    s2d2_check_orbit(p, g, R, k, best);
   }
   block_reduce_max(best, p.partials);
 }
@@ -192,7 +233,7 @@ inline void launch_sweep_s2d2(const SweepParams& p, int grid, cudaStream_t s) {
 }
 
 inline void launch_check_s2d2(const CheckParams& p, int grid, cudaStream_t s) {
-  check_s2d2_kernel<<<grid, kBlock, 0, s>>>(p);
+  check_s2d2_kernel<0><<<grid, kBlock, 0, s>>>(p);
 }
 
 inline KernelSet make_s2d2_set() {
@@ -203,7 +244,7 @@ inline KernelSet make_s2d2_set() {
   k.sweep = &launch_sweep_s2d2;
   k.check = &launch_check_s2d2;
   k.sweep_fn = (const void*)&sweep_s2d2_kernel<true>;
-  k.check_fn = (const void*)&check_s2d2_kernel;
+  k.check_fn = (const void*)&check_s2d2_kernel<0>;
   k.tails_per_thread = 4;
   k.sweep_algo_bytes = 20;  // 8 B of v_{t-1} + 4 B of v_{t-2} (its distinct half) + 8 B written
   k.check_algo_bytes = 8;

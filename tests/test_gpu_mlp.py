@@ -1,0 +1,112 @@
+"""The warm-start network's GPU kernels against the CPU reference, and the warm start itself.
+
+The forward and backward kernels are checked against oracle/mlp.py (float64)
+on random batches; FP32 accumulation differs from float64 by rounding only,
+so gradients must agree to 2e-3 of their scale.  The warm start must give
+the same rigorous bound as the zero start (the check decides the bound), and
+its effect on the iteration count is reported, whatever it is.
+"""
+import numpy as np
+import pytest
+
+from oracle import mlp as omlp
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2407_10925_gb300 as lb
+
+    lb.lib()
+    return lb
+
+
+def _unflatten(flat):
+    H, F = omlp.HIDDEN, omlp.N_FEAT
+    o = 0
+    out = {}
+    for name, shape in [("W1", (H, F)), ("b1", (H,)), ("W2", (H, H)), ("b2", (H,)), ("w3", (H,)), ("b3", ())]:
+        size = int(np.prod(shape)) if shape else 1
+        out[name] = flat[o:o + size].astype(np.float64).reshape(shape) if shape else np.array(float(flat[o]))
+        o += size
+    return out
+
+
+def _flatten(g):
+    return np.concatenate([np.asarray(g[k], dtype=np.float64).reshape(-1) for k in ("W1", "b1", "W2", "b2", "w3", "b3")])
+
+
+def _batch(seed, n=96):
+    rng = np.random.default_rng(seed)
+    hs = rng.integers(3, 15, size=n)
+    states = np.array([rng.integers(0, 1 << (2 * int(h))) for h in hs], dtype=np.int64)
+    t = rng.normal(0, 2, size=n).astype(np.float32)
+    return states, hs.astype(np.int32), t
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_gradient_matches_reference(lb, seed):
+    with lb.LcsMlp(seed=seed) as m:
+        flat = m.get_params()
+        states, hs, t = _batch(seed)
+        loss, g = m.gradient(states, hs, t)
+        P = _unflatten(flat)
+        X = np.concatenate([omlp.features(states[i:i + 1], int(hs[i])) for i in range(states.size)])
+        loss_ref, g_ref = omlp.loss_and_grads(P, X, t.astype(np.float64))
+        gr = _flatten(g_ref)
+        assert abs(loss - loss_ref) <= 1e-4 * max(1.0, abs(loss_ref))
+        assert np.max(np.abs(g - gr)) <= 2e-3 * np.max(np.abs(gr)) + 1e-7
+
+
+def test_predict_matches_reference(lb):
+    import torch
+
+    with lb.LcsMlp(seed=5) as m:
+        P = _unflatten(m.get_params())
+        h = 9
+        rng = np.random.default_rng(0)
+        states = rng.integers(0, 1 << (2 * h), size=3000).astype(np.int64)
+        out = torch.empty(states.size, dtype=torch.float32, device="cuda")
+        m.predict(h, torch.from_numpy(states).cuda(), out)
+        torch.cuda.synchronize()
+        y_ref, _ = omlp.forward(P, omlp.features(states, h))
+        assert np.max(np.abs(out.cpu().numpy() - y_ref)) <= 1e-4 * max(1.0, np.max(np.abs(y_ref)))
+
+
+def _converged(lb, h, iters=300):
+    import torch
+
+    with lb.LcsBound(2, 2, h, check_every=50) as hnd:
+        hnd.iterate(iters)
+        v = torch.empty(4 ** h, dtype=torch.int64, device="cuda")
+        lb.lcs_bound_export_fx(hnd.hnd, 0, v)
+        return v, hnd.read()
+
+
+def test_training_reduces_loss_and_warm_start_keeps_the_bound(lb):
+    import torch
+
+    data = {h: _converged(lb, h) for h in (5, 6, 7)}
+    with lb.LcsMlp(seed=11) as m:
+        vecs = [data[h][0] for h in (5, 6, 7)]
+        before = m.train(vecs, [5, 6, 7], steps=0, batch=2048)
+        after = m.train(vecs, [5, 6, 7], steps=400, batch=2048, lr=2e-3)
+        assert after < 0.25 * before
+        h = 8
+        r_hat = data[7][1][2]  # r of the h = 7 run
+        newest = torch.empty(4 ** h, dtype=torch.float64, device="cuda")
+        older = torch.empty(4 ** h, dtype=torch.float64, device="cuda")
+        m.start_vectors(h, r_hat, newest, older)
+    with lb.LcsBound(2, 2, h, check_every=10) as zero, lb.LcsBound(2, 2, h, check_every=10) as warm:
+        warm.set_start([newest, older])
+        zero.iterate(400)
+        warm.iterate(400)
+        bz, bw = zero.read()[0], warm.read()[0]
+    # both rigorous; both converge to Table 2's 0.776860 for h = 8
+    assert abs(bz - bw) < 1e-7
+    assert abs(bw - 0.776860) < 1e-6
