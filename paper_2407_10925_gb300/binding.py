@@ -121,6 +121,7 @@ def lib():
                 "lcs_mlp_train": [vp, i32, vp, vp, i64, i32, ctypes.c_float, u64, i32, P(ctypes.c_float)],
                 "lcs_mlp_predict": [vp, i32, i64, vp, vp],
                 "lcs_mlp_start_vectors": [vp, i32, dbl, vp, vp],
+                "lcs_mlp_predict_bf16": [vp, i32, u64, i64, vp],
                 "lcs_sweep_fx": [i32, i32, i32, i32, i32, vp, vp, vp],
                 "lcs_sweep_incr_fx_noalloc": [i32, i32, i32, i32, i32, vp, vp, vp, vp, vp],
             }
@@ -487,6 +488,12 @@ class LcsMlp:
 
         torch.cuda.current_stream().synchronize()
         _check(lib().lcs_mlp_predict(self.hnd, h, states_dev.numel(), ps, out_dev.data_ptr()), "lcs_mlp_predict")
+        return out_dev
+
+    def predict_bf16(self, h, base, n, out_dev):
+        if not out_dev.is_cuda:
+            raise TypeError("predict_bf16 writes a CUDA tensor")
+        _check(lib().lcs_mlp_predict_bf16(self.hnd, h, base, n, out_dev.data_ptr()), "lcs_mlp_predict_bf16")
         return out_dev
 
     def start_vectors(self, h, r_hat, newest_dev, older_dev):

@@ -26,6 +26,9 @@
 #include <cstring>
 #include <vector>
 
+#include <cublas_v2.h>
+#include <cuda_bf16.h>
+
 #include "../../include/lcs_bound.h"
 #include "lcs_common.h"
 
@@ -294,6 +297,45 @@ __global__ void mlp_to_start_kernel(const float* __restrict__ y, long long n, lo
   }
 }
 
+// BF16 inference, first layer: rows are the states base + i (i < n); A1 in bf16
+__global__ void mlp_layer1_bf16_kernel(const float* __restrict__ P, unsigned long long base, int h, int n,
+                                       __nv_bfloat16* __restrict__ A1) {
+  const int r = blockIdx.x;
+  if (r >= n) return;
+  __shared__ int idx[2 * kHin];
+  __shared__ int cnt;
+  if (threadIdx.x == 0) cnt = mlp_active(base + (unsigned long long)r, h, idx);
+  __syncthreads();
+  const int j = threadIdx.x;
+  const float* W1 = P + kOffW1;
+  float z = P[kOffB1 + j] + (float)h * (1.0f / 16.0f) * W1[j * kFeat + (kFeat - 1)];
+  for (int i = 0; i < cnt; ++i) z += W1[j * kFeat + idx[i]];
+  A1[(long long)r * kHid + j] = __float2bfloat16_rn(gelu_f(z));
+}
+
+__global__ void mlp_to_bf16_kernel(const float* __restrict__ x, long long n, __nv_bfloat16* __restrict__ y) {
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    y[i] = __float2bfloat16_rn(x[i]);
+}
+
+// BF16 inference, head: y = w3 . GELU(Z2 + b2) + b3 (Z2 without bias from the GEMM)
+__global__ void mlp_head_bias_kernel(const float* __restrict__ P, const float* __restrict__ Z2, int n,
+                                     float* __restrict__ y) {
+  const int r = blockIdx.x;
+  if (r >= n) return;
+  const int j = threadIdx.x;
+  float v = gelu_f(Z2[(long long)r * kHid + j] + P[kOffB2 + j]) * P[kOffW3 + j];
+  __shared__ float red[kHid / 32];
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  if ((j & 31) == 0) red[j >> 5] = v;
+  __syncthreads();
+  if (j == 0) {
+    float s = 0.f;
+    for (int w = 0; w < kHid / 32; ++w) s += red[w];
+    y[r] = s + P[kOffB3];
+  }
+}
+
 __global__ void iota_kernel(unsigned long long* __restrict__ s, long long n, unsigned long long base) {
   for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
     s[i] = base + (unsigned long long)i;
@@ -324,6 +366,13 @@ struct lcs_mlp {
   int* hs;
   TrainSet* sets;
   cudaStream_t stream;
+  // BF16 inference
+  cublasHandle_t cublas;
+  __nv_bfloat16* W2h;
+  __nv_bfloat16* A1h;
+  float* Zinf;
+  float* yinf;
+  int inf_cap;
 };
 
 static unsigned long long host_splitmix(unsigned long long seed, unsigned long long i) {
@@ -400,7 +449,8 @@ void lcs_mlp_destroy(lcs_mlp_t* M) {
   if (!M) return;
   if (M->stream) cudaStreamSynchronize(M->stream);
   void* ptrs[] = {M->P, M->G, M->Mm, M->V, M->Z1, M->A1, M->Z2, M->A2, M->y, M->t, M->dy, M->dZ2, M->dA1,
-                  M->states, M->mask, M->hs, M->sets};
+                  M->states, M->mask, M->hs, M->sets, M->W2h, M->A1h, M->Zinf, M->yinf};
+  if (M->cublas) cublasDestroy(M->cublas);
   for (void* p : ptrs) cudaFree(p);
   if (M->stream) cudaStreamDestroy(M->stream);
   delete M;
@@ -552,22 +602,78 @@ lcs_status lcs_mlp_train(lcs_mlp_t* M, int n_sets, const int64_t* const* vectors
   return LCS_OK;
 }
 
+// BF16 inference of rows base .. base+m-1 (states of length h) into M->yinf:
+// layer 1 and the head in the kernels above, the 256 x 256 layer as a plain
+// bf16 x bf16 -> fp32 GEMM on the tensor cores (cuBLAS)
+static lcs_status infer_bf16(lcs_mlp* M, int h, unsigned long long base, int m) {
+  cudaStream_t s = M->stream;
+  mlp_layer1_bf16_kernel<<<m, kHid, 0, s>>>(M->P, base, h, m, M->A1h);
+  M_CUDA(cudaGetLastError());
+  const float one = 1.0f, zero = 0.0f;
+  // column-major view: Z2^T (256 x m) = W2 (op T of its row-major storage) * A1^T
+  cublasStatus_t cs = cublasGemmEx(M->cublas, CUBLAS_OP_T, CUBLAS_OP_N, kHid, m, kHid, &one, M->W2h, CUDA_R_16BF,
+                                   kHid, M->A1h, CUDA_R_16BF, kHid, &zero, M->Zinf, CUDA_R_32F, kHid,
+                                   CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
+  if (cs != CUBLAS_STATUS_SUCCESS) return mfail(LCS_ECUDA, "cublasGemmEx failed (%d)", (int)cs);
+  mlp_head_bias_kernel<<<m, kHid, 0, s>>>(M->P, M->Zinf, m, M->yinf);
+  M_CUDA(cudaGetLastError());
+  return LCS_OK;
+}
+
+static lcs_status ensure_inference(lcs_mlp* M, int rows) {
+  if (!M->cublas) {
+    if (cublasCreate(&M->cublas) != CUBLAS_STATUS_SUCCESS) return mfail(LCS_ECUDA, "cublasCreate failed");
+    if (cublasSetStream(M->cublas, M->stream) != CUBLAS_STATUS_SUCCESS) return mfail(LCS_ECUDA, "cublasSetStream");
+    M_CUDA(cudaMalloc(&M->W2h, sizeof(__nv_bfloat16) * kHid * kHid));
+  }
+  if (rows > M->inf_cap) {
+    cudaFree(M->A1h);
+    cudaFree(M->Zinf);
+    cudaFree(M->yinf);
+    M->A1h = nullptr;
+    M->Zinf = nullptr;
+    M->yinf = nullptr;
+    M_CUDA(cudaMalloc(&M->A1h, sizeof(__nv_bfloat16) * (size_t)rows * kHid));
+    M_CUDA(cudaMalloc(&M->Zinf, sizeof(float) * (size_t)rows * kHid));
+    M_CUDA(cudaMalloc(&M->yinf, sizeof(float) * (size_t)rows));
+    M->inf_cap = rows;
+  }
+  // the current FP32 weights of the 256 x 256 layer, rounded to bf16
+  mlp_to_bf16_kernel<<<256, 256, 0, M->stream>>>(M->P + kOffW2, (long long)kHid * kHid, M->W2h);
+  M_CUDA(cudaGetLastError());
+  return LCS_OK;
+}
+
 // predictions for every state of length h, as two full-length double vectors
 // of a start: older = u_hat, newest = u_hat + r_hat (device pointers)
 lcs_status lcs_mlp_start_vectors(lcs_mlp_t* M, int h, double r_hat, double* newest_dev, double* older_dev) {
   if (!M || !newest_dev || !older_dev || h < 1 || h > 16) return mfail(LCS_EINVAL, "bad argument");
   const long long n = 1ll << (2 * h);
-  const int chunk = 1 << 20;
-  lcs_status st = ensure_cap(M, chunk);
+  const int chunk = 1 << 22;
+  lcs_status st = ensure_inference(M, (int)std::min<long long>(n, chunk));
   if (st) return st;
   for (long long off = 0; off < n; off += chunk) {
     const int m = (int)std::min<long long>(chunk, n - off);
-    iota_kernel<<<256, 256, 0, M->stream>>>(M->states, m, (unsigned long long)off);
-    fill_int_kernel<<<256, 256, 0, M->stream>>>(M->hs, m, h);
-    st = forward_rows(M, m, false);
+    st = infer_bf16(M, h, (unsigned long long)off, m);
     if (st) return st;
-    mlp_to_start_kernel<<<256, 256, 0, M->stream>>>(M->y, m, off, r_hat, 2, newest_dev, older_dev);
+    mlp_to_start_kernel<<<1024, 256, 0, M->stream>>>(M->yinf, m, off, r_hat, 2, newest_dev, older_dev);
     M_CUDA(cudaGetLastError());
+  }
+  M_CUDA(cudaStreamSynchronize(M->stream));
+  return LCS_OK;
+}
+
+// BF16 predictions for the consecutive states base .. base+n-1 (device output)
+lcs_status lcs_mlp_predict_bf16(lcs_mlp_t* M, int h, uint64_t base, int64_t n, float* out_dev) {
+  if (!M || !out_dev || n < 0 || h < 1 || h > 31) return mfail(LCS_EINVAL, "bad argument");
+  const int chunk = 1 << 22;
+  lcs_status st = ensure_inference(M, (int)std::min<int64_t>(std::max<int64_t>(n, 1), chunk));
+  if (st) return st;
+  for (int64_t off = 0; off < n; off += chunk) {
+    const int m = (int)std::min<int64_t>(chunk, n - off);
+    st = infer_bf16(M, h, base + (uint64_t)off, m);
+    if (st) return st;
+    M_CUDA(cudaMemcpyAsync(out_dev + off, M->yinf, sizeof(float) * m, cudaMemcpyDeviceToDevice, M->stream));
   }
   M_CUDA(cudaStreamSynchronize(M->stream));
   return LCS_OK;
