@@ -35,6 +35,8 @@ sys.path.insert(0, ROOT)
 BATCH_SHAPES = [(2, 2, 10), (2, 2, 12), (3, 2, 6), (3, 2, 7), (4, 2, 5), (2, 3, 6), (2, 3, 7), (2, 4, 5)]
 CONFIGS = {
     "batch": dict(sigma=0, d=0, h=0, shapes=BATCH_SHAPES),
+    "warm": dict(sigma=2, d=2, h=14, train_h=[10, 11, 12], ref_iters=4000, train_steps=3000),
+    "fp32": dict(sigma=0, d=0, h=0, shapes=[(2, 3, 8), (3, 2, 8)], iters=1500),
     "h16": dict(sigma=2, d=2, h=16),
     "h14": dict(sigma=2, d=2, h=14),
     "h12": dict(sigma=2, d=2, h=12),
@@ -310,6 +312,131 @@ def run_batch(args, cfg, world, rank, local_rank):
         print(json.dumps(line), flush=True)
 
 
+def run_warm(args, cfg, world, rank, local_rank):
+    """Config 5: iterations and wall time to a bound within 1e-7 of the zero-start
+    converged bound at h = 14, from the zero start, a prefix-truncation start and
+    the learned (MLP) start trained on converged iterates of h = 10, 11, 12."""
+    import torch
+
+    import paper_2407_10925_gb300 as lb
+
+    torch.cuda.set_device(local_rank)
+    H, train_h, chunk, tol = cfg["h"], cfg["train_h"], 10, 1e-7
+
+    def sync():
+        torch.cuda.synchronize()
+
+    def converged_vector(h, iters=1500):
+        with lb.LcsBound(2, 2, h, check_every=100) as hnd:
+            hnd.iterate(iters)
+            v = torch.empty(4 ** h, dtype=torch.int64, device="cuda")
+            lb.lcs_bound_export_fx(hnd.hnd, 0, v)
+            return v, hnd.read()
+
+    def run_to(target, start=None, limit=6000):
+        """iterations (a multiple of `chunk`) and seconds until the bound reaches target"""
+        sync()
+        t0 = time.perf_counter()
+        with lb.LcsBound(2, 2, H, check_every=chunk) as hnd:
+            if start is not None:
+                hnd.set_start(start)
+            it, bound = 0, 0.0
+            while it < limit:
+                hnd.iterate(chunk)
+                it += chunk
+                bound = hnd.read()[0]
+                if target is not None and bound >= target:
+                    break
+        return it, time.perf_counter() - t0, bound
+
+    # the zero-start reference: run long, the converged bound is the target
+    it_ref, t_ref, bound_ref = run_to(None, limit=cfg["ref_iters"])
+    target = bound_ref - tol
+    it_zero, t_zero, b_zero = run_to(target)
+
+    # training data: converged iterates of smaller h
+    sync()
+    t0 = time.perf_counter()
+    data = {h: converged_vector(h) for h in train_h}
+    t_data = time.perf_counter() - t0
+    r_hat = data[max(train_h)][1][2]
+
+    sync()
+    t0 = time.perf_counter()
+    mlp = lb.LcsMlp(seed=2024)
+    loss0 = mlp.train([data[h][0] for h in train_h], train_h, steps=0, batch=4096)
+    loss = mlp.train([data[h][0] for h in train_h], train_h, steps=cfg["train_steps"], batch=4096, lr=1e-3)
+    t_train = time.perf_counter() - t0
+
+    newest = torch.empty(4 ** H, dtype=torch.float64, device="cuda")
+    older = torch.empty(4 ** H, dtype=torch.float64, device="cuda")
+    sync()
+    t0 = time.perf_counter()
+    mlp.start_vectors(H, r_hat, newest, older)
+    t_infer = time.perf_counter() - t0
+    it_mlp, t_mlp, b_mlp = run_to(target, start=[newest, older])
+
+    sync()
+    t0 = time.perf_counter()
+    lb.lcs_lift_prefix(max(train_h), H, data[max(train_h)][0], r_hat, newest, older)
+    t_lift = time.perf_counter() - t0
+    it_lift, t_lift_run, b_lift = run_to(target, start=[newest, older])
+    mlp.close()
+
+    line = {
+        "metric": "iterations and wall time to a bound within 1e-7 of the zero-start converged bound",
+        "value": t_infer + t_mlp, "unit": "s", "n_gpus": world, "steps": 1, "warmup": 0,
+        "higher_is_better": False, "dtype": "int64", "data": "synthetic (the method's own iterates)",
+        "config": {"workload": f"sigma=2 d=2 h={H} ({4 ** H} states); MLP trained on converged iterates of h="
+                               f"{train_h}; checks every {chunk} iterations", "tolerance": tol},
+        "reference": {"zero_start_iterations": it_ref, "bound": bound_ref},
+        "zero_start": {"iterations": it_zero, "seconds": t_zero, "bound": b_zero},
+        "truncation_lift": {"iterations": it_lift, "seconds": t_lift + t_lift_run, "bound": b_lift},
+        "mlp": {"iterations": it_mlp, "seconds_iterating": t_mlp, "seconds_inference_bf16": t_infer,
+                "seconds_total_with_inference": t_infer + t_mlp, "bound": b_mlp,
+                "train_seconds": t_train, "train_steps": cfg["train_steps"], "loss_before": loss0,
+                "loss_after": loss, "training_data_seconds": t_data},
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
+def run_fp32(args, cfg, world, rank, local_rank):
+    """Config 4: (2,3,8) and (3,2,8), 1500 iterations from zero, exact fixed point vs float32 storage."""
+    import torch
+
+    import paper_2407_10925_gb300 as lb
+
+    torch.cuda.set_device(local_rank)
+    results = {}
+    for s_, d_, h_ in cfg["shapes"]:
+        n = s_ ** (d_ * h_)
+        iters = cfg["iters"]
+        with lb.LcsBound(s_, d_, h_, check_every=100, timing=1, symmetry=0) as hnd:
+            hnd.iterate(iters)
+            st = hnd.stats()
+            exact = torch.empty(n, dtype=torch.int64, device="cuda")
+            lb.lcs_bound_export_fx(hnd.hnd, 0, exact)
+            bound, _, r, eps, _ = hnd.read()
+        f32 = torch.empty(n, dtype=torch.float64, device="cuda")
+        ms32 = lb.lcs_fp32_experiment(s_, d_, h_, iters, r, f32)
+        ex = exact.double() / 2.0 ** 44
+        err = (f32 - ex).abs()
+        results[f"({s_},{d_},{h_})"] = {
+            "states": n, "iterations": iters, "bound_fixed_point": bound,
+            "fixed_point_ms_per_sweep": st["sweep_ms"] / max(1, st["sweep_launches"]),
+            "float32_ms_per_sweep": ms32,
+            "float32_max_abs_error": float(err.max()), "float32_max_rel_error": float((err / ex.abs()).max()),
+            "float32_mean_abs_error": float(err.mean()),
+        }
+        del exact, f32, ex, err
+        torch.cuda.empty_cache()
+    if rank == 0:
+        print(json.dumps({"metric": "float32 storage experiment: error vs exact iterates and sweep time",
+                          "config": {"workload": "zero start, full storage (no symmetry), 1500 iterations"},
+                          "results": results, "note": "no bound is derived from float32 iterates"}), flush=True)
+
+
 def main():
     args = parse()
     cfg = CONFIGS[args.config]
@@ -322,6 +449,12 @@ def main():
         return
     if args.config == "batch":
         run_batch(args, cfg, world, rank, local_rank)
+        return
+    if args.config == "warm":
+        run_warm(args, cfg, world, rank, local_rank)
+        return
+    if args.config == "fp32":
+        run_fp32(args, cfg, world, rank, local_rank)
         return
 
     cpu = None

@@ -74,7 +74,11 @@ typedef struct {
   /* 0: R = minimum increment (default).  1: R = maximum increment (the line of
    * Algorithm 2 as printed).  E is evaluated for whichever R is taken. */
   int r_mode;
-  /* 0: F as in the paper (max over z of F_z).  Other values: LCS_EUNSUPPORTED. */
+  /* 0: F as in the paper (max over z of F_z).  1: the max runs over every
+   * non-empty set of advanced strings, and for equal heads the full set carries
+   * the +1 of the match -- an extension the paper does not use (also a valid
+   * lower bound: dropping heads never increases an LCS); kernels for sigma = 2,
+   * d = 2, 3 and sigma = 3, d = 2, else LCS_EUNSUPPORTED. */
   int f_mode;
   /* K, the number of fractional bits of the fixed-point iterates; 0 -> 44.
    * Valid range 8..56. */
@@ -289,6 +293,27 @@ lcs_status lcs_mlp_predict_bf16(lcs_mlp_t* m, int h, uint64_t base, int64_t n, f
  * inference: older = u_hat, newest = u_hat + r_hat.  Synchronous. */
 lcs_status lcs_mlp_start_vectors(lcs_mlp_t* m, int h, double r_hat, double* newest_dev, double* older_dev);
 void lcs_mlp_destroy(lcs_mlp_t* m);
+
+/* The non-learned control for the warm start (sigma = d = 2): a start for
+ * shape h_to built from a full-length fixed-point vector of shape h_from by
+ * cutting each tuple to its first h_from letters (the state index shifted
+ * right by 2 (h_to - h_from) bits): older[x] = (src[x >> s] - src[0]) * 2^-K,
+ * newest = older + r_hat.  Device pointers; uses the legacy default stream;
+ * synchronous. */
+lcs_status lcs_lift_prefix(int h_from, int h_to, const int64_t* src_dev, int frac_bits, double r_hat,
+                           double* newest_dev, double* older_dev);
+
+/* ------------------------------------------------------------------------ */
+/* Experiment: float32 storage.  Runs n_iters iterations of Algorithm 2 from
+ * the zero start with iterates stored as float32 w_t = v_t - t rho (offset
+ * normalisation through F's translation invariance) and float32 arithmetic,
+ * then writes the newest iterate v = w + t rho as doubles to newest_dev
+ * (device, sigma^(d h) values).  (sigma, d) in {(2,2), (2,3), (3,2)}, full
+ * storage.  *ms_per_sweep receives the mean sweep time.  No bound is derived:
+ * the rounding is not directed; the point is the error against the exact
+ * fixed-point iterates at half the bytes.  Legacy default stream; synchronous. */
+lcs_status lcs_fp32_experiment(int sigma, int d, int h, int64_t n_iters, double rho, double* newest_dev,
+                               double* ms_per_sweep);
 
 /* ------------------------------------------------------------------------ */
 /* Stateless entry point.

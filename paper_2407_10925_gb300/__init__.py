@@ -31,6 +31,8 @@ from .binding import (  # noqa: F401
     lcs_bound_size,
     lcs_bound_stats,
     lcs_bound_synchronize,
+    lcs_fp32_experiment,
+    lcs_lift_prefix,
     lcs_sweep_fx,
     lcs_sweep_incr_fx_noalloc,
     lib,

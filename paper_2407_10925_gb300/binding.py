@@ -122,6 +122,8 @@ def lib():
                 "lcs_mlp_predict": [vp, i32, i64, vp, vp],
                 "lcs_mlp_start_vectors": [vp, i32, dbl, vp, vp],
                 "lcs_mlp_predict_bf16": [vp, i32, u64, i64, vp],
+                "lcs_lift_prefix": [i32, i32, vp, i32, dbl, vp, vp],
+                "lcs_fp32_experiment": [i32, i32, i32, i64, dbl, vp, P(dbl)],
                 "lcs_sweep_fx": [i32, i32, i32, i32, i32, vp, vp, vp],
                 "lcs_sweep_incr_fx_noalloc": [i32, i32, i32, i32, i32, vp, vp, vp, vp, vp],
             }
@@ -420,6 +422,26 @@ class LcsBatch:
 
     def set_spin_budget(self, cycles):
         lcs_bound_batch_set_spin_budget(self.hnd, cycles)
+
+
+def lcs_fp32_experiment(sigma, d, h, n_iters, rho, newest_dev):
+    """Float32-stored iteration from the zero start (an experiment, no bound); returns ms per sweep."""
+    p, on = _ptr_and_kind(newest_dev, np.float64)
+    if not on:
+        raise TypeError("lcs_fp32_experiment writes a CUDA tensor")
+    ms = ctypes.c_double()
+    _check(lib().lcs_fp32_experiment(sigma, d, h, n_iters, float(rho), p, ctypes.byref(ms)), "lcs_fp32_experiment")
+    return ms.value
+
+
+def lcs_lift_prefix(h_from, h_to, src_dev, r_hat, newest_dev, older_dev, frac_bits=44):
+    """Prefix-truncation start: every tuple of length h_to takes the value of its first h_from letters."""
+    ps, a = _ptr_and_kind(src_dev, np.int64)
+    pn, b = _ptr_and_kind(newest_dev, np.float64)
+    po, c = _ptr_and_kind(older_dev, np.float64)
+    if not (a and b and c):
+        raise TypeError("lcs_lift_prefix takes CUDA tensors")
+    _check(lib().lcs_lift_prefix(h_from, h_to, ps, frac_bits, float(r_hat), pn, po), "lcs_lift_prefix")
 
 
 def lcs_mlp_param_count() -> int:

@@ -27,6 +27,7 @@ SOURCES = [
     "kernels_s2d2.cu",
     "batch.cu",
     "mlp.cu",
+    "fp32.cu",
 ]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]

@@ -3,7 +3,8 @@
 
 namespace lcs {
 
-const KernelSet* kernels_sigma45(int sigma, int d) {
+const KernelSet* kernels_sigma45(int sigma, int d, int f_mode) {
+  if (f_mode != 0) return nullptr;
   static const KernelSet sets[] = {make_generic_set<4, 2, false>(), make_generic_set<5, 2, false>()};
   for (const auto& k : sets)
     if (k.sigma == sigma && k.d == d) return &k;

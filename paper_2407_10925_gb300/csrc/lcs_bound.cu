@@ -354,7 +354,7 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   if (opts.frac_bits < 8 || opts.frac_bits > 56) return fail(LCS_EINVAL, "frac_bits %d outside 8..56", opts.frac_bits);
   if (opts.r_mode != 0 && opts.r_mode != 1) return fail(LCS_EINVAL, "r_mode %d", opts.r_mode);
   if (opts.check_every < 0) return fail(LCS_EINVAL, "check_every %d", opts.check_every);
-  if (opts.f_mode != 0) return fail(LCS_EUNSUPPORTED, "f_mode %d has no GPU kernel", opts.f_mode);
+  if (opts.f_mode != 0 && opts.f_mode != 1) return fail(LCS_EINVAL, "f_mode %d", opts.f_mode);
   if (opts.alloc && !opts.free) return fail(LCS_EINVAL, "alloc given without free");
   // state count below 2^40
   unsigned long long n = 1;
@@ -363,9 +363,9 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
     if (n >= (1ull << 40)) return fail(LCS_EINVAL, "sigma^(d h) must be below 2^40");
   }
   const int sym = (sigma == 2 && opts.symmetry && h >= 2) ? 1 : 0;
-  const KernelSet* ks = find_kernels(sigma, d, sym);
-  if (!ks) return fail(LCS_EUNSUPPORTED, "no kernel compiled for sigma=%d d=%d", sigma, d);
-  const KernelSet* ks_swap = (sym && d == 2 && h >= 6) ? find_kernels(sigma, d, 2) : nullptr;
+  const KernelSet* ks = find_kernels(sigma, d, sym, opts.f_mode);
+  if (!ks) return fail(LCS_EUNSUPPORTED, "no kernel compiled for sigma=%d d=%d f_mode=%d", sigma, d, opts.f_mode);
+  const KernelSet* ks_swap = (sym && d == 2 && h >= 6 && opts.f_mode == 0) ? find_kernels(sigma, d, 2) : nullptr;
 
   lcs_bound* H = new (std::nothrow) lcs_bound();
   if (!H) return fail(LCS_ENOMEM, "host allocation");
@@ -941,7 +941,7 @@ lcs_status lcs_bound_batch_set_spin_budget(lcs_bound_t* H, int64_t cycles) {
 lcs_status lcs_sweep_fx(int sigma, int d, int h, int f_mode, int frac_bits, const int64_t* const* v_prev,
                         int64_t* v_out, void* stream) {
   if (sigma < 2 || d < 2 || h < 1 || d > kMaxD) return fail(LCS_EINVAL, "bad shape");
-  if (f_mode != 0) return fail(LCS_EUNSUPPORTED, "f_mode %d", f_mode);
+  if (f_mode != 0 && f_mode != 1) return fail(LCS_EINVAL, "f_mode %d", f_mode);
   if (frac_bits == 0) frac_bits = 44;
   if (frac_bits < 8 || frac_bits > 56) return fail(LCS_EINVAL, "frac_bits");
   if (!v_prev || !v_out) return fail(LCS_EINVAL, "NULL argument");
@@ -951,8 +951,8 @@ lcs_status lcs_sweep_fx(int sigma, int d, int h, int f_mode, int frac_bits, cons
     if (n >= (1ull << 40)) return fail(LCS_EINVAL, "sigma^(d h) must be below 2^40");
   }
   for (int i = 0; i < d; ++i) sd *= (unsigned long long)sigma;
-  const KernelSet* ks = find_kernels(sigma, d, 0);
-  if (!ks) return fail(LCS_EUNSUPPORTED, "no kernel for sigma=%d d=%d", sigma, d);
+  const KernelSet* ks = find_kernels(sigma, d, 0, f_mode);
+  if (!ks) return fail(LCS_EUNSUPPORTED, "no kernel for sigma=%d d=%d f_mode=%d", sigma, d, f_mode);
   SweepParams p{};
   for (int k = 0; k < d; ++k) {
     if (!v_prev[k]) return fail(LCS_EINVAL, "v_prev[%d] is NULL", k);

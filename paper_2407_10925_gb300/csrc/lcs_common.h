@@ -66,6 +66,7 @@ struct CheckParams {
 // Host-visible description of the kernels compiled for one (sigma, d).
 struct KernelSet {
   int sigma, d;
+  int f_mode;                    // 0: the paper's F; 1: every non-empty advance set
   int sym;                       // 0: full storage; 1: complement-symmetric storage (sigma = 2);
                                  // 2: complement storage + swap-aware reads (sigma = d = 2)
   void (*sweep)(const SweepParams&, int grid, cudaStream_t);
@@ -80,6 +81,6 @@ struct KernelSet {
 };
 
 // Registry filled by the per-alphabet translation units.
-const KernelSet* find_kernels(int sigma, int d, int sym);
+const KernelSet* find_kernels(int sigma, int d, int sym, int f_mode = 0);
 
 }  // namespace lcs

@@ -4,17 +4,17 @@
 
 namespace lcs {
 
-const KernelSet* kernels_sigma2(int d, int sym);
-const KernelSet* kernels_sigma3(int d);
-const KernelSet* kernels_sigma45(int sigma, int d);
+const KernelSet* kernels_sigma2(int d, int sym, int f_mode);
+const KernelSet* kernels_sigma3(int d, int f_mode);
+const KernelSet* kernels_sigma45(int sigma, int d, int f_mode);
 const KernelSet* kernels_s2d2();
 
-const KernelSet* find_kernels(int sigma, int d, int sym) {
-  if (sym == 2) return (sigma == 2 && d == 2) ? kernels_s2d2() : nullptr;
-  if (sigma == 2) return kernels_sigma2(d, sym);
+const KernelSet* find_kernels(int sigma, int d, int sym, int f_mode) {
+  if (sym == 2) return (sigma == 2 && d == 2 && f_mode == 0) ? kernels_s2d2() : nullptr;
+  if (sigma == 2) return kernels_sigma2(d, sym, f_mode);
   if (sym) return nullptr;
-  if (sigma == 3) return kernels_sigma3(d);
-  if (sigma == 4 || sigma == 5) return kernels_sigma45(sigma, d);
+  if (sigma == 3) return kernels_sigma3(d, f_mode);
+  if (sigma == 4 || sigma == 5) return kernels_sigma45(sigma, d, f_mode);
   return nullptr;
 }
 

@@ -142,6 +142,8 @@ struct Geo {
   static constexpr unsigned FULL = (1u << D) - 1;               // every string advanced
   static constexpr int NSETS = (int)FULL - 1;                   // proper non-empty advance sets
   static constexpr int NP = NSETS * SIG;                        // partial sums (N, z)
+  static constexpr int HW = (int)cpow(SIG, D - 1);              // f_mode 1: head slots per advance set
+  static constexpr int NPA = (NSETS > 0 ? NSETS : 1) * HW;      // f_mode 1: partial sums (N, heads outside N)
   static constexpr bool POW2 = (SIG & (SIG - 1)) == 0;
   static constexpr int BITS = POW2 ? cctz(SIG) : 0;
 
@@ -176,6 +178,15 @@ struct Geo {
         cc /= SIG;
       }
     return off;
+  }
+
+  // the heads of the strings outside N in head tuple H, first such string most
+  // significant (f_mode 1)
+  __host__ __device__ static constexpr int heads_outside(int H, unsigned N) {
+    int hc = 0;
+    for (int j = 0; j < D; ++j)
+      if (!(N >> j & 1u)) hc = hc * SIG + head(H, j);
+    return hc;
   }
 
   // pattern of string j's digits inside a tail index (power-of-two SIG)
@@ -233,6 +244,98 @@ __device__ __forceinline__ long long partial_sum(const long long* const* prev, c
     acc += ld_vec<CG>(v + (REFLECT ? (n_total - 1 - y) : y));
   });
   return acc;
+}
+
+// As partial_sum, but the strings outside N keep arbitrary heads: HC lists
+// them (the head digit of the k-th string outside N, string order, as a
+// base-SIG number with the first such string most significant).
+template <int SIG, int D, unsigned N, int HC, bool REFLECT, bool CG>
+__device__ __forceinline__ long long partial_sum_heads(const long long* const* prev, const unsigned long long (&S)[D],
+                                                       unsigned long long n_tail, unsigned long long n_total) {
+  using G = Geo<SIG, D>;
+  constexpr int K = cpopc(N);
+  const long long* v = prev[K - 1];
+  unsigned long long base = 0;
+  int hc = HC;
+#pragma unroll
+  for (int j = D - 1; j >= 0; --j) {
+    if (N >> j & 1u) {
+      base += S[j] * G::SD;
+    } else {
+      base += S[j] + (unsigned long long)(hc % SIG) * n_tail * G::wlast(j);
+      hc /= SIG;
+    }
+  }
+  long long acc = 0;
+  static_for<0, (int)cpow(SIG, K)>([&](auto cc) {
+    constexpr unsigned long long off = G::coff(N, decltype(cc)::value);
+    const unsigned long long y = base + off;
+    acc += ld_vec<CG>(v + (REFLECT ? (n_total - 1 - y) : y));
+  });
+  return acc;
+}
+
+// f_mode = 1: one partial sum per (proper non-empty N, heads outside N);
+// index (N - 1) * SIG^(D-1) + HC.  With SYM only heads with H_0 = 0 are
+// computed, so sets without string 0 need HC with string 0's head 0.
+template <int SIG, int D, bool SYM, bool UPPER, bool CG>
+__device__ __forceinline__ void all_partials_fall(const long long* const* prev, const unsigned long long (&S)[D],
+                                                  unsigned long long n_tail, unsigned long long n_total,
+                                                  long long (&P)[Geo<SIG, D>::NPA]) {
+  using G = Geo<SIG, D>;
+  constexpr int W = G::HW;
+  static_for<0, G::NSETS * W>([&](auto ic) {
+    constexpr int i = decltype(ic)::value;
+    constexpr unsigned N = (unsigned)(i / W) + 1;
+    constexpr int HC = i % W;
+    constexpr int K = cpopc(N);
+    if constexpr (HC >= (int)cpow(SIG, D - K)) {
+      P[i] = 0;  // fewer strings outside N than the slot allows
+    } else {
+      constexpr bool has0 = (N & 1u) != 0;
+      // string 0 outside N: its head is HC's leading digit
+      constexpr int head0 = has0 ? 0 : (int)(HC / cpow(SIG, D - K - 1));
+      if constexpr (SYM && !has0 && head0 != 0) {
+        P[i] = 0;  // only heads with H_0 = 0 are stored
+      } else {
+        P[i] = partial_sum_heads<SIG, D, N, HC, SYM && UPPER && has0, CG>(prev, S, n_tail, n_total);
+      }
+    }
+  });
+}
+
+// f_mode = 1 value of head tuple H: the max over every non-empty advance set;
+// the full set carries the +1 when all heads agree
+template <int SIG, int D, int H>
+__device__ __forceinline__ long long state_value_fall(
+    long long s_all, const long long (&P)[Geo<SIG, D>::NPA],
+    long long one) {
+  using G = Geo<SIG, D>;
+  constexpr int W = G::HW;
+  long long key = G::all_equal(H) ? s_all + (long long)G::SD * one : s_all;
+  static_for<1, (int)G::FULL>([&](auto Nc) {
+    constexpr unsigned N = (unsigned)decltype(Nc)::value;
+    constexpr int i = (int)(N - 1) * W + G::heads_outside(H, N);
+    key = max(key, P[i] * (long long)cpow(SIG, D - cpopc(N)));
+  });
+  return floor_div<G::SD>(key);
+}
+
+template <int SIG, int D, int H>
+__device__ __forceinline__ long long state_w_fall(
+    long long u, long long s_all,
+    const long long (&P)[Geo<SIG, D>::NPA], long long one,
+    long long R) {
+  using G = Geo<SIG, D>;
+  constexpr int W = G::HW;
+  long long best = floor_div<G::SD>(s_all) + (G::all_equal(H) ? one : 0);
+  static_for<1, (int)G::FULL>([&](auto Nc) {
+    constexpr unsigned N = (unsigned)decltype(Nc)::value;
+    constexpr int K = cpopc(N);
+    constexpr int i = (int)(N - 1) * W + G::heads_outside(H, N);
+    best = max(best, floor_div<cpow(SIG, K)>(P[i]) + (long long)(D - K) * R);
+  });
+  return u + (long long)D * R - best;
 }
 
 // Every partial sum a head tuple of the thread may need.  With SYM only heads
@@ -321,12 +424,96 @@ __device__ __forceinline__ long long state_w(long long u, long long s_all,
 // ---------------------------------------------------------------------------
 // Kernels.
 
+// f_mode = 1 bodies (every non-empty advance set; an extension the paper does
+// not use, see the oracle's reading R9)
+template <int SIG, int D, bool SYM, bool INCR, bool CG>
+__device__ __forceinline__ void generic_sweep_thread_fall(const SweepParams& p, unsigned long long t, long long& best_v,
+                                                          unsigned long long& best_x) {
+  using G = Geo<SIG, D>;
+  constexpr int NPA = G::NPA;
+  const unsigned long long nt = p.n_tail;
+  const unsigned long long n_total = nt * G::SD;
+  unsigned long long S[D];
+  tail_fields<SIG, D>(t, p.h, S);
+  long long s_all = 0;
+  {
+    const long long* vd = p.prev[D - 1];
+    const unsigned long long b = t * G::SD;
+    static_for<0, (int)G::SD>([&](auto c) { s_all += ld_vec<CG>(vd + b + decltype(c)::value); });
+  }
+  long long P[NPA];
+  all_partials_fall<SIG, D, SYM, false, CG>(p.prev, S, nt, n_total, P);
+  auto emit = [&](auto Hc, unsigned long long tt, const auto& PP) {
+    constexpr int H = decltype(Hc)::value;
+    const long long val = state_value_fall<SIG, D, H>(s_all, PP, p.one);
+    const unsigned long long x = (unsigned long long)H * nt + tt;
+    if constexpr (INCR) {
+      const long long inc = val - ld_vec<CG>(p.prev[0] + x);
+      if (red_better(inc, x, best_v, best_x, p.r_mode)) best_v = inc, best_x = x;
+    }
+    p.out[x] = val;
+  };
+  constexpr int NH = SYM ? (int)(G::SD / SIG) : (int)G::SD;
+  static_for<0, NH>([&](auto Hc) { emit(Hc, t, P); });
+  if constexpr (SYM) {
+    const unsigned long long tu = nt - 1 - t;
+    unsigned long long SU[D];
+    tail_fields<SIG, D>(tu, p.h, SU);
+    long long PU[NPA];
+    all_partials_fall<SIG, D, true, true, CG>(p.prev, SU, nt, n_total, PU);
+    static_for<0, NH>([&](auto Hc) { emit(Hc, tu, PU); });
+  }
+}
+
+template <int SIG, int D, bool SYM, bool CG>
+__device__ __forceinline__ void generic_check_thread_fall(const CheckParams& p, long long R, unsigned long long t,
+                                                          long long& best) {
+  using G = Geo<SIG, D>;
+  constexpr int NPA = G::NPA;
+  const unsigned long long nt = p.n_tail;
+  const unsigned long long n_total = nt * G::SD;
+  const long long* prev[kMaxD];
+#pragma unroll
+  for (int k = 0; k < D; ++k) prev[k] = p.u;
+  unsigned long long S[D];
+  tail_fields<SIG, D>(t, p.h, S);
+  long long s_all = 0;
+  {
+    const unsigned long long b = t * G::SD;
+    static_for<0, (int)G::SD>([&](auto c) { s_all += ld_vec<CG>(p.u + b + decltype(c)::value); });
+  }
+  long long P[NPA];
+  all_partials_fall<SIG, D, SYM, false, CG>(prev, S, nt, n_total, P);
+  constexpr int NH = SYM ? (int)(G::SD / SIG) : (int)G::SD;
+  static_for<0, NH>([&](auto Hc) {
+    constexpr int H = decltype(Hc)::value;
+    const unsigned long long x = (unsigned long long)H * nt + t;
+    best = max(best, state_w_fall<SIG, D, H>(ld_vec<CG>(p.u + x), s_all, P, p.one, R));
+  });
+  if constexpr (SYM) {
+    const unsigned long long tu = nt - 1 - t;
+    unsigned long long SU[D];
+    tail_fields<SIG, D>(tu, p.h, SU);
+    long long PU[NPA];
+    all_partials_fall<SIG, D, true, true, CG>(prev, SU, nt, n_total, PU);
+    static_for<0, NH>([&](auto Hc) {
+      constexpr int H = decltype(Hc)::value;
+      const unsigned long long x = (unsigned long long)H * nt + tu;
+      best = max(best, state_w_fall<SIG, D, H>(ld_vec<CG>(p.u + x), s_all, PU, p.one, R));
+    });
+  }
+}
+
 // One thread's share of a sweep: tail tuple t (with SYM also its complement)
 // and every head tuple stored for it.  INCR folds the increment of each state
 // into (best_v, best_x).
-template <int SIG, int D, bool SYM, bool INCR, bool CG = false>
+template <int SIG, int D, bool SYM, bool INCR, bool CG = false, bool FALL = false>
 __device__ __forceinline__ void generic_sweep_thread(const SweepParams& p, unsigned long long t, long long& best_v,
                                                      unsigned long long& best_x) {
+  if constexpr (FALL) {
+    generic_sweep_thread_fall<SIG, D, SYM, INCR, CG>(p, t, best_v, best_x);
+    return;
+  }
   using G = Geo<SIG, D>;
   const unsigned long long nt = p.n_tail;
   const unsigned long long n_total = nt * G::SD;
@@ -365,9 +552,13 @@ __device__ __forceinline__ void generic_sweep_thread(const SweepParams& p, unsig
 }
 
 // One thread's share of a check: max of W over the states it owns.
-template <int SIG, int D, bool SYM, bool CG = false>
+template <int SIG, int D, bool SYM, bool CG = false, bool FALL = false>
 __device__ __forceinline__ void generic_check_thread(const CheckParams& p, long long R, unsigned long long t,
                                                      long long& best) {
+  if constexpr (FALL) {
+    generic_check_thread_fall<SIG, D, SYM, CG>(p, R, t, best);
+    return;
+  }
   using G = Geo<SIG, D>;
   const unsigned long long nt = p.n_tail;
   const unsigned long long n_total = nt * G::SD;
@@ -409,51 +600,52 @@ __host__ __device__ inline unsigned long long generic_threads(unsigned long long
   return SYM ? n_tail / 2 : n_tail;
 }
 
-template <int SIG, int D, bool SYM, bool INCR>
+template <int SIG, int D, bool SYM, bool INCR, bool FALL = false>
 __global__ void __launch_bounds__(kBlock) sweep_generic_kernel(SweepParams p) {
   const unsigned long long n_threads = generic_threads<SIG, D, SYM>(p.n_tail);
   long long best_v = p.r_mode ? LLONG_MIN : LLONG_MAX;
   unsigned long long best_x = ULLONG_MAX;
   for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < n_threads;
        t += (unsigned long long)gridDim.x * blockDim.x)
-    generic_sweep_thread<SIG, D, SYM, INCR>(p, t, best_v, best_x);
+    generic_sweep_thread<SIG, D, SYM, INCR, false, FALL>(p, t, best_v, best_x);
   if constexpr (INCR) block_reduce_arg(best_v, best_x, p.r_mode, p.partials);
 }
 
-template <int SIG, int D, bool SYM>
+template <int SIG, int D, bool SYM, bool FALL = false>
 __global__ void __launch_bounds__(kBlock) check_generic_kernel(CheckParams p) {
   const unsigned long long n_threads = generic_threads<SIG, D, SYM>(p.n_tail);
   const long long R = p.R_from_state ? p.state->R : p.R;
   long long best = LLONG_MIN;
   for (unsigned long long t = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; t < n_threads;
        t += (unsigned long long)gridDim.x * blockDim.x)
-    generic_check_thread<SIG, D, SYM>(p, R, t, best);
+    generic_check_thread<SIG, D, SYM, false, FALL>(p, R, t, best);
   block_reduce_max(best, p.partials);
 }
 
-template <int SIG, int D, bool SYM>
+template <int SIG, int D, bool SYM, bool FALL = false>
 void launch_sweep_generic(const SweepParams& p, int grid, cudaStream_t s) {
   if (p.incr)
-    sweep_generic_kernel<SIG, D, SYM, true><<<grid, kBlock, 0, s>>>(p);
+    sweep_generic_kernel<SIG, D, SYM, true, FALL><<<grid, kBlock, 0, s>>>(p);
   else
-    sweep_generic_kernel<SIG, D, SYM, false><<<grid, kBlock, 0, s>>>(p);
+    sweep_generic_kernel<SIG, D, SYM, false, FALL><<<grid, kBlock, 0, s>>>(p);
 }
 
-template <int SIG, int D, bool SYM>
+template <int SIG, int D, bool SYM, bool FALL = false>
 void launch_check_generic(const CheckParams& p, int grid, cudaStream_t s) {
-  check_generic_kernel<SIG, D, SYM><<<grid, kBlock, 0, s>>>(p);
+  check_generic_kernel<SIG, D, SYM, FALL><<<grid, kBlock, 0, s>>>(p);
 }
 
-template <int SIG, int D, bool SYM>
+template <int SIG, int D, bool SYM, bool FALL = false>
 KernelSet make_generic_set() {
   KernelSet k{};
   k.sigma = SIG;
   k.d = D;
   k.sym = SYM ? 1 : 0;
-  k.sweep = &launch_sweep_generic<SIG, D, SYM>;
-  k.check = &launch_check_generic<SIG, D, SYM>;
-  k.sweep_fn = (const void*)&sweep_generic_kernel<SIG, D, SYM, true>;
-  k.check_fn = (const void*)&check_generic_kernel<SIG, D, SYM>;
+  k.f_mode = FALL ? 1 : 0;
+  k.sweep = &launch_sweep_generic<SIG, D, SYM, FALL>;
+  k.check = &launch_check_generic<SIG, D, SYM, FALL>;
+  k.sweep_fn = (const void*)&sweep_generic_kernel<SIG, D, SYM, true, FALL>;
+  k.check_fn = (const void*)&check_generic_kernel<SIG, D, SYM, FALL>;
   k.tails_per_thread = SYM ? 2 : 1;
   k.sweep_algo_bytes = 8 * (D + 1);
   k.check_algo_bytes = 8;

@@ -73,10 +73,14 @@ def test_bad_options_rejected(L):
         binding.lcs_bound_create(2, 2, 3, o)
     assert e.value.status == binding.LCS_EINVAL
     o = binding.lcs_bound_default_opts()
-    o.f_mode = 1
+    o.f_mode = 1  # every non-empty advance set: compiled for sigma = 2 (d = 2, 3) and (3, 2) only
+    with pytest.raises(binding.LcsError) as e:
+        binding.lcs_bound_create(4, 2, 3, o)
+    assert e.value.status == binding.LCS_EUNSUPPORTED
+    o.f_mode = 2
     with pytest.raises(binding.LcsError) as e:
         binding.lcs_bound_create(2, 2, 3, o)
-    assert e.value.status == binding.LCS_EUNSUPPORTED
+    assert e.value.status == binding.LCS_EINVAL
 
 
 def test_null_handle_calls_fail_cleanly(L):

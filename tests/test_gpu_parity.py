@@ -251,3 +251,35 @@ def test_timing_stats(lb):
     with lb.LcsBound(2, 2, 5, timing=1) as hnd:
         hnd.iterate(4)
         assert hnd.stats()["sweep_bytes"] == 4 * 24 * (4 ** 5 // 2)
+
+
+# ---------------------------------------------------------------------------
+# f_mode = 1: the max over every non-empty advance set (an extension the paper
+# does not use; parity against the oracle's plain definition of it)
+
+FALL_SHAPES = [(2, 2, 1), (2, 2, 4), (2, 3, 1), (2, 3, 3), (3, 2, 1), (3, 2, 3)]
+
+
+@pytest.mark.parametrize("s,d,h", FALL_SHAPES)
+def test_all_subsets_sweep_bit_exact(lb, torch_mod, orc, s, d, h):
+    torch = torch_mod
+    vs = inputs.random_history(s, d, h, seed=300 + 7 * h + d + s)
+    want = orc.F(s, d, h, vs, arith="fx", f_mode=1)
+    out = torch.empty(want.size, dtype=torch.int64, device="cuda")
+    lb.lcs_sweep_fx(s, d, h, [torch.from_numpy(v).cuda() for v in vs], out, f_mode=1)
+    torch.cuda.synchronize()
+    assert np.array_equal(out.cpu().numpy(), want)
+
+
+@pytest.mark.parametrize("s,d,h,sym", [(2, 2, 5, 1), (2, 2, 4, 0), (2, 3, 3, 1), (2, 3, 3, 0), (3, 2, 3, 0)])
+def test_all_subsets_run_bit_exact(lb, orc, s, d, h, sym):
+    iters, ce = 40, 7
+    want = orc.run(s, d, h, iters, arith="fx", check_every=ce, f_mode=1)
+    with lb.LcsBound(s, d, h, check_every=ce, symmetry=sym, f_mode=1) as hnd:
+        hnd.iterate(iters)
+        rep = hnd.report()
+        for k in range(d):
+            assert np.array_equal(hnd.export_fx(k), want["iterates"][k])
+        assert (rep["R"], rep["argmin"], rep["E"], rep["r"], rep["eps"]) == (
+            want["R"], want["argmin"], want["E"], want["r"], want["eps"])
+        assert hnd.read()[0] == want["bound_rd"]
