@@ -31,21 +31,11 @@
 
 #include "../../include/lcs_bound.h"
 #include "lcs_common.h"
+#include "mlp_net.h"
 
 namespace lcs {
 
 void record_error(const char* msg);
-
-constexpr int kHin = 12;                 // encoded positions per string
-constexpr int kFeat = 4 * kHin + 1;      // 49
-constexpr int kHid = 256;
-constexpr long long kOffW1 = 0;
-constexpr long long kOffB1 = kOffW1 + (long long)kHid * kFeat;
-constexpr long long kOffW2 = kOffB1 + kHid;
-constexpr long long kOffB2 = kOffW2 + (long long)kHid * kHid;
-constexpr long long kOffW3 = kOffB2 + kHid;
-constexpr long long kOffB3 = kOffW3 + kHid;
-constexpr long long kNParams = kOffB3 + 1;
 
 static lcs_status mfail(lcs_status st, const char* fmt, ...) {
   char buf[512];
@@ -63,37 +53,6 @@ static lcs_status mfail(lcs_status st, const char* fmt, ...) {
     if (e_ != cudaSuccess) return mfail(LCS_ECUDA, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), \
                                         __FILE__, __LINE__);                                              \
   } while (0)
-
-// ---------------------------------------------------------------------------
-// features
-
-__host__ __device__ inline unsigned long long mlp_canonical(unsigned long long x, int h) {
-  const unsigned long long n1 = (h >= 32) ? ~0ull : ((1ull << (2 * h)) - 1);
-  const unsigned long long c = n1 - x;
-  const unsigned long long w = ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
-  const unsigned long long wc = n1 - w;
-  unsigned long long m = x < c ? x : c;
-  m = m < w ? m : w;
-  return m < wc ? m : wc;
-}
-
-// indices of the active one-hot features (2 per encoded position)
-__device__ __forceinline__ int mlp_active(unsigned long long x, int h, int* idx) {
-  x = mlp_canonical(x, h);
-  const int np = h < kHin ? h : kHin;
-  for (int p = 0; p < np; ++p) {
-    const unsigned pair = (unsigned)((x >> (2 * (h - 1 - p))) & 3ull);
-    idx[2 * p] = 4 * p + (int)(pair >> 1);
-    idx[2 * p + 1] = 4 * p + 2 + (int)(pair & 1u);
-  }
-  return 2 * np;
-}
-
-__device__ __forceinline__ float gelu_f(float z) { return 0.5f * z * (1.0f + erff(z * 0.70710678118654752f)); }
-
-__device__ __forceinline__ float gelu_grad_f(float z) {
-  return 0.5f * (1.0f + erff(z * 0.70710678118654752f)) + z * expf(-0.5f * z * z) * 0.39894228040143268f;
-}
 
 // ---------------------------------------------------------------------------
 // kernels
@@ -333,6 +292,19 @@ __global__ void mlp_head_bias_kernel(const float* __restrict__ P, const float* _
     float s = 0.f;
     for (int w = 0; w < kHid / 32; ++w) s += red[w];
     y[r] = s + P[kOffB3];
+  }
+}
+
+// the prefix-truncation lift (the non-learned control of the warm start):
+// dst[x] = src[x >> 2 (h_to - h_from)] - src[0], i.e. the value of the tuple
+// cut to its first h_from letters, as doubles in units; both full length
+__global__ void lift_prefix_kernel(const long long* __restrict__ src, int shift, long long n_to, double scale,
+                                   double r_hat, double* __restrict__ newest, double* __restrict__ older) {
+  const long long ref = src[0];
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_to; x += (long long)gridDim.x * blockDim.x) {
+    const double u = (double)(src[x >> shift] - ref) * scale;
+    older[x] = u;
+    newest[x] = u + r_hat;
   }
 }
 
@@ -660,6 +632,19 @@ lcs_status lcs_mlp_start_vectors(lcs_mlp_t* M, int h, double r_hat, double* newe
     M_CUDA(cudaGetLastError());
   }
   M_CUDA(cudaStreamSynchronize(M->stream));
+  return LCS_OK;
+}
+
+lcs_status lcs_lift_prefix(int h_from, int h_to, const int64_t* src_dev, int frac_bits, double r_hat,
+                           double* newest_dev, double* older_dev) {
+  if (!src_dev || !newest_dev || !older_dev || h_from < 1 || h_to < h_from || h_to > 16)
+    return mfail(LCS_EINVAL, "bad argument");
+  if (frac_bits == 0) frac_bits = 44;
+  const long long n_to = 1ll << (2 * h_to);
+  lift_prefix_kernel<<<4096, 256>>>((const long long*)src_dev, 2 * (h_to - h_from), n_to,
+                                    std::ldexp(1.0, -frac_bits), r_hat, newest_dev, older_dev);
+  M_CUDA(cudaGetLastError());
+  M_CUDA(cudaDeviceSynchronize());
   return LCS_OK;
 }
 
