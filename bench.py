@@ -374,6 +374,13 @@ def run_warm(args, cfg, world, rank, local_rank):
     t0 = time.perf_counter()
     mlp.start_vectors(H, r_hat, newest, older)
     t_infer = time.perf_counter() - t0
+    dummy = torch.empty(1, dtype=torch.float32, device="cuda")
+    t_tab = []
+    for _ in range(3):  # the tensor-core table kernel alone (the gather reads it for each state)
+        sync()
+        t0 = time.perf_counter()
+        mlp.predict_bf16(H, 0, 0, dummy)
+        t_tab.append(time.perf_counter() - t0)
     it_mlp, t_mlp, b_mlp = run_to(target, start=[newest, older])
 
     sync()
@@ -393,6 +400,7 @@ def run_warm(args, cfg, world, rank, local_rank):
         "zero_start": {"iterations": it_zero, "seconds": t_zero, "bound": b_zero},
         "truncation_lift": {"iterations": it_lift, "seconds": t_lift + t_lift_run, "bound": b_lift},
         "mlp": {"iterations": it_mlp, "seconds_iterating": t_mlp, "seconds_inference_bf16": t_infer,
+                "seconds_table_kernel_min_of_3": min(t_tab), "table_rows": 2 ** (2 * min(H, 12) - 1),
                 "seconds_total_with_inference": t_infer + t_mlp, "bound": b_mlp,
                 "train_seconds": t_train, "train_steps": cfg["train_steps"], "loss_before": loss0,
                 "loss_after": loss, "training_data_seconds": t_data},

@@ -285,12 +285,18 @@ lcs_status lcs_mlp_train(lcs_mlp_t* m, int n_sets, const int64_t* const* vectors
                          int batch, float lr, uint64_t seed, int frac_bits, float* last_loss);
 /* predictions (units) for n device states of length h into out_dev (device) */
 lcs_status lcs_mlp_predict(lcs_mlp_t* m, int h, int64_t n, const int64_t* states_dev, float* out_dev);
-/* the same predictions with BF16 inference (the 256 x 256 layer on the
- * tensor cores, bf16 operands, fp32 accumulation) for the consecutive states
- * base .. base+n-1 */
+/* the same predictions with BF16 inference for the consecutive states
+ * base .. base+n-1 (base + n <= 4^h).  A state enters the network only
+ * through the first min(h, 12) positions of its canonical form, so one fused
+ * tensor-core kernel (tcgen05: layer 1 and GELU on the CUDA cores, the
+ * 256 x 256 layer with bf16 operands and fp32 accumulators in tensor memory,
+ * bias, GELU and head in the epilogue) evaluates a table over those prefixes
+ * (2^(2 min(h,12) - 1) rows) and a gather reads it for each state.
+ * Synchronous.  LCS_ETIMEOUT if a bounded wait on the tensor core ran out. */
 lcs_status lcs_mlp_predict_bf16(lcs_mlp_t* m, int h, uint64_t base, int64_t n, float* out_dev);
-/* a start for lcs_bound_set_start (device doubles, 4^h values each), by BF16
- * inference: older = u_hat, newest = u_hat + r_hat.  Synchronous. */
+/* a start for lcs_bound_set_start (device doubles, 4^h values each, h <= 16),
+ * from the same BF16 table: older = u_hat, newest = u_hat + r_hat.
+ * Synchronous. */
 lcs_status lcs_mlp_start_vectors(lcs_mlp_t* m, int h, double r_hat, double* newest_dev, double* older_dev);
 void lcs_mlp_destroy(lcs_mlp_t* m);
 

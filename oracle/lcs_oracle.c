@@ -51,7 +51,9 @@
  *   R8  The triplet test uses ">=", so a later iteration wins ties.
  *   R9  f_mode = 1 (an extension the paper does not use): the max runs over
  *       every non-empty set of advanced strings; for equal heads the full set
- *       carries the +1 of the match.  Parity unpinned by the paper.
+ *       carries the +1 of the match.  The paper prints no value for it;
+ *       it is pinned by brute force instead: every candidate drops heads,
+ *       which can only lower the LCS, so F <= F_all <= W_n.
  */
 #include <math.h>
 #include <stdint.h>

@@ -82,3 +82,22 @@ def loss_and_grads(params, X, t):
     g["W1"] = dZ1.T @ X
     g["b1"] = dZ1.sum(axis=0)
     return loss, g
+
+
+def to_bf16(a: np.ndarray) -> np.ndarray:
+    """Round to bfloat16 (round to nearest, ties to even) through float32; returns float64."""
+    f = np.asarray(a, dtype=np.float32)
+    bits = f.view(np.uint32).astype(np.uint64)
+    bits = (bits + 0x7FFF + ((bits >> 16) & 1)) & 0xFFFF0000
+    return bits.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def forward_bf16(params, X):
+    """BF16 inference as the tensor-core path defines it: the first layer and
+    GELU in full precision, its output and W2 rounded to bfloat16, the 256 x 256
+    product accumulated exactly (float64 here), then bias, GELU and head in
+    full precision."""
+    W1, b1, W2, b2, w3, b3 = (params[k] for k in ("W1", "b1", "W2", "b2", "w3", "b3"))
+    A1 = to_bf16(gelu(X @ W1.T + b1))
+    Z2 = A1 @ to_bf16(W2).T + b2
+    return gelu(Z2) @ w3 + b3

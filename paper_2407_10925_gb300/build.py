@@ -27,6 +27,7 @@ SOURCES = [
     "kernels_s2d2.cu",
     "batch.cu",
     "mlp.cu",
+    "mlp_tc.cu",
     "fp32.cu",
 ]
 
@@ -75,8 +76,7 @@ def build(force: bool = False, verbose: bool = False) -> str:
     with cf.ThreadPoolExecutor(max_workers=min(len(SOURCES), os.cpu_count() or 4)) as ex:
         objs = list(ex.map(compile_one, SOURCES))
     tmp = LIB + f".tmp{os.getpid()}"
-    cuda_lib = os.path.join(os.path.dirname(os.path.dirname(nvcc)), "lib64")
-    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs, f"-L{cuda_lib}", "-lcublas", "-Xlinker", f"-rpath={cuda_lib}"]
+    cmd = [nvcc, *ARCH, "-shared", "-o", tmp, *objs]
     r = subprocess.run(cmd, capture_output=True, text=True)
     if r.returncode != 0:
         raise RuntimeError(f"nvcc link failed:\n{r.stdout}\n{r.stderr}")

@@ -26,7 +26,6 @@
 #include <cstring>
 #include <vector>
 
-#include <cublas_v2.h>
 #include <cuda_bf16.h>
 
 #include "../../include/lcs_bound.h"
@@ -36,6 +35,9 @@
 namespace lcs {
 
 void record_error(const char* msg);
+int mlp_table_rows(int h);
+size_t mlp_w2c_bytes();
+cudaError_t mlp_table_tc(const float* P, int h, float* table, void* w2c, int* err_dev, cudaStream_t s);
 
 static lcs_status mfail(lcs_status st, const char* fmt, ...) {
   char buf[512];
@@ -256,43 +258,23 @@ __global__ void mlp_to_start_kernel(const float* __restrict__ y, long long n, lo
   }
 }
 
-// BF16 inference, first layer: rows are the states base + i (i < n); A1 in bf16
-__global__ void mlp_layer1_bf16_kernel(const float* __restrict__ P, unsigned long long base, int h, int n,
-                                       __nv_bfloat16* __restrict__ A1) {
-  const int r = blockIdx.x;
-  if (r >= n) return;
-  __shared__ int idx[2 * kHin];
-  __shared__ int cnt;
-  if (threadIdx.x == 0) cnt = mlp_active(base + (unsigned long long)r, h, idx);
-  __syncthreads();
-  const int j = threadIdx.x;
-  const float* W1 = P + kOffW1;
-  float z = P[kOffB1 + j] + (float)h * (1.0f / 16.0f) * W1[j * kFeat + (kFeat - 1)];
-  for (int i = 0; i < cnt; ++i) z += W1[j * kFeat + idx[i]];
-  A1[(long long)r * kHid + j] = __float2bfloat16_rn(gelu_f(z));
-}
-
-__global__ void mlp_to_bf16_kernel(const float* __restrict__ x, long long n, __nv_bfloat16* __restrict__ y) {
-  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
-    y[i] = __float2bfloat16_rn(x[i]);
-}
-
-// BF16 inference, head: y = w3 . GELU(Z2 + b2) + b3 (Z2 without bias from the GEMM)
-__global__ void mlp_head_bias_kernel(const float* __restrict__ P, const float* __restrict__ Z2, int n,
-                                     float* __restrict__ y) {
-  const int r = blockIdx.x;
-  if (r >= n) return;
-  const int j = threadIdx.x;
-  float v = gelu_f(Z2[(long long)r * kHid + j] + P[kOffB2 + j]) * P[kOffW3 + j];
-  __shared__ float red[kHid / 32];
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-  if ((j & 31) == 0) red[j >> 5] = v;
-  __syncthreads();
-  if (j == 0) {
-    float s = 0.f;
-    for (int w = 0; w < kHid / 32; ++w) s += red[w];
-    y[r] = s + P[kOffB3];
+// full-length vectors from the prediction table (mlp_tc.cu): the value of a
+// state is the table entry of its canonical form's first np positions
+__global__ void mlp_table_start_kernel(const float* __restrict__ T, int h, int np, long long n, double r_hat,
+                                       double* __restrict__ newest, double* __restrict__ older) {
+  const int shift = 2 * (h - np);
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n; x += (long long)gridDim.x * blockDim.x) {
+    const double u = (double)T[mlp_canonical((unsigned long long)x, h) >> shift];
+    older[x] = u;
+    newest[x] = u + r_hat;
   }
+}
+
+__global__ void mlp_table_predict_kernel(const float* __restrict__ T, int h, int np, unsigned long long base,
+                                         long long n, float* __restrict__ out) {
+  const int shift = 2 * (h - np);
+  for (long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (long long)gridDim.x * blockDim.x)
+    out[i] = T[mlp_canonical(base + (unsigned long long)i, h) >> shift];
 }
 
 // the prefix-truncation lift (the non-learned control of the warm start):
@@ -338,13 +320,10 @@ struct lcs_mlp {
   int* hs;
   TrainSet* sets;
   cudaStream_t stream;
-  // BF16 inference
-  cublasHandle_t cublas;
-  __nv_bfloat16* W2h;
-  __nv_bfloat16* A1h;
-  float* Zinf;
-  float* yinf;
-  int inf_cap;
+  // BF16 inference: W2 in bf16 (core-matrix layout), the prediction table, an error flag
+  void* W2c;
+  float* table;
+  int* err;
 };
 
 static unsigned long long host_splitmix(unsigned long long seed, unsigned long long i) {
@@ -421,8 +400,7 @@ void lcs_mlp_destroy(lcs_mlp_t* M) {
   if (!M) return;
   if (M->stream) cudaStreamSynchronize(M->stream);
   void* ptrs[] = {M->P, M->G, M->Mm, M->V, M->Z1, M->A1, M->Z2, M->A2, M->y, M->t, M->dy, M->dZ2, M->dA1,
-                  M->states, M->mask, M->hs, M->sets, M->W2h, M->A1h, M->Zinf, M->yinf};
-  if (M->cublas) cublasDestroy(M->cublas);
+                  M->states, M->mask, M->hs, M->sets, M->W2c, M->table, M->err};
   for (void* p : ptrs) cudaFree(p);
   if (M->stream) cudaStreamDestroy(M->stream);
   delete M;
@@ -574,45 +552,18 @@ lcs_status lcs_mlp_train(lcs_mlp_t* M, int n_sets, const int64_t* const* vectors
   return LCS_OK;
 }
 
-// BF16 inference of rows base .. base+m-1 (states of length h) into M->yinf:
-// layer 1 and the head in the kernels above, the 256 x 256 layer as a plain
-// bf16 x bf16 -> fp32 GEMM on the tensor cores (cuBLAS)
-static lcs_status infer_bf16(lcs_mlp* M, int h, unsigned long long base, int m) {
-  cudaStream_t s = M->stream;
-  mlp_layer1_bf16_kernel<<<m, kHid, 0, s>>>(M->P, base, h, m, M->A1h);
-  M_CUDA(cudaGetLastError());
-  const float one = 1.0f, zero = 0.0f;
-  // column-major view: Z2^T (256 x m) = W2 (op T of its row-major storage) * A1^T
-  cublasStatus_t cs = cublasGemmEx(M->cublas, CUBLAS_OP_T, CUBLAS_OP_N, kHid, m, kHid, &one, M->W2h, CUDA_R_16BF,
-                                   kHid, M->A1h, CUDA_R_16BF, kHid, &zero, M->Zinf, CUDA_R_32F, kHid,
-                                   CUBLAS_COMPUTE_32F, CUBLAS_GEMM_DEFAULT);
-  if (cs != CUBLAS_STATUS_SUCCESS) return mfail(LCS_ECUDA, "cublasGemmEx failed (%d)", (int)cs);
-  mlp_head_bias_kernel<<<m, kHid, 0, s>>>(M->P, M->Zinf, m, M->yinf);
-  M_CUDA(cudaGetLastError());
-  return LCS_OK;
-}
-
-static lcs_status ensure_inference(lcs_mlp* M, int rows) {
-  if (!M->cublas) {
-    if (cublasCreate(&M->cublas) != CUBLAS_STATUS_SUCCESS) return mfail(LCS_ECUDA, "cublasCreate failed");
-    if (cublasSetStream(M->cublas, M->stream) != CUBLAS_STATUS_SUCCESS) return mfail(LCS_ECUDA, "cublasSetStream");
-    M_CUDA(cudaMalloc(&M->W2h, sizeof(__nv_bfloat16) * kHid * kHid));
+// the BF16 prediction table of shape h (mlp_tc.cu) into M->table
+static lcs_status build_table(lcs_mlp* M, int h) {
+  if (!M->W2c) {
+    M_CUDA(cudaMalloc(&M->W2c, mlp_w2c_bytes()));
+    M_CUDA(cudaMalloc(&M->table, sizeof(float) * (size_t)mlp_table_rows(kHin)));
+    M_CUDA(cudaMalloc(&M->err, sizeof(int)));
   }
-  if (rows > M->inf_cap) {
-    cudaFree(M->A1h);
-    cudaFree(M->Zinf);
-    cudaFree(M->yinf);
-    M->A1h = nullptr;
-    M->Zinf = nullptr;
-    M->yinf = nullptr;
-    M_CUDA(cudaMalloc(&M->A1h, sizeof(__nv_bfloat16) * (size_t)rows * kHid));
-    M_CUDA(cudaMalloc(&M->Zinf, sizeof(float) * (size_t)rows * kHid));
-    M_CUDA(cudaMalloc(&M->yinf, sizeof(float) * (size_t)rows));
-    M->inf_cap = rows;
-  }
-  // the current FP32 weights of the 256 x 256 layer, rounded to bf16
-  mlp_to_bf16_kernel<<<256, 256, 0, M->stream>>>(M->P + kOffW2, (long long)kHid * kHid, M->W2h);
-  M_CUDA(cudaGetLastError());
+  M_CUDA(mlp_table_tc(M->P, h, M->table, M->W2c, M->err, M->stream));
+  int err = 0;
+  M_CUDA(cudaMemcpyAsync(&err, M->err, sizeof(int), cudaMemcpyDeviceToHost, M->stream));
+  M_CUDA(cudaStreamSynchronize(M->stream));
+  if (err) return mfail(LCS_ETIMEOUT, "tensor-core inference: a wait on the tensor core ran out");
   return LCS_OK;
 }
 
@@ -620,17 +571,11 @@ static lcs_status ensure_inference(lcs_mlp* M, int rows) {
 // of a start: older = u_hat, newest = u_hat + r_hat (device pointers)
 lcs_status lcs_mlp_start_vectors(lcs_mlp_t* M, int h, double r_hat, double* newest_dev, double* older_dev) {
   if (!M || !newest_dev || !older_dev || h < 1 || h > 16) return mfail(LCS_EINVAL, "bad argument");
-  const long long n = 1ll << (2 * h);
-  const int chunk = 1 << 22;
-  lcs_status st = ensure_inference(M, (int)std::min<long long>(n, chunk));
+  lcs_status st = build_table(M, h);
   if (st) return st;
-  for (long long off = 0; off < n; off += chunk) {
-    const int m = (int)std::min<long long>(chunk, n - off);
-    st = infer_bf16(M, h, (unsigned long long)off, m);
-    if (st) return st;
-    mlp_to_start_kernel<<<1024, 256, 0, M->stream>>>(M->yinf, m, off, r_hat, 2, newest_dev, older_dev);
-    M_CUDA(cudaGetLastError());
-  }
+  mlp_table_start_kernel<<<4096, 256, 0, M->stream>>>(M->table, h, std::min(h, kHin), 1ll << (2 * h), r_hat,
+                                                      newest_dev, older_dev);
+  M_CUDA(cudaGetLastError());
   M_CUDA(cudaStreamSynchronize(M->stream));
   return LCS_OK;
 }
@@ -651,14 +596,12 @@ lcs_status lcs_lift_prefix(int h_from, int h_to, const int64_t* src_dev, int fra
 // BF16 predictions for the consecutive states base .. base+n-1 (device output)
 lcs_status lcs_mlp_predict_bf16(lcs_mlp_t* M, int h, uint64_t base, int64_t n, float* out_dev) {
   if (!M || !out_dev || n < 0 || h < 1 || h > 31) return mfail(LCS_EINVAL, "bad argument");
-  const int chunk = 1 << 22;
-  lcs_status st = ensure_inference(M, (int)std::min<int64_t>(std::max<int64_t>(n, 1), chunk));
+  if (h < 32 && base + (uint64_t)n > (1ull << (2 * h)) && n > 0) return mfail(LCS_EINVAL, "states out of range");
+  lcs_status st = build_table(M, h);
   if (st) return st;
-  for (int64_t off = 0; off < n; off += chunk) {
-    const int m = (int)std::min<int64_t>(chunk, n - off);
-    st = infer_bf16(M, h, base + (uint64_t)off, m);
-    if (st) return st;
-    M_CUDA(cudaMemcpyAsync(out_dev + off, M->yinf, sizeof(float) * m, cudaMemcpyDeviceToDevice, M->stream));
+  if (n > 0) {
+    mlp_table_predict_kernel<<<2048, 256, 0, M->stream>>>(M->table, h, std::min(h, kHin), base, n, out_dev);
+    M_CUDA(cudaGetLastError());
   }
   M_CUDA(cudaStreamSynchronize(M->stream));
   return LCS_OK;

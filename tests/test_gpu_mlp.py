@@ -78,6 +78,60 @@ def test_predict_matches_reference(lb):
         assert np.max(np.abs(out.cpu().numpy() - y_ref)) <= 1e-4 * max(1.0, np.max(np.abs(y_ref)))
 
 
+@pytest.mark.parametrize("h,base,n", [(1, 0, 4), (5, 0, 4 ** 5), (9, 0, 4 ** 9), (12, 123456, 5000),
+                                      (14, 3 * 4 ** 13 + 777, 6000), (16, 4 ** 16 - 4096, 4096)])
+def test_predict_bf16_matches_reference(lb, h, base, n):
+    """Tensor-core inference (one fused kernel per prediction table, then a
+    gather) against the float64 network with the same two bf16 roundings,
+    and loosely against the unrounded network."""
+    import torch
+
+    with lb.LcsMlp(seed=7) as m:
+        P = _unflatten(m.get_params())
+        out = torch.empty(n, dtype=torch.float32, device="cuda")
+        m.predict_bf16(h, base, n, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().astype(np.float64)
+    rng = np.random.default_rng(h)
+    idx = np.unique(np.concatenate([rng.integers(0, n, size=min(n, 2500)), [0, n - 1]]))
+    states = base + idx.astype(np.int64)
+    X = omlp.features(states, h)
+    y_bf16 = omlp.forward_bf16(P, X)
+    y_ref, _ = omlp.forward(P, X)
+    scale = max(1e-3, float(np.max(np.abs(y_ref))))
+    err = np.abs(got[idx] - y_bf16)
+    # most rows differ by the fp32 accumulation order only; a first-layer
+    # activation whose fp32 and float64 values straddle a bf16 rounding
+    # boundary rounds one ulp (2^-8 relative) apart, which moves y by up to
+    # about 2^-8 |a| sum_j |w3_j W2_jk| ~ 5e-4 of its scale
+    assert np.median(err) <= 1e-6 * scale
+    assert np.max(err) <= 1e-3 * scale
+    assert np.max(np.abs(got[idx] - y_ref)) <= 2e-2 * scale
+
+
+def test_start_vectors_are_the_table_and_symmetric(lb):
+    """The start has the iterate's symmetries exactly and newest - older = r_hat."""
+    import torch
+
+    h, r_hat = 10, 0.390625
+    n = 4 ** h
+    with lb.LcsMlp(seed=8) as m:
+        newest = torch.empty(n, dtype=torch.float64, device="cuda")
+        older = torch.empty(n, dtype=torch.float64, device="cuda")
+        m.start_vectors(h, r_hat, newest, older)
+        pred = torch.empty(n, dtype=torch.float32, device="cuda")
+        m.predict_bf16(h, 0, n, pred)
+        torch.cuda.synchronize()
+    o = older.cpu().numpy()
+    assert np.array_equal(o, pred.cpu().numpy().astype(np.float64))
+    assert np.array_equal(newest.cpu().numpy(), o + r_hat)
+    x = np.arange(n, dtype=np.int64)
+    comp = (n - 1) - x
+    swap = ((x >> 1) & 0x5555555555555555) | ((x & 0x5555555555555555) << 1)
+    assert np.array_equal(o[comp], o)
+    assert np.array_equal(o[swap], o)
+
+
 def _converged(lb, h, iters=300):
     import torch
 

@@ -74,3 +74,30 @@ def test_gelu_is_the_erf_form():
     from math import erf, sqrt
 
     assert np.allclose(mlp.gelu(z), [0.5 * v * (1 + erf(v / sqrt(2))) for v in z], atol=1e-15)
+
+
+def test_bf16_rounding_is_nearest_even():
+    # bfloat16 keeps 8 significant bits: spacing 2^-7 in [1, 2)
+    vals = np.array([1.0, 1 + 2.0 ** -8, 1 + 3 * 2.0 ** -8, 1 + 2.0 ** -9, -2.5 - 2.0 ** -7, 0.0])
+    want = np.array([1.0, 1.0, 1 + 2 * 2.0 ** -7, 1.0, -2.5, 0.0])
+    # the two ties (1 + 2^-8 and 1 + 3 2^-8) go to the neighbour with an even last bit
+    assert np.array_equal(mlp.to_bf16(vals), want)
+    got = mlp.to_bf16(np.random.default_rng(0).normal(0, 100, 1000))
+    # every result is representable: the low 16 bits of its float32 are zero
+    assert np.all(got.astype(np.float32).view(np.uint32) & 0xFFFF == 0)
+
+
+def test_bf16_forward_differs_by_rounding_only():
+    P = _params(3)
+    X = mlp.features(np.random.default_rng(3).integers(0, 1 << 20, size=500), 10)
+    y, _ = mlp.forward(P, X)
+    yb = mlp.forward_bf16(P, X)
+    diff = np.max(np.abs(y - yb))
+    assert 0 < diff <= 1e-2 * np.max(np.abs(y))
+    # a first layer whose GELU output is representable (GELU(40) = 40) and
+    # parameters already in bfloat16: the rounded network is the network
+    P2 = {k: mlp.to_bf16(v) for k, v in P.items()}
+    P2["W1"] = np.zeros_like(P2["W1"])
+    P2["b1"] = np.full(mlp.HIDDEN, 40.0)
+    y2, _ = mlp.forward(P2, X)
+    assert np.array_equal(mlp.forward_bf16(P2, X), y2)

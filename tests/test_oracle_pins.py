@@ -212,6 +212,52 @@ def test_iterates_below_W(orc, brute_tables, case, arith):
             assert val <= W[n][x] + Fraction(1, 10 ** 12)
 
 
+@pytest.mark.parametrize("case", [c for c in BRUTE if c[1] <= 3])
+def test_all_subsets_F_between_F_and_W(orc, brute_tables, case):
+    """f_mode 1 (every non-empty advance set, +1 on the full set for equal
+    heads): each candidate drops the heads of some strings, a move that can
+    only lower the LCS, so F_all(W) <= W; its candidates include every N_z of
+    Alg. 1, so F(W) <= F_all(W); hence equality wherever F(W) = W."""
+    s, d, h, nm = case
+    W = brute_tables[case]
+    N = s ** (d * h)
+    K = 44
+    for n in range(d, nm + 1):
+        vs = [np.array([math.floor(W[n - k][x] * (1 << K)) for x in range(N)], dtype=np.int64)
+              for k in range(1, d + 1)]
+        F0 = orc.F(s, d, h, vs, arith="fx")
+        F1 = orc.F(s, d, h, vs, arith="fx", f_mode=1)
+        assert np.all(F1 >= F0)
+        for x in range(N):
+            assert Fraction(int(F1[x]), 1 << K) <= W[n][x]
+        assert min(W[n][x] - Fraction(int(F1[x]), 1 << K) for x in range(N)) < Fraction(4, 1 << K)
+
+
+@pytest.mark.parametrize("case", [c for c in BRUTE if c[1] <= 3])
+def test_all_subsets_iterates_below_W(orc, brute_tables, case):
+    s, d, h, nm = case
+    W = brute_tables[case]
+    for n in range(d, nm + 1):
+        v = orc.run(s, d, h, n - d + 1, f_mode=1)["iterates"][0]
+        v0 = orc.run(s, d, h, n - d + 1)["iterates"][0]
+        assert np.all(v >= v0)
+        for x in range(s ** (d * h)):
+            assert Fraction(int(v[x]), 1 << 44) <= W[n][x]
+
+
+def test_all_subsets_adds_candidates():
+    """On random arguments the extra advance sets win somewhere (the test above is not vacuous)."""
+    import oracle as orc_mod
+
+    rng = np.random.default_rng(5)
+    for s, d, h in [(2, 2, 3), (2, 3, 2), (3, 2, 2)]:
+        N = s ** (d * h)
+        vs = [rng.integers(-(1 << 46), 1 << 46, size=N, dtype=np.int64) for _ in range(d)]
+        F0 = orc_mod.F(s, d, h, vs, arith="fx")
+        F1 = orc_mod.F(s, d, h, vs, arith="fx", f_mode=1)
+        assert np.all(F1 >= F0) and np.any(F1 > F0)
+
+
 # ---------------------------------------------------------------------------
 # invariants of F and of the iteration
 
