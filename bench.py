@@ -36,6 +36,7 @@ BATCH_SHAPES = [(2, 2, 10), (2, 2, 12), (3, 2, 6), (3, 2, 7), (4, 2, 5), (2, 3, 
 CONFIGS = {
     "batch": dict(sigma=0, d=0, h=0, shapes=BATCH_SHAPES),
     "warm": dict(sigma=2, d=2, h=14, train_h=[10, 11, 12], ref_iters=4000, train_steps=3000),
+    "warm16": dict(sigma=2, d=2, h=16, train_h=[10, 11, 12], ref_iters=1000, train_steps=3000),
     "fp32": dict(sigma=0, d=0, h=0, shapes=[(2, 3, 8), (3, 2, 8)], iters=1500),
     "h16": dict(sigma=2, d=2, h=16),
     "h14": dict(sigma=2, d=2, h=14),
@@ -458,7 +459,7 @@ def main():
     if args.config == "batch":
         run_batch(args, cfg, world, rank, local_rank)
         return
-    if args.config == "warm":
+    if args.config in ("warm", "warm16"):
         run_warm(args, cfg, world, rank, local_rank)
         return
     if args.config == "fp32":

@@ -225,8 +225,9 @@ const char* lcs_bound_last_error(void);
  * the increment reduction, the check and the keep test).  The launch of each
  * distinct n is captured once in a CUDA graph and replayed.  opts as for
  * lcs_bound_create (keep_u unsupported).  At creation an autotuner times a few
- * iterations for each candidate grid size and item size and keeps the
- * fastest, then returns every vector to the zero start.
+ * iterations for each candidate grid size and item size, and the concurrent
+ * mode (lcs_bound_batch_set_mode), keeps the fastest, then returns every
+ * vector to the zero start.
  *
  * The grid barrier waits with a clock budget (about 2 s by default); if it
  * runs out the launch ends and the status LCS_ETIMEOUT is reported by the
@@ -246,9 +247,19 @@ typedef struct {
   int units_per_item;     /* tiles per work item chosen by the autotuner */
   int graph;              /* 1: launches replay a captured CUDA graph */
   double tuned_ms_per_iter;
-  int64_t launches;       /* persistent launches or graph replays so far */
+  int64_t launches;       /* persistent launches or graph replays so far (kernel launches in mode 1) */
+  int mode;               /* 0: one persistent launch; 1: concurrent single-instance kernels */
+  double persistent_ms_per_iter;  /* the autotuner's timings of both modes */
+  double concurrent_ms_per_iter;
 } lcs_bound_batch_info_t;
 lcs_status lcs_bound_batch_info(lcs_bound_t* hnd, lcs_bound_batch_info_t* out);
+/* Force the execution mode of a batch before its first iteration (LCS_EINVAL
+ * afterwards): 0 = the persistent launch with the autotuner's shape, 1 = each
+ * instance's single-instance kernels on a stream of its own, forked from and
+ * joined to the handle's stream, so the instances run concurrently.  Both
+ * modes compute the same iterates and bounds bit for bit; the autotuner
+ * times both at creation and keeps the faster. */
+lcs_status lcs_bound_batch_set_mode(lcs_bound_t* hnd, int mode);
 
 /* Set the grid barrier's clock budget in cycles (testing the timeout path);
  * also clears a previous LCS_ETIMEOUT status. */

@@ -14,6 +14,7 @@ from .binding import (  # noqa: F401
     lcs_bound_batch_info,
     lcs_bound_batch_read,
     lcs_bound_batch_report,
+    lcs_bound_batch_set_mode,
     lcs_bound_batch_set_spin_budget,
     lcs_bound_check_vector,
     lcs_bound_create,

@@ -73,6 +73,9 @@ class lcs_bound_batch_info_t(ctypes.Structure):
         ("graph", ctypes.c_int),
         ("tuned_ms_per_iter", ctypes.c_double),
         ("launches", ctypes.c_int64),
+        ("mode", ctypes.c_int),
+        ("persistent_ms_per_iter", ctypes.c_double),
+        ("concurrent_ms_per_iter", ctypes.c_double),
     ]
 
 
@@ -113,6 +116,7 @@ def lib():
                 "lcs_bound_batch_report": [vp, i32, P(lcs_bound_report)],
                 "lcs_bound_batch_export_fx": [vp, i32, i32, vp, i32],
                 "lcs_bound_batch_info": [vp, P(lcs_bound_batch_info_t)],
+                "lcs_bound_batch_set_mode": [vp, i32],
                 "lcs_bound_batch_set_spin_budget": [vp, i64],
                 "lcs_mlp_create": [u64, P(vp)],
                 "lcs_mlp_get_params": [vp, vp],
@@ -362,6 +366,10 @@ def lcs_bound_batch_export_fx(hnd, i: int, k: int, out):
     return out
 
 
+def lcs_bound_batch_set_mode(hnd, mode):
+    _check(lib().lcs_bound_batch_set_mode(hnd, mode), "lcs_bound_batch_set_mode")
+
+
 def lcs_bound_batch_info(hnd) -> dict:
     info = lcs_bound_batch_info_t()
     _check(lib().lcs_bound_batch_info(hnd, ctypes.byref(info)), "lcs_bound_batch_info")
@@ -422,6 +430,10 @@ class LcsBatch:
 
     def set_spin_budget(self, cycles):
         lcs_bound_batch_set_spin_budget(self.hnd, cycles)
+
+    def set_mode(self, mode):
+        """0: the persistent launch, 1: concurrent single-instance kernels (before the first iteration)."""
+        lcs_bound_batch_set_mode(self.hnd, mode)
 
 
 def lcs_fp32_experiment(sigma, d, h, n_iters, rho, newest_dev):

@@ -16,6 +16,15 @@
 // CTA records LCS_ETIMEOUT; every CTA checks that status at each barrier and
 // leaves, so a lost participant ends the launch with an error, not a hang.
 // Cooperative launch guarantees that all CTAs are resident together.
+//
+// Concurrent mode.  The persistent kernel carries every instance kind's body,
+// so its register count (and occupancy) is set by the heaviest kind.  The
+// alternative mode runs each instance's own single-instance kernels (the
+// ones lcs_bound_iterate uses) on a stream of its own, forked from and joined
+// to the handle's stream; the GPU overlaps the instances, and each kernel
+// keeps its own occupancy.  Both modes share the buffers, the device states
+// and the check schedule, so they give the same iterates and bounds bit for
+// bit; the autotuner times both and keeps the faster.
 #include <algorithm>
 #include <climits>
 #include <cmath>
@@ -358,6 +367,16 @@ __global__ void batch_init_kernel(DevState* st) {
 // ---------------------------------------------------------------------------
 // host side
 
+// one instance in the concurrent mode (work-list position r)
+struct ConcInst {
+  const KernelSet* ks;
+  int grid_sweep, grid_check;
+  RedPartial* partials;  // max(grid_sweep, grid_check) entries
+  cudaStream_t stream;
+  cudaEvent_t join;
+  int newest;            // ring slot of the newest iterate (host copy of the device ring state)
+};
+
 struct BatchState {
   int n;
   int slot[kMaxBatch];  // user index -> position in the work-list order
@@ -384,6 +403,10 @@ struct BatchState {
   int tune_grid_choice, tune_units_choice;
   double tuned_ms;
   long long launches;
+  int mode;  // 0 persistent launch, 1 concurrent single-instance kernels
+  double ms_persistent, ms_concurrent;
+  ConcInst conc[kMaxBatch];
+  cudaEvent_t fork;
 };
 
 static void* balloc(BatchState* B, size_t bytes) {
@@ -400,6 +423,14 @@ static void* balloc(BatchState* B, size_t bytes) {
 
 void batch_destroy(BatchState* B) {
   if (!B) return;
+  for (int r = 0; r < kMaxBatch; ++r) {
+    if (B->conc[r].stream) {
+      cudaStreamSynchronize(B->conc[r].stream);
+      cudaStreamDestroy(B->conc[r].stream);
+    }
+    if (B->conc[r].join) cudaEventDestroy(B->conc[r].join);
+  }
+  if (B->fork) cudaEventDestroy(B->fork);
   for (auto& g : B->graphs) cudaGraphExecDestroy(g.second);
   for (void* p : B->owned) {
     if (B->alloc) {
@@ -451,6 +482,113 @@ static lcs_status reset_zero(BatchState* B, cudaStream_t s) {
   B_CUDA(cudaMemcpyAsync(B->d_ctl, &c, sizeof c, cudaMemcpyHostToDevice, s));
   B_CUDA(cudaStreamSynchronize(s));
   B->iter_done_host = 0;
+  for (int r = 0; r < B->n; ++r) B->conc[r].newest = B->inst[r].d - 1;
+  return LCS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// concurrent mode
+
+// the single-instance kernel set of a batch kind
+static const KernelSet* conc_kernels(int kind) {
+  switch (kind) {
+    case BK_S2D2: return find_kernels(2, 2, 2);
+    case BK_G22S: return find_kernels(2, 2, 1);
+    case BK_G23S: return find_kernels(2, 3, 1);
+    case BK_G24S: return find_kernels(2, 4, 1);
+    case BK_G32: return find_kernels(3, 2, 0);
+    case BK_G42: return find_kernels(4, 2, 0);
+    case BK_G22: return find_kernels(2, 2, 0);
+    case BK_G23: return find_kernels(2, 3, 0);
+  }
+  return nullptr;
+}
+
+// one iteration of instance r on its stream: the sweep, and on a checked
+// iteration the increment reduction, the check and the keep test -- the
+// sequence lcs_bound_iterate issues for a single instance
+static lcs_status conc_step(BatchState* B, int r, long long it, bool check) {
+  ConcInst& c = B->conc[r];
+  const BatchInst& in = B->inst[r];
+  const int rows = in.rows;
+  SweepParams p{};
+  for (int k = 1; k <= in.d; ++k) p.prev[k - 1] = in.ring[(c.newest - (k - 1) + rows) % rows];
+  p.out = in.ring[(c.newest + 1) % rows];
+  p.n_tail = in.n_tail;
+  p.n_stored = in.n_stored;
+  p.h = in.h;
+  p.incr = check ? 1 : 0;
+  p.r_mode = B->r_mode;
+  p.one = B->one;
+  p.partials = c.partials;
+  c.ks->sweep(p, c.grid_sweep, c.stream);
+  B_CUDA(cudaGetLastError());
+  B->launches++;
+  if (check) {
+    launch_finalize_incr(c.partials, c.grid_sweep, B->r_mode, in.state, it, c.stream);
+    CheckParams q{};
+    q.u = p.out;
+    q.n_tail = in.n_tail;
+    q.n_stored = in.n_stored;
+    q.h = in.h;
+    q.one = B->one;
+    q.state = in.state;
+    q.R_from_state = 1;
+    q.R = 0;
+    q.partials = c.partials;
+    c.ks->check(q, c.grid_check, c.stream);
+    launch_finalize_check(c.partials, c.grid_check, in.state, it, c.stream);
+    B_CUDA(cudaGetLastError());
+    B->launches += 3;
+  }
+  c.newest = (c.newest + 1) % rows;
+  return LCS_OK;
+}
+
+// n_iters iterations of every instance, interleaved in rounds so that all
+// streams are fed while the host enqueues
+static lcs_status conc_iterate(BatchState* B, cudaStream_t s, long long n_iters) {
+  const long long call_end = B->iter_done_host + n_iters;
+  B_CUDA(cudaEventRecord(B->fork, s));
+  for (int r = 0; r < B->n; ++r) B_CUDA(cudaStreamWaitEvent(B->conc[r].stream, B->fork, 0));
+  const long long round = 16;
+  for (long long base = 0; base < n_iters; base += round) {
+    const long long m = std::min(round, n_iters - base);
+    for (int r = 0; r < B->n; ++r) {
+      for (long long j = 0; j < m; ++j) {
+        const long long it = B->iter_done_host + base + j + 1;
+        const bool check = (B->check_every > 0 && it % B->check_every == 0) || it == call_end;
+        lcs_status st = conc_step(B, r, it, check);
+        if (st) return st;
+      }
+    }
+  }
+  for (int r = 0; r < B->n; ++r) {
+    B_CUDA(cudaEventRecord(B->conc[r].join, B->conc[r].stream));
+    B_CUDA(cudaStreamWaitEvent(s, B->conc[r].join, 0));
+  }
+  B->iter_done_host = call_end;
+  return LCS_OK;
+}
+
+static lcs_status conc_setup(BatchState* B, int sms) {
+  B_CUDA(cudaEventCreateWithFlags(&B->fork, cudaEventDisableTiming));
+  for (int r = 0; r < B->n; ++r) {
+    ConcInst& c = B->conc[r];
+    const BatchInst& in = B->inst[r];
+    c.ks = conc_kernels(in.kind);
+    if (!c.ks) return bfail(LCS_EUNSUPPORTED, "no single-instance kernels for batch kind %d", in.kind);
+    // the grids lcs_bound_create picks for the same shape
+    const unsigned long long work =
+        in.kind == BK_S2D2 ? 2ull * in.tn * in.tn * (unsigned long long)kBlock : in.n_threads;
+    c.grid_sweep = grid_for_work(c.ks->sweep_fn, sms, work);
+    c.grid_check = grid_for_work(c.ks->check_fn, sms, work);
+    c.partials = (RedPartial*)balloc(B, sizeof(RedPartial) * (size_t)std::max(c.grid_sweep, c.grid_check));
+    if (!c.partials) return bfail(LCS_ENOMEM, "concurrent-mode partials");
+    B_CUDA(cudaStreamCreateWithFlags(&c.stream, cudaStreamNonBlocking));
+    B_CUDA(cudaEventCreateWithFlags(&c.join, cudaEventDisableTiming));
+    c.newest = in.d - 1;
+  }
   return LCS_OK;
 }
 
@@ -481,6 +619,7 @@ static lcs_status enqueue_call(BatchState* B, cudaStream_t s, long long n_iters)
 
 lcs_status batch_iterate(BatchState* B, cudaStream_t s, long long n_iters) {
   if (n_iters <= 0) return LCS_OK;
+  if (B->mode == 1) return conc_iterate(B, s, n_iters);
   *B->h_call_end = B->iter_done_host + n_iters;
   if (B->use_graph) {
     auto it = B->graphs.find(n_iters);
@@ -519,7 +658,7 @@ lcs_status batch_iterate(BatchState* B, cudaStream_t s, long long n_iters) {
 // keep the fastest, then return every vector to the zero start
 static lcs_status autotune(BatchState* B, cudaStream_t s, int max_grid, int sms) {
   const int grid_choices[] = {sms, 2 * sms};
-  const int unit_choices[] = {1, 2, 4, 8};
+  const int unit_choices[] = {2, 4};
   double best = 1e30;
   int bg = max_grid, bu = 1;
   cudaEvent_t e0, e1;
@@ -527,7 +666,7 @@ static lcs_status autotune(BatchState* B, cudaStream_t s, int max_grid, int sms)
   B_CUDA(cudaEventCreate(&e1));
   const bool saved_graph = B->use_graph;
   B->use_graph = false;
-  const long long probe_iters = 6;
+  const long long probe_iters = 8;
   for (int gc : grid_choices) {
     const int grid = std::min(gc, max_grid);
     for (int uc : unit_choices) {
@@ -548,15 +687,34 @@ static lcs_status autotune(BatchState* B, cudaStream_t s, int max_grid, int sms)
       if (ms < best) best = ms, bg = grid, bu = uc;
     }
   }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
   B->use_graph = saved_graph;
   B->grid = bg;
   B->tune_grid_choice = bg;
   B->tune_units_choice = bu;
-  B->tuned_ms = best / (double)probe_iters;
+  B->ms_persistent = best / (double)probe_iters;
   layout_items(B, bu);
   B_CUDA(cudaMemcpyAsync(B->d_inst, B->inst.data(), sizeof(BatchInst) * B->n, cudaMemcpyHostToDevice, s));
+  // the concurrent mode, timed the same way
+  {
+    lcs_status st = reset_zero(B, s);
+    if (st) return st;
+    B->mode = 1;
+    st = batch_iterate(B, s, 2);
+    if (st) return st;
+    B_CUDA(cudaEventRecord(e0, s));
+    st = batch_iterate(B, s, probe_iters);
+    if (st) return st;
+    B_CUDA(cudaEventRecord(e1, s));
+    B_CUDA(cudaEventSynchronize(e1));
+    float ms = 0;
+    B_CUDA(cudaEventElapsedTime(&ms, e0, e1));
+    B->ms_concurrent = ms / (double)probe_iters;
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  B->mode = B->ms_concurrent < B->ms_persistent ? 1 : 0;
+  B->tuned_ms = std::min(B->ms_concurrent, B->ms_persistent);
+  B->launches = 0;
   return reset_zero(B, s);
 }
 
@@ -668,7 +826,12 @@ lcs_status batch_create(int n, const int (*shapes)[3], const lcs_bound_opts& o, 
   const int max_grid = per_sm * sms;
   layout_items(B, 1);
   B->grid = max_grid;
-  lcs_status st = autotune(B, s, max_grid, sms);
+  lcs_status st = conc_setup(B, sms);
+  if (st) {
+    batch_destroy(B);
+    return st;
+  }
+  st = autotune(B, s, max_grid, sms);
   if (st) {
     batch_destroy(B);
     return st;
@@ -682,6 +845,12 @@ lcs_status batch_status(BatchState* B, cudaStream_t s, long long* status, long l
   B_CUDA(cudaMemcpyAsync(&c, B->d_ctl, sizeof c, cudaMemcpyDeviceToHost, s));
   B_CUDA(cudaStreamSynchronize(s));
   if (status) *status = c.status;
+  if (B->mode == 1) {
+    // the ring state lives on the host in this mode
+    if (iter_done) *iter_done = B->iter_done_host;
+    if (newest) *newest = B->conc[i].newest;
+    return LCS_OK;
+  }
   if (iter_done) *iter_done = c.iter_done;
   if (newest) *newest = c.newest[i];
   return LCS_OK;
@@ -726,12 +895,22 @@ const long long* batch_vector(BatchState* B, cudaStream_t s, int i, int k, unsig
 int batch_size(const BatchState* B) { return B->n; }
 int batch_d(const BatchState* B, int i) { return B->d[i]; }
 
-void batch_tuning(const BatchState* B, int* grid, int* units, double* ms, long long* launches, int* graph) {
+void batch_tuning(const BatchState* B, int* grid, int* units, double* ms, long long* launches, int* graph, int* mode,
+                  double* ms_persistent, double* ms_concurrent) {
   *grid = B->tune_grid_choice;
   *units = B->tune_units_choice;
   *ms = B->tuned_ms;
   *launches = B->launches;
-  *graph = B->use_graph ? 1 : 0;
+  *graph = (B->mode == 0 && B->use_graph) ? 1 : 0;
+  *mode = B->mode;
+  *ms_persistent = B->ms_persistent;
+  *ms_concurrent = B->ms_concurrent;
+}
+
+lcs_status batch_set_mode(BatchState* B, cudaStream_t s, int mode) {
+  if (B->iter_done_host != 0) return bfail(LCS_EINVAL, "the mode can only be set before the first iteration");
+  B->mode = mode;
+  return reset_zero(B, s);
 }
 
 lcs_status batch_set_spin_budget(BatchState* B, cudaStream_t s, long long cycles) {

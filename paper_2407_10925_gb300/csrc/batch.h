@@ -20,9 +20,16 @@ const long long* batch_vector(BatchState* B, cudaStream_t s, int i, int k, unsig
                               unsigned long long* n_total, lcs_status* err);
 lcs_status batch_set_spin_budget(BatchState* B, cudaStream_t s, long long cycles);
 lcs_status batch_clear_status(BatchState* B, cudaStream_t s);
-void batch_tuning(const BatchState* B, int* grid, int* units, double* ms, long long* launches, int* graph);
+void batch_tuning(const BatchState* B, int* grid, int* units, double* ms, long long* launches, int* graph, int* mode,
+                  double* ms_persistent, double* ms_concurrent);
+lcs_status batch_set_mode(BatchState* B, cudaStream_t s, int mode);
 int batch_size(const BatchState* B);
 int batch_d(const BatchState* B, int i);
 void batch_destroy(BatchState* B);
+
+// provided by lcs_bound.cu for the concurrent mode (the single-instance kernels)
+void launch_finalize_incr(const RedPartial* parts, int n, int r_mode, DevState* st, long long iter, cudaStream_t s);
+void launch_finalize_check(const RedPartial* parts, int n, DevState* st, long long iter, cudaStream_t s);
+int grid_for_work(const void* fn, int sms, unsigned long long work_items);
 
 }  // namespace lcs

@@ -282,6 +282,20 @@ static int grid_for(const void* fn, int sms, unsigned long long work_items) {
   return (int)std::min(full, need);
 }
 
+namespace lcs {
+
+int grid_for_work(const void* fn, int sms, unsigned long long work_items) { return grid_for(fn, sms, work_items); }
+
+void launch_finalize_incr(const RedPartial* parts, int n, int r_mode, DevState* st, long long iter, cudaStream_t s) {
+  finalize_incr_kernel<<<1, kFinalBlock, 0, s>>>(parts, n, r_mode, st, iter);
+}
+
+void launch_finalize_check(const RedPartial* parts, int n, DevState* st, long long iter, cudaStream_t s) {
+  finalize_check_kernel<<<1, kFinalBlock, 0, s>>>(parts, n, st, iter);
+}
+
+}  // namespace lcs
+
 // headroom: every intermediate of a sweep or check is at most sigma^d times the
 // largest |value| (plus lower-order terms); keep it below 2^62
 static bool headroom_ok(const lcs_bound* H, double vb) {
@@ -925,10 +939,19 @@ lcs_status lcs_bound_batch_info(lcs_bound_t* H, lcs_bound_batch_info_t* out) {
   if (!H || !out) return fail(LCS_EINVAL, "NULL argument");
   if (!H->batch) return fail(LCS_EINVAL, "not a batch handle");
   long long launches = 0;
-  batch_tuning(H->batch, &out->grid, &out->units_per_item, &out->tuned_ms_per_iter, &launches, &out->graph);
+  batch_tuning(H->batch, &out->grid, &out->units_per_item, &out->tuned_ms_per_iter, &launches, &out->graph,
+               &out->mode, &out->persistent_ms_per_iter, &out->concurrent_ms_per_iter);
   out->launches = launches;
   out->n_instances = batch_size(H->batch);
   return LCS_OK;
+}
+
+lcs_status lcs_bound_batch_set_mode(lcs_bound_t* H, int mode) {
+  if (!H) return fail(LCS_EINVAL, "NULL argument");
+  if (!H->batch) return fail(LCS_EINVAL, "not a batch handle");
+  if (mode != 0 && mode != 1) return fail(LCS_EINVAL, "mode %d (0 persistent, 1 concurrent)", mode);
+  if (H->iters_done != 0) return fail(LCS_EINVAL, "the mode can only be set before the first iteration");
+  return batch_set_mode(H->batch, H->stream, mode);
 }
 
 lcs_status lcs_bound_batch_set_spin_budget(lcs_bound_t* H, int64_t cycles) {

@@ -14,7 +14,8 @@
 // One CTA per SM, persistent over tiles of 128 rows; 256 threads:
 //   layer 1 (SIMT, fp32): thread j holds the 48 one-hot weights of hidden
 //     unit j in registers and adds the selected ones in feature order (the
-//     same sum the FP32 path forms), applies GELU and stores the activation,
+//     same sum the FP32 path forms; the part shared by a tile's rows once per
+//     tile), applies GELU and stores the activation,
 //     rounded to bf16, in shared memory in the no-swizzle K-major core-matrix
 //     layout the tensor core reads (8 x 8 bf16 blocks of 128 contiguous bytes,
 //     32 blocks per 8-row group);
@@ -118,6 +119,21 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, long lo
   }
 }
 
+// GELU(x) = x Phi(x) with Phi(x) = (1 + erf(x / sqrt 2)) / 2 and erf from
+// Abramowitz & Stegun 7.1.26 (|error| <= 1.5e-7 for y >= 0):
+//   erfc(y) ~ (a1 t + a2 t^2 + a3 t^3 + a4 t^4 + a5 t^5) exp(-y^2),  t = 1 / (1 + p y).
+// Phi(-|x|) = erfc(|x| / sqrt 2) / 2 is formed directly (no cancellation for
+// x << 0) and Phi(|x|) = 1 - Phi(-|x|).  The absolute error of the GELU is at
+// most 1e-7 |x|, far below the bf16 rounding that follows it.
+__device__ __forceinline__ float gelu_as(float x) {
+  const float y = fabsf(x) * 0.70710678118654752f;
+  const float t = __fdividef(1.0f, fmaf(0.3275911f, y, 1.0f));
+  const float poly =
+      t * fmaf(t, fmaf(t, fmaf(t, fmaf(t, 1.061405429f, -1.453152027f), 1.421413741f), -0.284496736f), 0.254829592f);
+  const float lower = 0.5f * poly * __expf(-y * y);  // Phi(-|x|)
+  return x * (x >= 0.0f ? 1.0f - lower : lower);
+}
+
 struct TcParams {
   const float* P;       // FP32 parameters
   const uint4* w2c;     // W2 in bf16, core-matrix layout (kW2Bytes)
@@ -179,17 +195,43 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_table_tc_kernel(TcParams p)
   const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sW2);
   uint32_t parity = 0;
   for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    // ---- layer 1 into shared memory (bf16)
-    for (int r = 0; r < kTileRows; ++r) {
-      const uint32_t q = (uint32_t)(tile * kTileRows + r) << shift;
-      float z = z0;
+    // ---- layer 1 into shared memory (bf16); the sum runs over the features in
+    // order, position 0 first, as in the FP32 path
+    if (p.np == kHin) {
+      // the 128 rows of a tile share positions 0..7 and the first letter of
+      // position 8: that part of the sum is formed once per tile
+      const uint32_t q0 = (uint32_t)(tile * kTileRows);
+      float zf = z0;
 #pragma unroll
-      for (int pp = 0; pp < kHin; ++pp) {
-        const uint32_t pair = (q >> (2 * (kHin - 1 - pp))) & 3u;
-        z += (pair & 2u) ? w[pp][1] : w[pp][0];
-        z += (pair & 1u) ? w[pp][3] : w[pp][2];
+      for (int pp = 0; pp < 8; ++pp) {
+        const uint32_t pair = (q0 >> (2 * (kHin - 1 - pp))) & 3u;
+        zf += (pair & 2u) ? w[pp][1] : w[pp][0];
+        zf += (pair & 1u) ? w[pp][3] : w[pp][2];
       }
-      *reinterpret_cast<__nv_bfloat16*>(sA + cm_off(r, tid)) = __float2bfloat16_rn(gelu_f(z));
+      zf += (q0 & 128u) ? w[8][1] : w[8][0];
+#pragma unroll 4
+      for (int r = 0; r < kTileRows; ++r) {
+        float z = zf + ((r & 64) ? w[8][3] : w[8][2]);
+#pragma unroll
+        for (int pp = 9; pp < kHin; ++pp) {
+          const uint32_t pair = ((uint32_t)r >> (2 * (kHin - 1 - pp))) & 3u;
+          z += (pair & 2u) ? w[pp][1] : w[pp][0];
+          z += (pair & 1u) ? w[pp][3] : w[pp][2];
+        }
+        *reinterpret_cast<__nv_bfloat16*>(sA + cm_off(r, tid)) = __float2bfloat16_rn(gelu_as(z));
+      }
+    } else {
+      for (int r = 0; r < kTileRows; ++r) {
+        const uint32_t q = (uint32_t)(tile * kTileRows + r) << shift;
+        float z = z0;
+#pragma unroll
+        for (int pp = 0; pp < kHin; ++pp) {
+          const uint32_t pair = (q >> (2 * (kHin - 1 - pp))) & 3u;
+          z += (pair & 2u) ? w[pp][1] : w[pp][0];
+          z += (pair & 1u) ? w[pp][3] : w[pp][2];
+        }
+        *reinterpret_cast<__nv_bfloat16*>(sA + cm_off(r, tid)) = __float2bfloat16_rn(gelu_as(z));
+      }
     }
     asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
     tc_fence_before();
@@ -220,7 +262,7 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_table_tc_kernel(TcParams p)
       float v[32];
       tc_ld32(tmem + ((uint32_t)(quarter * 32) << 16) + (uint32_t)col0, v);
 #pragma unroll
-      for (int i = 0; i < 32; ++i) s += gelu_f(v[i] + sb2[col0 + i]) * sw3[col0 + i];
+      for (int i = 0; i < 32; ++i) s += gelu_as(v[i] + sb2[col0 + i]) * sw3[col0 + i];
     }
     spart[half * kTileRows + quarter * 32 + lane] = s;
     tc_fence_before();

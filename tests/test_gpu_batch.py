@@ -1,8 +1,9 @@
-"""Batched persistent launch: every instance of a batch, bit for bit, against the oracle.
+"""Batched instances: every instance of a batch, bit for bit, against the oracle.
 
-All instances advance in lockstep inside one cooperative persistent kernel
-(captured in a CUDA graph); each must produce exactly what Algorithm 2 gives
-for it alone.  The grid barrier's timeout path is exercised with a zero clock
+Mode 0: all instances advance in lockstep inside one cooperative persistent
+kernel (captured in a CUDA graph).  Mode 1: each instance's single-instance
+kernels run on a stream of its own.  In both, each instance must produce
+exactly what Algorithm 2 gives for it alone.  The grid barrier's timeout path is exercised with a zero clock
 budget: the launch must end with LCS_ETIMEOUT, not hang.
 """
 import numpy as np
@@ -28,10 +29,13 @@ def lb():
 MIXED = [(2, 2, 3), (2, 2, 6), (3, 2, 2), (4, 2, 2), (2, 3, 2), (2, 4, 2), (2, 2, 7), (3, 2, 3)]
 
 
+@pytest.mark.parametrize("mode", [0, 1])
 @pytest.mark.parametrize("check_every,pieces", [(0, [17]), (5, [7, 9, 1]), (1, [6])])
-def test_batch_matches_oracle(lb, orc, check_every, pieces):
+def test_batch_matches_oracle(lb, orc, check_every, pieces, mode):
     iters = sum(pieces)
     with lb.LcsBatch(MIXED, check_every=check_every) as b:
+        b.set_mode(mode)
+        assert b.info()["mode"] == mode
         for n in pieces:
             b.iterate(n)
         for i, (s, d, h) in enumerate(MIXED):
@@ -72,14 +76,21 @@ def _oracle_in_pieces(orc, s, d, h, pieces, check_every):
     return out
 
 
-def test_batch_config3_shapes_match_single_handles(lb):
-    """The spec batch (config 3 shapes) against the validated single-instance path."""
+@pytest.mark.parametrize("mode", [None, 0, 1])
+def test_batch_config3_shapes_match_single_handles(lb, mode):
+    """The eight-instance benchmark batch against the validated single-instance
+    path, in the autotuner's mode and in each mode forced."""
     shapes = [(2, 2, 10), (2, 2, 12), (3, 2, 6), (3, 2, 7), (4, 2, 5), (2, 3, 6), (2, 3, 7), (2, 4, 5)]
     iters = 60
     with lb.LcsBatch(shapes, check_every=20) as b:
+        if mode is not None:
+            b.set_mode(mode)
         b.iterate(iters)
         info = b.info()
         assert info["n_instances"] == 8 and info["grid"] > 0
+        assert info["persistent_ms_per_iter"] > 0 and info["concurrent_ms_per_iter"] > 0
+        if mode is None:
+            assert info["mode"] == (1 if info["concurrent_ms_per_iter"] < info["persistent_ms_per_iter"] else 0)
         for i, (s, d, h) in enumerate(shapes):
             with lb.LcsBound(s, d, h, check_every=20) as one:
                 one.iterate(iters)
@@ -90,6 +101,7 @@ def test_batch_config3_shapes_match_single_handles(lb):
 def test_batch_barrier_timeout_reports_status(lb):
     """A zero clock budget makes every waiting CTA give up: LCS_ETIMEOUT, and the context stays usable."""
     with lb.LcsBatch([(2, 2, 8), (3, 2, 3)]) as b:
+        b.set_mode(0)
         b.set_spin_budget(0)
         b.iterate(3)
         rep = b.report(0)
@@ -101,6 +113,14 @@ def test_batch_barrier_timeout_reports_status(lb):
     with lb.LcsBound(2, 2, 6) as one:
         one.iterate(200)
         assert abs(one.read()[0] - 0.770273) < 1e-6
+
+
+def test_batch_mode_is_fixed_once_iterating(lb):
+    with lb.LcsBatch([(2, 2, 6), (3, 2, 2)]) as b:
+        b.iterate(2)
+        with pytest.raises(lb.LcsError) as e:
+            b.set_mode(0)
+        assert e.value.status == 1
 
 
 def test_batch_rejects_unsupported(lb):
