@@ -59,6 +59,8 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--symmetry", type=int, default=1)
+    ap.add_argument("--batch-mode", choices=["auto", "0", "1"], default="auto",
+                    help="batch config: the autotuner's mode, or force 0 (persistent launch) / 1 (concurrent)")
     return ap.parse_args()
 
 
@@ -265,6 +267,8 @@ def run_batch(args, cfg, world, rank, local_rank):
     torch.cuda.synchronize()
     t0_batch = time.perf_counter()
     b = lb.LcsBatch(shapes, check_every=C, stream=stream.cuda_stream)
+    if args.batch_mode != "auto":
+        b.set_mode(int(args.batch_mode))
     t_created = time.perf_counter()
     b.iterate(total_iters)
     bounds_batch = [b.read(i)[0] for i in range(len(shapes))]
@@ -300,8 +304,10 @@ def run_batch(args, cfg, world, rank, local_rank):
         "metric": METRIC, "value": value, "unit": "state-updates/s", "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "config": {"workload": "8 instances (sigma,d,h) " + str(shapes) + f" in one persistent launch, "
-                   f"{C} iterations per step", "states": sum(n_states), "sweeps_per_step": C,
+        "config": {"workload": "8 instances (sigma,d,h) " + str(shapes) + " in one batch handle ("
+                   + ("concurrent single-instance kernels" if info["mode"] == 1 else "one persistent launch")
+                   + f", the autotuner's choice unless forced), {C} iterations per step",
+                   "states": sum(n_states), "sweeps_per_step": C,
                    "l2": "working set of the batch (about 0.6 GB) is larger than L2"},
         "batch": {"time_to_bounds_s": t_batch, "create_and_tune_s": t_created - t0_batch,
                   "plain_sequential_time_to_bounds_s": t_plain, "speedup_vs_plain": t_plain / t_batch,
