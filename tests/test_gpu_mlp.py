@@ -164,3 +164,19 @@ def test_training_reduces_loss_and_warm_start_keeps_the_bound(lb):
     # both rigorous; both converge to Table 2's 0.776860 for h = 8
     assert abs(bz - bw) < 1e-7
     assert abs(bw - 0.776860) < 1e-6
+
+
+def test_lift_prefix_cuts_tuples(lb):
+    """The non-learned control: the value of a tuple is that of its first h_from letters, relative to state 0."""
+    import torch
+
+    h_from, h_to, r_hat = 4, 6, 0.375
+    rng = np.random.default_rng(2)
+    src = rng.integers(-(1 << 50), 1 << 50, size=4 ** h_from, dtype=np.int64)
+    newest = torch.empty(4 ** h_to, dtype=torch.float64, device="cuda")
+    older = torch.empty(4 ** h_to, dtype=torch.float64, device="cuda")
+    lb.lcs_lift_prefix(h_from, h_to, torch.from_numpy(src).cuda(), r_hat, newest, older)
+    x = np.arange(4 ** h_to)
+    want = (src[x >> (2 * (h_to - h_from))] - src[0]).astype(np.float64) * 2.0 ** -44
+    assert np.array_equal(older.cpu().numpy(), want)
+    assert np.array_equal(newest.cpu().numpy(), want + r_hat)
