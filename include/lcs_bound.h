@@ -63,7 +63,8 @@ typedef enum {
   LCS_ETIMEOUT = 4,     /* a bounded device-side wait gave up */
   LCS_ENOBOUND = 5,     /* no feasibility check has run yet */
   LCS_EOVERFLOW = 6,    /* fixed-point headroom would be exceeded */
-  LCS_EUNSUPPORTED = 7  /* (sigma, d, f_mode) has no kernel in this build */
+  LCS_EUNSUPPORTED = 7, /* (sigma, d, f_mode) has no kernel in this build */
+  LCS_EIO = 8           /* a checkpoint file could not be written or read */
 } lcs_status;
 
 typedef struct {
@@ -163,6 +164,33 @@ lcs_status lcs_bound_set_start(lcs_bound_t* hnd, const double* const* v, int on_
 
 /* As lcs_bound_set_start with fixed-point values (units of 2^-K), exact. */
 lcs_status lcs_bound_set_start_fx(lcs_bound_t* hnd, const int64_t* const* v, int on_device);
+
+/* The STORED FORM of an iterate: the n_stored values the handle keeps
+ * (lcs_bound_size).  Under complement-symmetric storage (sigma = 2 and
+ * opts.symmetry) that is the states x < N/2, the rest following from
+ * v[N-1-x] = v[x] (section 3.3, Eq. impl:comp_eq); otherwise all N states.
+ * These calls move iterates in that form -- half the bytes of the full
+ * vectors under symmetry, with no conversion or symmetry check on the way.
+ * set_start_stored_fx: as lcs_bound_set_start_fx (v[0] newest, same resets,
+ * synchronous), each v[k] holding n_stored fixed-point values.
+ * export_stored_fx: as lcs_bound_export_fx for k = -1..d-1, n_stored values;
+ * synchronous for a host dst, asynchronous for a device dst.  The paper has
+ * no counterpart of either call beyond the symmetry itself. */
+lcs_status lcs_bound_set_start_stored_fx(lcs_bound_t* hnd, const int64_t* const* v, int on_device);
+lcs_status lcs_bound_export_stored_fx(lcs_bound_t* hnd, int k, int64_t* dst, int on_device);
+
+/* Checkpoint and resume (no counterpart in the paper).  lcs_bound_save writes
+ * the whole state of a single-instance handle to a file: shape and options,
+ * the d most recent iterates in stored form (newest first), the retained u
+ * (keep_u), the device results (R, argmin, E, the kept r, eps and iteration,
+ * the sticky status) and the iteration count.  lcs_bound_restore reads such a
+ * file into a handle created with the same shape and options (LCS_EINVAL
+ * otherwise); iterate then continues exactly -- bit for bit -- as the saved
+ * handle would have.  Binary, little-endian, for this library version.
+ * LCS_EIO when the file cannot be opened, written or is truncated.
+ * Synchronous. */
+lcs_status lcs_bound_save(lcs_bound_t* hnd, const char* path);
+lcs_status lcs_bound_restore(lcs_bound_t* hnd, const char* path);
 
 /* Copy the iterate k steps older than the newest (k = 0..d-1), or with
  * k = -1 the kept u (needs keep_u), into dst: sigma^(d h) values in

@@ -10,13 +10,14 @@ loudly -- there is no CPU fallback.
 from __future__ import annotations
 
 import ctypes
+import os
 import threading
 
 import numpy as np
 
 from . import build as _build
 
-LCS_OK, LCS_EINVAL, LCS_ENOMEM, LCS_ECUDA, LCS_ETIMEOUT, LCS_ENOBOUND, LCS_EOVERFLOW, LCS_EUNSUPPORTED = range(8)
+LCS_OK, LCS_EINVAL, LCS_ENOMEM, LCS_ECUDA, LCS_ETIMEOUT, LCS_ENOBOUND, LCS_EOVERFLOW, LCS_EUNSUPPORTED, LCS_EIO = range(9)
 
 _ALLOC = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 _FREE = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -106,6 +107,10 @@ def lib():
                 "lcs_bound_read_report": [vp, P(lcs_bound_report)],
                 "lcs_bound_set_start": [vp, vp, i32],
                 "lcs_bound_set_start_fx": [vp, vp, i32],
+                "lcs_bound_set_start_stored_fx": [vp, vp, i32],
+                "lcs_bound_export_stored_fx": [vp, i32, vp, i32],
+                "lcs_bound_save": [vp, ctypes.c_char_p],
+                "lcs_bound_restore": [vp, ctypes.c_char_p],
                 "lcs_bound_export": [vp, i32, vp, i32],
                 "lcs_bound_export_fx": [vp, i32, vp, i32],
                 "lcs_bound_check_vector": [vp, vp, i64, P(i64)],
@@ -269,6 +274,28 @@ def lcs_bound_set_start(hnd, vs):
 def lcs_bound_set_start_fx(hnd, vs):
     arr, on_dev = _vec_array(vs, np.int64)
     _check(lib().lcs_bound_set_start_fx(hnd, arr, on_dev), "lcs_bound_set_start_fx")
+
+
+def lcs_bound_set_start_stored_fx(hnd, vs):
+    """vs[k]: the stored form (lcs_bound_size's n_stored values) of the iterate k steps older than the newest."""
+    arr, on_dev = _vec_array(vs, np.int64)
+    _check(lib().lcs_bound_set_start_stored_fx(hnd, arr, on_dev), "lcs_bound_set_start_stored_fx")
+
+
+def lcs_bound_export_stored_fx(hnd, k: int, out):
+    p, on_dev = _ptr_and_kind(out, np.int64)
+    _check(lib().lcs_bound_export_stored_fx(hnd, k, p, on_dev), "lcs_bound_export_stored_fx")
+    if on_dev:
+        lcs_bound_synchronize(hnd)
+    return out
+
+
+def lcs_bound_save(hnd, path):
+    _check(lib().lcs_bound_save(hnd, os.fsencode(path)), "lcs_bound_save")
+
+
+def lcs_bound_restore(hnd, path):
+    _check(lib().lcs_bound_restore(hnd, os.fsencode(path)), "lcs_bound_restore")
 
 
 def lcs_bound_synchronize(hnd):
@@ -605,6 +632,20 @@ class LcsBound:
         if out is None:
             out = np.empty(self.n_states, dtype=np.int64)
         return lcs_bound_export_fx(self.hnd, k, out)
+
+    def set_start_stored_fx(self, vs):
+        lcs_bound_set_start_stored_fx(self.hnd, vs)
+
+    def export_stored_fx(self, k=0, out=None):
+        if out is None:
+            out = np.empty(self.n_stored, dtype=np.int64)
+        return lcs_bound_export_stored_fx(self.hnd, k, out)
+
+    def save(self, path):
+        lcs_bound_save(self.hnd, path)
+
+    def restore(self, path):
+        lcs_bound_restore(self.hnd, path)
 
     def check_vector(self, u_dev, R):
         return lcs_bound_check_vector(self.hnd, u_dev, R)

@@ -328,6 +328,7 @@ const char* lcs_bound_errstr(lcs_status st) {
     case LCS_ENOBOUND: return "no feasibility check has run";
     case LCS_EOVERFLOW: return "fixed-point range exceeded";
     case LCS_EUNSUPPORTED: return "no kernel for this shape or mode";
+    case LCS_EIO: return "file input/output failed";
   }
   return "unknown status";
 }
@@ -695,7 +696,9 @@ static lcs_status ingest_range(lcs_bound* H, const void* src, unsigned long long
   return LCS_OK;
 }
 
-static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_device, bool from_double) {
+// stored = true: v[k] holds the n_stored stored values (the storage form), copied as they are
+static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_device, bool from_double,
+                                    bool stored = false) {
   if (!H) return fail(LCS_EINVAL, "handle is NULL");
   if (H->batch) return fail(LCS_EINVAL, "a batch handle: use the lcs_bound_batch_* calls");
   if (!v) return fail(LCS_EINVAL, "NULL argument");
@@ -704,7 +707,10 @@ static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_d
   for (int k = 0; k < H->d; ++k) {
     if (!v[k]) return fail(LCS_EINVAL, "start vector %d is NULL", k);
     long long* dst = H->ring[H->d - 1 - k];
-    if (on_device) {
+    if (stored) {
+      LCS_CUDA(cudaMemcpyAsync(dst, v[k], H->n_stored * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
+                               H->stream));
+    } else if (on_device) {
       lcs_status st = ingest_range(H, v[k], 0, H->n_total, dst, from_double, scale);
       if (st) return st;
     } else {
@@ -752,6 +758,157 @@ lcs_status lcs_bound_set_start(lcs_bound_t* H, const double* const* v, int on_de
 
 lcs_status lcs_bound_set_start_fx(lcs_bound_t* H, const int64_t* const* v, int on_device) {
   return set_start_checked(H, (const void* const*)v, on_device, false);
+}
+
+lcs_status lcs_bound_set_start_stored_fx(lcs_bound_t* H, const int64_t* const* v, int on_device) {
+  return set_start_checked(H, (const void* const*)v, on_device, false, true);
+}
+
+lcs_status lcs_bound_export_stored_fx(lcs_bound_t* H, int k, int64_t* dst, int on_device) {
+  if (!H || !dst) return fail(LCS_EINVAL, "NULL argument");
+  if (H->batch) return fail(LCS_EINVAL, "a batch handle: use the lcs_bound_batch_* calls");
+  if (k < -1 || k >= H->d) return fail(LCS_EINVAL, "k=%d outside -1..d-1", k);
+  const long long* src;
+  if (k == -1) {
+    if (!H->ubuf) return fail(LCS_EINVAL, "u is not retained (opts.keep_u = 0)");
+    src = H->ubuf;
+  } else {
+    const int rows = H->d + 1;
+    src = H->ring[(H->newest - k + rows) % rows];
+  }
+  LCS_CUDA(cudaMemcpyAsync(dst, src, H->n_stored * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
+                           H->stream));
+  if (!on_device) LCS_CUDA(cudaStreamSynchronize(H->stream));
+  return LCS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// checkpoint / resume
+
+namespace {
+
+struct CkptHeader {
+  char magic[8];  // "LCSCKPT1"
+  int32_t version;
+  int32_t sigma, d, h;
+  int32_t frac_bits, sym, f_mode, r_mode, check_every, keep_u;
+  int32_t swap_ok;
+  int32_t devstate_bytes;
+  int64_t iters_done;
+  uint64_t n_stored;
+  double vbound;
+};
+
+constexpr char kCkptMagic[8] = {'L', 'C', 'S', 'C', 'K', 'P', 'T', '1'};
+constexpr size_t kFileChunk = (size_t)8 << 20;  // int64 values per file transfer (64 MiB)
+
+struct FileCloser {
+  FILE* f;
+  ~FileCloser() {
+    if (f) fclose(f);
+  }
+};
+
+}  // namespace
+
+static lcs_status write_vector(lcs_bound* H, FILE* f, const long long* src, std::vector<long long>& buf) {
+  for (unsigned long long off = 0; off < H->n_stored; off += kFileChunk) {
+    const size_t len = (size_t)std::min<unsigned long long>(kFileChunk, H->n_stored - off);
+    LCS_CUDA(cudaMemcpyAsync(buf.data(), src + off, len * 8, cudaMemcpyDeviceToHost, H->stream));
+    LCS_CUDA(cudaStreamSynchronize(H->stream));
+    if (fwrite(buf.data(), 8, len, f) != len) return fail(LCS_EIO, "checkpoint write failed");
+  }
+  return LCS_OK;
+}
+
+static lcs_status read_vector(lcs_bound* H, FILE* f, long long* dst, std::vector<long long>& buf) {
+  for (unsigned long long off = 0; off < H->n_stored; off += kFileChunk) {
+    const size_t len = (size_t)std::min<unsigned long long>(kFileChunk, H->n_stored - off);
+    if (fread(buf.data(), 8, len, f) != len) return fail(LCS_EIO, "checkpoint file is truncated");
+    LCS_CUDA(cudaMemcpyAsync(dst + off, buf.data(), len * 8, cudaMemcpyHostToDevice, H->stream));
+    LCS_CUDA(cudaStreamSynchronize(H->stream));
+  }
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_save(lcs_bound_t* H, const char* path) {
+  if (!H || !path) return fail(LCS_EINVAL, "NULL argument");
+  if (H->batch) return fail(LCS_EINVAL, "batch handles have no checkpoint");
+  CkptHeader hd{};
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.version = 1;
+  hd.sigma = H->sigma;
+  hd.d = H->d;
+  hd.h = H->h;
+  hd.frac_bits = H->opts.frac_bits;
+  hd.sym = H->sym;
+  hd.f_mode = H->opts.f_mode;
+  hd.r_mode = H->opts.r_mode;
+  hd.check_every = H->opts.check_every;
+  hd.keep_u = H->ubuf ? 1 : 0;
+  hd.swap_ok = H->swap_ok ? 1 : 0;
+  hd.devstate_bytes = (int32_t)sizeof(DevState);
+  hd.iters_done = H->iters_done;
+  hd.n_stored = H->n_stored;
+  hd.vbound = H->vbound;
+  DevState ds;
+  LCS_CUDA(cudaMemcpyAsync(&ds, H->dstate, sizeof ds, cudaMemcpyDeviceToHost, H->stream));
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
+  if (ds.status) return fail((lcs_status)ds.status, "device status %lld: nothing to save", (long long)ds.status);
+  FileCloser fc{fopen(path, "wb")};
+  if (!fc.f) return fail(LCS_EIO, "cannot open %s for writing", path);
+  if (fwrite(&hd, sizeof hd, 1, fc.f) != 1 || fwrite(&ds, sizeof ds, 1, fc.f) != 1)
+    return fail(LCS_EIO, "checkpoint write failed");
+  std::vector<long long> buf((size_t)std::min<unsigned long long>(kFileChunk, H->n_stored));
+  const int rows = H->d + 1;
+  for (int k = 0; k < H->d; ++k) {  // newest first
+    lcs_status st = write_vector(H, fc.f, H->ring[(H->newest - k + rows) % rows], buf);
+    if (st) return st;
+  }
+  if (H->ubuf) {
+    lcs_status st = write_vector(H, fc.f, H->ubuf, buf);
+    if (st) return st;
+  }
+  if (fflush(fc.f) != 0) return fail(LCS_EIO, "checkpoint write failed");
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_restore(lcs_bound_t* H, const char* path) {
+  if (!H || !path) return fail(LCS_EINVAL, "NULL argument");
+  if (H->batch) return fail(LCS_EINVAL, "batch handles have no checkpoint");
+  FileCloser fc{fopen(path, "rb")};
+  if (!fc.f) return fail(LCS_EIO, "cannot open %s", path);
+  CkptHeader hd;
+  DevState ds;
+  if (fread(&hd, sizeof hd, 1, fc.f) != 1) return fail(LCS_EIO, "checkpoint file is truncated");
+  if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.version != 1)
+    return fail(LCS_EINVAL, "%s is not a checkpoint of this library", path);
+  if (hd.devstate_bytes != (int32_t)sizeof(DevState)) return fail(LCS_EINVAL, "checkpoint layout differs");
+  if (hd.sigma != H->sigma || hd.d != H->d || hd.h != H->h)
+    return fail(LCS_EINVAL, "checkpoint of shape (%d,%d,%d), handle (%d,%d,%d)", hd.sigma, hd.d, hd.h, H->sigma,
+                H->d, H->h);
+  if (hd.frac_bits != H->opts.frac_bits || hd.sym != H->sym || hd.f_mode != H->opts.f_mode ||
+      hd.r_mode != H->opts.r_mode || hd.check_every != H->opts.check_every || hd.keep_u != (H->ubuf ? 1 : 0) ||
+      hd.n_stored != H->n_stored)
+    return fail(LCS_EINVAL, "checkpoint options differ from the handle's");
+  if (fread(&ds, sizeof ds, 1, fc.f) != 1) return fail(LCS_EIO, "checkpoint file is truncated");
+  std::vector<long long> buf((size_t)std::min<unsigned long long>(kFileChunk, H->n_stored));
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
+  for (int k = 0; k < H->d; ++k) {
+    lcs_status st = read_vector(H, fc.f, H->ring[H->d - 1 - k], buf);
+    if (st) return st;
+  }
+  if (H->ubuf) {
+    lcs_status st = read_vector(H, fc.f, H->ubuf, buf);
+    if (st) return st;
+  }
+  LCS_CUDA(cudaMemcpyAsync(H->dstate, &ds, sizeof ds, cudaMemcpyHostToDevice, H->stream));
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
+  H->newest = H->d - 1;
+  H->iters_done = hd.iters_done;
+  H->vbound = hd.vbound;
+  H->swap_ok = H->ks_swap != nullptr && hd.swap_ok;
+  return LCS_OK;
 }
 
 static lcs_status export_impl(lcs_bound* H, int k, void* dst, int on_device, bool to_double) {

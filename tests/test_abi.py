@@ -43,8 +43,8 @@ def test_every_declared_symbol_is_exported(L):
 def test_status_strings(L):
     from paper_2407_10925_gb300 import binding
 
-    for st in range(8):
-        assert binding.lcs_bound_errstr(st)
+    for st in range(9):
+        assert binding.lcs_bound_errstr(st) != "unknown status"
     assert binding.lcs_bound_errstr(0) == "ok"
 
 
@@ -87,5 +87,8 @@ def test_null_handle_calls_fail_cleanly(L):
     from paper_2407_10925_gb300 import binding
 
     assert L.lcs_bound_iterate(None, 1) == binding.LCS_EINVAL
+    assert L.lcs_bound_save(None, b"/nonexistent/x") == binding.LCS_EINVAL
+    assert L.lcs_bound_restore(None, b"/nonexistent/x") == binding.LCS_EINVAL
+    assert L.lcs_bound_export_stored_fx(None, 0, None, 0) == binding.LCS_EINVAL
     assert L.lcs_bound_read(None, None, None, None, None, None) == binding.LCS_EINVAL
     L.lcs_bound_destroy(None)

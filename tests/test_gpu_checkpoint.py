@@ -1,0 +1,111 @@
+"""Stored-form transfers and checkpoint/resume against an uninterrupted run.
+
+A handle saved after some iterations and restored into a fresh handle must
+continue bit for bit as the original does: same iterates, same R, argmin, E,
+kept triplet and bound.  The stored form of an iterate is the prefix of the
+full vector that the handle keeps (the states x < N/2 under complement
+symmetry); a start given in that form must behave exactly as the same start
+given in full.
+"""
+import numpy as np
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2407_10925_gb300 as lb
+
+    lb.lib()
+    return lb
+
+
+SHAPES = [(2, 2, 7, {}), (3, 2, 3, {}), (2, 3, 4, {"keep_u": 1}), (2, 2, 5, {"symmetry": 0, "r_mode": 1})]
+
+
+@pytest.mark.parametrize("s,d,h,kw", SHAPES)
+def test_resume_continues_bit_for_bit(lb, tmp_path, s, d, h, kw):
+    path = str(tmp_path / "ckpt.bin")
+    with lb.LcsBound(s, d, h, check_every=7, **kw) as a:
+        a.iterate(23)
+        a.save(path)
+        a.iterate(19)
+        want = [a.export_fx(k) for k in range(d)]
+        want_rep = a.report()
+        want_read = a.read()
+        want_u = a.export_fx(-1) if kw.get("keep_u") else None
+    with lb.LcsBound(s, d, h, check_every=7, **kw) as b:
+        b.iterate(3)  # whatever the handle held is replaced
+        b.restore(path)
+        b.iterate(19)
+        for k in range(d):
+            assert np.array_equal(b.export_fx(k), want[k]), k
+        assert b.report() == want_rep
+        assert b.read() == want_read
+        if want_u is not None:
+            assert np.array_equal(b.export_fx(-1), want_u)
+
+
+def test_restore_rejects_other_shapes_and_bad_files(lb, tmp_path):
+    path = str(tmp_path / "ckpt.bin")
+    with lb.LcsBound(2, 2, 6, check_every=5) as a:
+        a.iterate(10)
+        a.save(path)
+    for shape, kw in [((2, 2, 5), {}), ((2, 2, 6), {"check_every": 4}), ((2, 2, 6), {"symmetry": 0})]:
+        kw = {"check_every": 5, **kw}
+        with lb.LcsBound(*shape, **kw) as b:
+            with pytest.raises(lb.LcsError) as e:
+                b.restore(path)
+            assert e.value.status == lb.LCS_EINVAL
+    data = open(path, "rb").read()
+    short = str(tmp_path / "short.bin")
+    open(short, "wb").write(data[: len(data) // 2])
+    junk = str(tmp_path / "junk.bin")
+    open(junk, "wb").write(b"not a checkpoint" * 16)
+    with lb.LcsBound(2, 2, 6, check_every=5) as b:
+        with pytest.raises(lb.LcsError) as e:
+            b.restore(short)
+        assert e.value.status == lb.LCS_EIO
+        with pytest.raises(lb.LcsError) as e:
+            b.restore(junk)
+        assert e.value.status == lb.LCS_EINVAL
+        with pytest.raises(lb.LcsError) as e:
+            b.restore(str(tmp_path / "missing.bin"))
+        assert e.value.status == lb.LCS_EIO
+        with pytest.raises(lb.LcsError) as e:
+            b.save(str(tmp_path / "no_such_dir" / "x.bin"))
+        assert e.value.status == lb.LCS_EIO
+
+
+@pytest.mark.parametrize("s,d,h,sym", [(2, 2, 7, 1), (2, 3, 4, 1), (3, 2, 3, 0), (2, 2, 6, 0)])
+def test_stored_form_round_trip(lb, s, d, h, sym):
+    import torch
+
+    with lb.LcsBound(s, d, h, check_every=10, symmetry=sym) as a:
+        a.iterate(30)
+        full = [a.export_fx(k) for k in range(d)]
+        stored = [a.export_stored_fx(k) for k in range(d)]
+        stored_dev = [torch.empty(a.n_stored, dtype=torch.int64, device="cuda") for _ in range(d)]
+        for k in range(d):
+            a.export_stored_fx(k, stored_dev[k])
+        for k in range(d):
+            assert stored[k].size == a.n_stored
+            assert np.array_equal(stored[k], full[k][: a.n_stored])
+            assert np.array_equal(stored_dev[k].cpu().numpy(), stored[k])
+    with lb.LcsBound(s, d, h, check_every=10, symmetry=sym) as b, \
+            lb.LcsBound(s, d, h, check_every=10, symmetry=sym) as c, \
+            lb.LcsBound(s, d, h, check_every=10, symmetry=sym) as e:
+        b.set_start_fx(full)
+        c.set_start_stored_fx(stored)
+        e.set_start_stored_fx(stored_dev)
+        for hnd in (b, c, e):
+            hnd.iterate(25)
+        for k in range(d):
+            assert np.array_equal(c.export_fx(k), b.export_fx(k))
+            assert np.array_equal(e.export_fx(k), b.export_fx(k))
+        assert c.read() == b.read() == e.read()
