@@ -25,6 +25,7 @@ SOURCES = [
     "kernels_s4.cu",
     "noalloc.cu",
     "kernels_s2d2.cu",
+    "kernels_d2s.cu",
     "batch.cu",
     "mlp.cu",
     "mlp_tc.cu",

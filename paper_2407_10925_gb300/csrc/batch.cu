@@ -489,15 +489,16 @@ static lcs_status reset_zero(BatchState* B, cudaStream_t s) {
 // ---------------------------------------------------------------------------
 // concurrent mode
 
-// the single-instance kernel set of a batch kind
-static const KernelSet* conc_kernels(int kind) {
+// the single-instance kernel set of a batch kind (the zero start is
+// swap-symmetric, so d = 2 with sigma >= 3 takes the swap-aware kernels)
+static const KernelSet* conc_kernels(int kind, int h) {
   switch (kind) {
     case BK_S2D2: return find_kernels(2, 2, 2);
     case BK_G22S: return find_kernels(2, 2, 1);
     case BK_G23S: return find_kernels(2, 3, 1);
     case BK_G24S: return find_kernels(2, 4, 1);
-    case BK_G32: return find_kernels(3, 2, 0);
-    case BK_G42: return find_kernels(4, 2, 0);
+    case BK_G32: return find_kernels(3, 2, h >= d2s_min_h(3) ? 3 : 0);
+    case BK_G42: return find_kernels(4, 2, h >= d2s_min_h(4) ? 3 : 0);
     case BK_G22: return find_kernels(2, 2, 0);
     case BK_G23: return find_kernels(2, 3, 0);
   }
@@ -576,11 +577,12 @@ static lcs_status conc_setup(BatchState* B, int sms) {
   for (int r = 0; r < B->n; ++r) {
     ConcInst& c = B->conc[r];
     const BatchInst& in = B->inst[r];
-    c.ks = conc_kernels(in.kind);
+    c.ks = conc_kernels(in.kind, in.h);
     if (!c.ks) return bfail(LCS_EUNSUPPORTED, "no single-instance kernels for batch kind %d", in.kind);
     // the grids lcs_bound_create picks for the same shape
-    const unsigned long long work =
-        in.kind == BK_S2D2 ? 2ull * in.tn * in.tn * (unsigned long long)kBlock : in.n_threads;
+    const unsigned long long work = in.kind == BK_S2D2 ? 2ull * in.tn * in.tn * (unsigned long long)kBlock
+                                    : c.ks->sym == 3   ? d2s_slots(c.ks->sigma, in.h) * kBlock
+                                                       : in.n_threads;
     c.grid_sweep = grid_for_work(c.ks->sweep_fn, sms, work);
     c.grid_check = grid_for_work(c.ks->check_fn, sms, work);
     c.partials = (RedPartial*)balloc(B, sizeof(RedPartial) * (size_t)std::max(c.grid_sweep, c.grid_check));

@@ -32,4 +32,10 @@ void launch_finalize_incr(const RedPartial* parts, int n, int r_mode, DevState* 
 void launch_finalize_check(const RedPartial* parts, int n, DevState* st, long long iter, cudaStream_t s);
 int grid_for_work(const void* fn, int sms, unsigned long long work_items);
 
+// provided by kernels_d2s.cu (d = 2, sigma >= 3, swap-aware)
+int d2s_min_h(int sigma);
+unsigned long long d2s_slots(int sigma, int h);
+void launch_swap_check_d2s(int sigma, const long long* v, unsigned long long n, int h, DevState* st, int grid,
+                           cudaStream_t s);
+
 }  // namespace lcs

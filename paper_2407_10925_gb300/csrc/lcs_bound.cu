@@ -380,7 +380,14 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   const int sym = (sigma == 2 && opts.symmetry && h >= 2) ? 1 : 0;
   const KernelSet* ks = find_kernels(sigma, d, sym, opts.f_mode);
   if (!ks) return fail(LCS_EUNSUPPORTED, "no kernel compiled for sigma=%d d=%d f_mode=%d", sigma, d, opts.f_mode);
-  const KernelSet* ks_swap = (sym && d == 2 && h >= 6 && opts.f_mode == 0) ? find_kernels(sigma, d, 2) : nullptr;
+  // kernels that also use the swap symmetry (used while the iterates have it)
+  const KernelSet* ks_swap = nullptr;
+  if (d == 2 && opts.f_mode == 0) {
+    if (sym && h >= 6)
+      ks_swap = find_kernels(sigma, d, 2);
+    else if (!sym && sigma >= 3 && h >= d2s_min_h(sigma))
+      ks_swap = find_kernels(sigma, d, 3);
+  }
 
   lcs_bound* H = new (std::nothrow) lcs_bound();
   if (!H) return fail(LCS_ENOMEM, "host allocation");
@@ -424,8 +431,10 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   H->grid_check = grid_for(ks->check_fn, sms, thread_items);
   H->n_partials = std::max(H->grid_sweep, H->grid_check);
   if (ks_swap) {
-    // one CTA per 16 x 16 tile of orbit representatives
-    const unsigned long long tiles = 2ull * (1ull << (h - 6)) * (1ull << (h - 6));
+    // sigma = d = 2: one CTA per 16 x 16 tile of orbit representatives;
+    // d = 2, sigma >= 3: one CTA per slot of tiles of (A, B) pairs
+    const unsigned long long tiles =
+        ks_swap->sym == 2 ? 2ull * (1ull << (h - 6)) * (1ull << (h - 6)) : d2s_slots(sigma, h);
     H->grid_sweep_swap = grid_for(ks_swap->sweep_fn, sms, tiles * kBlock);
     H->grid_check_swap = grid_for(ks_swap->check_fn, sms, tiles * kBlock);
     H->n_partials = std::max(H->n_partials, std::max(H->grid_sweep_swap, H->grid_check_swap));
@@ -728,7 +737,10 @@ static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_d
     LCS_CUDA(cudaGetLastError());
     H->launches++;
     if (H->ks_swap) {
-      swap_check_kernel<<<grid, kBlock, 0, H->stream>>>(dst, H->n_stored, H->n_total, H->dstate);
+      if (H->ks_swap->sym == 2)
+        swap_check_kernel<<<grid, kBlock, 0, H->stream>>>(dst, H->n_stored, H->n_total, H->dstate);
+      else
+        launch_swap_check_d2s(H->sigma, dst, H->n_stored, H->h, H->dstate, grid, H->stream);
       LCS_CUDA(cudaGetLastError());
       H->launches++;
     }

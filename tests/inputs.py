@@ -29,6 +29,21 @@ def swap_index(n: int) -> np.ndarray:
     return ((y >> 1) & 0x5555555555555555) | ((y & 0x5555555555555555) << 1)
 
 
+def swap_index_d2(sigma: int, h: int) -> np.ndarray:
+    """d = 2, any sigma: the index with the two strings exchanged (the two base-sigma
+    digits of every position swapped in the interleaved index)."""
+    n = sigma ** (2 * h)
+    x = np.arange(n, dtype=np.int64)
+    y = np.zeros(n, dtype=np.int64)
+    m = 1
+    for _ in range(h):
+        pd = x % (sigma * sigma)
+        x //= sigma * sigma
+        y += ((pd % sigma) * sigma + pd // sigma) * m
+        m *= sigma * sigma
+    return y
+
+
 def symmetrize(v: np.ndarray, swap: bool = False) -> np.ndarray:
     """The smallest value over each orbit of the complement map (and of the string swap)."""
     n = v.size
@@ -36,6 +51,11 @@ def symmetrize(v: np.ndarray, swap: bool = False) -> np.ndarray:
     if swap:
         out = np.minimum(out, out[swap_index(n)])
     return out
+
+
+def swap_symmetrize(v: np.ndarray, sigma: int, h: int) -> np.ndarray:
+    """d = 2, any sigma: the smaller value of each pair of states exchanged by the string swap."""
+    return np.minimum(v, v[swap_index_d2(sigma, h)])
 
 
 def random_fx(sigma, d, h, seed, base_units=200.0, spread_units=4.0, frac_bits=K_DEFAULT, symmetric=False,
@@ -47,6 +67,10 @@ def random_fx(sigma, d, h, seed, base_units=200.0, spread_units=4.0, frac_bits=K
     v = (base_units + spread_units * rng.random(n)) * one
     v = v.astype(np.int64)
     v += rng.integers(0, 1 << 20, size=n, dtype=np.int64)  # low-order noise below the unit
+    if sigma != 2 and swap and not symmetric:
+        if d != 2:
+            raise ValueError("the swap needs d = 2")
+        return swap_symmetrize(v, sigma, h)
     if symmetric or swap:
         if sigma != 2 or (swap and d != 2):
             raise ValueError("complement symmetry needs sigma = 2; the swap needs d = 2")
@@ -63,7 +87,9 @@ def random_history(sigma, d, h, seed, step_units=0.4, frac_bits=K_DEFAULT, symme
     out = []
     for k in range(d):
         jitter = rng.integers(0, one // 16, size=n, dtype=np.int64)
-        if symmetric or swap:
+        if sigma != 2 and swap and not symmetric:
+            jitter = swap_symmetrize(jitter, sigma, h)
+        elif symmetric or swap:
             jitter = symmetrize(jitter, swap)
         out.append(base - int(k * step_units * one) - jitter)
     return out

@@ -123,7 +123,37 @@ def test_swap_kernel_zero_start_many_checks(lb, orc, h):
         _check_run_against_oracle(lb, orc, 2, 2, h, 12 if h > 8 else 30, 1, 1, r_mode)
 
 
-@pytest.mark.parametrize("s,d,h,sym", [(2, 2, 5, 1), (2, 2, 5, 0), (2, 3, 3, 1), (3, 2, 3, 0), (4, 2, 2, 0)])
+D2S_SHAPES = [(3, 4), (3, 5), (4, 3), (4, 4), (5, 3)]
+
+
+@pytest.mark.parametrize("s,h", D2S_SHAPES)
+@pytest.mark.parametrize("swap", [False, True])
+def test_d2_swap_paths_bit_exact(lb, orc, s, h, swap):
+    """d = 2, sigma >= 3: swap-symmetric starts run the kernels that read each
+    value of v_{t-1} once through the string swap; other starts run the generic
+    kernels.  Both exact, with checks at every third iteration."""
+    hist = inputs.random_history(s, 2, h, seed=60 + 3 * h + s, swap=swap)
+    start = [hist[1], hist[0]]  # oldest first
+    _check_run_against_oracle(lb, orc, s, 2, h, 9, 3, 0, 0, start=start)
+
+
+@pytest.mark.parametrize("s,h", D2S_SHAPES)
+@pytest.mark.parametrize("r_mode", [0, 1])
+def test_d2_swap_zero_start_every_iteration_checked(lb, orc, s, h, r_mode):
+    """Zero start (swap-symmetric): the fused increment's argmin classes and the check, every iteration."""
+    _check_run_against_oracle(lb, orc, s, 2, h, 12, 1, 0, r_mode)
+
+
+def test_d2_swap_kernel_is_used_and_counted(lb):
+    with lb.LcsBound(3, 2, 6, timing=1) as hnd:
+        hnd.iterate(5)
+        st = hnd.stats()
+        # 20 algorithmic bytes per state (v_{t-1} once, half of v_{t-2}, one write) instead of 8 (d+1) = 24
+        assert st["sweep_bytes"] == 5 * 20 * 3 ** 12
+
+
+@pytest.mark.parametrize("s,d,h,sym", [(2, 2, 5, 1), (2, 2, 5, 0), (2, 3, 3, 1), (3, 2, 3, 0), (4, 2, 2, 0),
+                                       (3, 2, 4, 0), (4, 2, 3, 0)])
 def test_check_vector_matches_oracle(lb, torch_mod, orc, s, d, h, sym):
     torch = torch_mod
     u = inputs.random_fx(s, d, h, seed=77 + h, symmetric=(s == 2))
