@@ -446,9 +446,23 @@ def run_fp32(args, cfg, world, rank, local_rank):
         }
         del exact, f32, ex, err
         torch.cuda.empty_cache()
+        # the library's default path for the shape (symmetric storage where it
+        # applies) and, for d >= 3, the max over every non-empty advance set
+        variants = [("default_storage", {})]
+        if d_ >= 3:
+            variants.append(("all_advance_sets", {"f_mode": 1}))
+        for name, kw in variants:
+            with lb.LcsBound(s_, d_, h_, check_every=100, timing=1, **kw) as hnd:
+                hnd.iterate(iters)
+                st = hnd.stats()
+                results[f"({s_},{d_},{h_})"][name] = {
+                    "ms_per_sweep": st["sweep_ms"] / max(1, st["sweep_launches"]), "bound": hnd.read()[0],
+                    "stored_states": hnd.n_stored, **kw}
     if rank == 0:
         print(json.dumps({"metric": "float32 storage experiment: error vs exact iterates and sweep time",
-                          "config": {"workload": "zero start, full storage (no symmetry), 1500 iterations"},
+                          "config": {"workload": "zero start, 1500 iterations; float32 vs fixed point with full "
+                                                 "storage (no symmetry), plus the library's default storage and "
+                                                 "(d >= 3) the all-advance-sets F"},
                           "results": results, "note": "no bound is derived from float32 iterates"}), flush=True)
 
 

@@ -290,7 +290,7 @@ KernelSet make_d2s_set() {
   k.sym = 3;
   k.sweep = &launch_sweep_d2s<SIG>;
   k.check = &launch_check_d2s<SIG>;
-  k.sweep_fn = (const void*)&sweep_d2s_kernel<SIG, true>;
+  k.sweep_fn = (const void*)&sweep_d2s_kernel<SIG, false>;  // the plain sweep sizes the grid
   k.check_fn = (const void*)&check_d2s_kernel<SIG>;
   k.tails_per_thread = 2;
   k.sweep_algo_bytes = 20;  // 8 B of v_{t-1} + 4 B of v_{t-2} (the block serves both tails) + 8 B written

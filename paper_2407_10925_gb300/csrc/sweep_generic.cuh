@@ -644,7 +644,9 @@ KernelSet make_generic_set() {
   k.f_mode = FALL ? 1 : 0;
   k.sweep = &launch_sweep_generic<SIG, D, SYM, FALL>;
   k.check = &launch_check_generic<SIG, D, SYM, FALL>;
-  k.sweep_fn = (const void*)&sweep_generic_kernel<SIG, D, SYM, true, FALL>;
+  // the plain sweep sizes the grid: the fused-increment variant (one launch in
+  // check_every) needs more registers, and its extra CTAs simply queue
+  k.sweep_fn = (const void*)&sweep_generic_kernel<SIG, D, SYM, false, FALL>;
   k.check_fn = (const void*)&check_generic_kernel<SIG, D, SYM, FALL>;
   k.tails_per_thread = SYM ? 2 : 1;
   k.sweep_algo_bytes = 8 * (D + 1);
