@@ -490,12 +490,13 @@ static lcs_status reset_zero(BatchState* B, cudaStream_t s) {
 // concurrent mode
 
 // the single-instance kernel set of a batch kind (the zero start is
-// swap-symmetric, so d = 2 with sigma >= 3 takes the swap-aware kernels)
+// symmetric under exchanging strings, so d = 2 with sigma >= 3 and
+// sigma = 2 with d = 3 take the kernels that use it)
 static const KernelSet* conc_kernels(int kind, int h) {
   switch (kind) {
     case BK_S2D2: return find_kernels(2, 2, 2);
     case BK_G22S: return find_kernels(2, 2, 1);
-    case BK_G23S: return find_kernels(2, 3, 1);
+    case BK_G23S: return find_kernels(2, 3, h >= d3s_min_h() ? 4 : 1);
     case BK_G24S: return find_kernels(2, 4, 1);
     case BK_G32: return find_kernels(3, 2, h >= d2s_min_h(3) ? 3 : 0);
     case BK_G42: return find_kernels(4, 2, h >= d2s_min_h(4) ? 3 : 0);
@@ -582,6 +583,7 @@ static lcs_status conc_setup(BatchState* B, int sms) {
     // the grids lcs_bound_create picks for the same shape
     const unsigned long long work = in.kind == BK_S2D2 ? 2ull * in.tn * in.tn * (unsigned long long)kBlock
                                     : c.ks->sym == 3   ? d2s_slots(c.ks->sigma, in.h) * kBlock
+                                    : c.ks->sym == 4   ? d3s_tiles(in.h) * kBlock
                                                        : in.n_threads;
     c.grid_sweep = grid_for_work(c.ks->sweep_fn, sms, work);
     c.grid_check = grid_for_work(c.ks->check_fn, sms, work);

@@ -228,7 +228,7 @@ struct lcs_bound {
   bool own_stream;
   int device;
   const KernelSet* ks;       // kernels for the storage scheme (complement-symmetric or full)
-  const KernelSet* ks_swap;  // sigma = d = 2, h >= 6: kernels that also use the swap symmetry
+  const KernelSet* ks_swap;  // kernels that also use the string swap / permutations (d = 2, 3)
   bool swap_ok;              // the live iterates are swap-symmetric: ks_swap may run
   long long* ring[kMaxD + 1];
   int newest;  // ring slot of the newest iterate
@@ -388,6 +388,7 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
     else if (!sym && sigma >= 3 && h >= d2s_min_h(sigma))
       ks_swap = find_kernels(sigma, d, 3);
   }
+  if (d == 3 && sigma == 2 && sym && h >= d3s_min_h() && opts.f_mode == 0) ks_swap = find_kernels(sigma, d, 4);
 
   lcs_bound* H = new (std::nothrow) lcs_bound();
   if (!H) return fail(LCS_ENOMEM, "host allocation");
@@ -433,8 +434,9 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   if (ks_swap) {
     // sigma = d = 2: one CTA per 16 x 16 tile of orbit representatives;
     // d = 2, sigma >= 3: one CTA per slot of tiles of (A, B) pairs
-    const unsigned long long tiles =
-        ks_swap->sym == 2 ? 2ull * (1ull << (h - 6)) * (1ull << (h - 6)) : d2s_slots(sigma, h);
+    const unsigned long long tiles = ks_swap->sym == 2   ? 2ull * (1ull << (h - 6)) * (1ull << (h - 6))
+                                     : ks_swap->sym == 3 ? d2s_slots(sigma, h)
+                                                         : d3s_tiles(h);
     H->grid_sweep_swap = grid_for(ks_swap->sweep_fn, sms, tiles * kBlock);
     H->grid_check_swap = grid_for(ks_swap->check_fn, sms, tiles * kBlock);
     H->n_partials = std::max(H->n_partials, std::max(H->grid_sweep_swap, H->grid_check_swap));
@@ -739,8 +741,10 @@ static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_d
     if (H->ks_swap) {
       if (H->ks_swap->sym == 2)
         swap_check_kernel<<<grid, kBlock, 0, H->stream>>>(dst, H->n_stored, H->n_total, H->dstate);
-      else
+      else if (H->ks_swap->sym == 3)
         launch_swap_check_d2s(H->sigma, dst, H->n_stored, H->h, H->dstate, grid, H->stream);
+      else
+        launch_perm_check_d3s(dst, H->n_stored, H->n_total, H->dstate, grid, H->stream);
       LCS_CUDA(cudaGetLastError());
       H->launches++;
     }

@@ -69,7 +69,8 @@ struct KernelSet {
   int f_mode;                    // 0: the paper's F; 1: every non-empty advance set
   int sym;                       // 0: full storage; 1: complement-symmetric storage (sigma = 2);
                                  // 2: complement storage + swap-aware reads (sigma = d = 2);
-                                 // 3: full storage + swap-aware reads (d = 2, sigma >= 3)
+                                 // 3: full storage + swap-aware reads (d = 2, sigma >= 3);
+                                 // 4: complement storage + permutation-aware reads (sigma = 2, d = 3)
   void (*sweep)(const SweepParams&, int grid, cudaStream_t);
   void (*check)(const CheckParams&, int grid, cudaStream_t);
   const void* sweep_fn;          // kernel symbols, for occupancy queries

@@ -1,0 +1,315 @@
+// sweep_d3s.cuh -- the sweep and check for sigma = 2, d = 3 that use the
+// permutations of the three strings and the complement, under
+// complement-symmetric storage (states x < N/2, the first letter of string 0
+// is 0).  Both symmetries hold bit for bit in fixed point once the start
+// vectors have them (the zero start does): the LCS does not depend on the
+// order of its arguments, and F commutes with permuting the strings and with
+// complementing every letter (section 3.3).
+//
+// A tail tuple is tau = (T0, T1, T2), three strings of L = h - 1 bits.  One
+// thread owns the orbit of tau under the 6 permutations together with the
+// orbit of its complement ~tau (never the same orbit): up to 12 tails, 96
+// states, 48 of them stored.  With binary heads a state whose heads are not
+// all equal has a majority letter m (two strings) and a minority string j,
+// and Eq. ineq3 has two candidates (Algorithm 1):
+//   z = m: advance j alone, the others keep head m   -> v_{t-1}, 2 values
+//   z = 1 - m: advance the two majority strings     -> v_{t-2}, 4 values
+// By the permutation symmetry the first sum depends only on which component
+// of the tail string j carries and on m; by the complement, m = 1 is the
+// m = 0 sum of the complemented tail.  So the thread forms
+//   A1(X, k) = sum over c of v_{t-1}[(0 U0, 0 U1, U2 c)],     U2 = X_k,
+//   A2(X, k) = sum over c1, c2 of v_{t-2}[(0 U0, U1 c1, U2 c2)], U0 = X_k,
+// ({U0, U1} resp. {U1, U2} the other two components) for X in {tau, ~tau}
+// and k in {0, 1, 2}, all in the stored half, plus the all-advance block of
+// v_{t-3} once (permuting or complementing the tail only permutes it): 44
+// reads for 48 stored outputs, against roughly 40 B read per stored state by
+// the generic gather.  Tails with equal components reuse the equal sums.
+//
+// Orbit representatives: T0 <= T1 <= T2 and (T0, T1, T2) <= (~T2, ~T1, ~T0)
+// lexicographically, i.e. T0 + T2 < 2^L - 1, or T0 + T2 = 2^L - 1 and
+// T1 < 2^(L-1).  Tiles of 4 x 8 x 8 (T0, T1, T2) values, one per CTA; tiles
+// with no representative are skipped whole.
+#pragma once
+
+#include <climits>
+
+#include "lcs_common.h"
+#include "sweep_generic.cuh"
+
+namespace lcs {
+
+// bit i of x (i < 21) moved to bit 3i
+__device__ __forceinline__ unsigned long long spread3(unsigned long long x) {
+  x &= 0x1fffffull;
+  x = (x | (x << 32)) & 0x1f00000000ffffull;
+  x = (x | (x << 16)) & 0x1f0000ff0000ffull;
+  x = (x | (x << 8)) & 0x100f00f00f00f00full;
+  x = (x | (x << 4)) & 0x10c30c30c30c30c3ull;
+  x = (x | (x << 2)) & 0x1249249249249249ull;
+  return x;
+}
+
+// two adjacent values at an even index (16-byte aligned)
+template <bool CG>
+__device__ __forceinline__ longlong2 d3s_ld2(const long long* v, unsigned long long y) {
+  const longlong2* q = reinterpret_cast<const longlong2*>(v + y);
+  if constexpr (CG)
+    return __ldcg(q);
+  else
+    return __ldg(q);
+}
+
+__device__ __forceinline__ unsigned long long d3s_tail(unsigned long long a, unsigned long long b,
+                                                       unsigned long long c) {
+  return (spread3(a) << 2) | (spread3(b) << 1) | spread3(c);
+}
+
+struct D3sOrbit {
+  unsigned long long T[3];  // the representative tau
+  unsigned long long C[3];  // its complement ~tau
+};
+
+// tiles of 4 x 8 x 8 representatives; tile k = (I0 n1 + I1) n2 + I2
+__device__ __forceinline__ void d3s_tile(unsigned long long k, int L, unsigned long long& I0, unsigned long long& I1,
+                                         unsigned long long& I2) {
+  const unsigned long long n12 = 1ull << (L - 3);
+  I2 = k & (n12 - 1);
+  I1 = (k >> (L - 3)) & (n12 - 1);
+  I0 = k >> (2 * (L - 3));
+}
+
+// does tile (I0, I1, I2) hold a representative?
+__device__ __forceinline__ bool d3s_tile_live(unsigned long long I0, unsigned long long I1, unsigned long long I2,
+                                              unsigned long long M) {
+  return 4 * I0 <= 8 * I1 + 7 && 8 * I1 <= 8 * I2 + 7 && 4 * I0 + 8 * I2 <= M;
+}
+
+// the representative of thread tid in tile (I0, I1, I2); false if none.  The
+// thread's bits are T1_0, T0_0, T2_0, T1_1, T0_1, T2_1, T1_2, T2_2 (low
+// first): the digit order of the addresses of A1(tau, 2).
+__device__ __forceinline__ bool d3s_rep(unsigned long long I0, unsigned long long I1, unsigned long long I2,
+                                        unsigned long long M, int L, unsigned tid, D3sOrbit& o) {
+  const unsigned t0 = ((tid >> 1) & 1u) | (((tid >> 4) & 1u) << 1);
+  const unsigned t1 = (tid & 1u) | (((tid >> 3) & 1u) << 1) | (((tid >> 6) & 1u) << 2);
+  const unsigned t2 = ((tid >> 2) & 1u) | (((tid >> 5) & 1u) << 1) | (((tid >> 7) & 1u) << 2);
+  const unsigned long long T0 = 4 * I0 + t0, T1 = 8 * I1 + t1, T2 = 8 * I2 + t2;
+  if (T0 > T1 || T1 > T2) return false;
+  if (T0 + T2 > M) return false;
+  if (T0 + T2 == M && T1 >= (1ull << (L - 1))) return false;
+  o.T[0] = T0, o.T[1] = T1, o.T[2] = T2;
+  o.C[0] = M - T0, o.C[1] = M - T1, o.C[2] = M - T2;
+  return true;
+}
+
+// the six sums of one tail X (A1 from v1, A2 from v2)
+template <bool CG>
+__device__ __forceinline__ void d3s_sums(const long long* v1, const long long* v2, const unsigned long long (&X)[3],
+                                         long long (&A1)[3], long long (&A2)[3]) {
+  const bool e01 = X[0] == X[1], e12 = X[1] == X[2];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const bool reuse = (k == 1 && e01) || (k == 2 && e12);
+    if (reuse) {
+      A1[k] = A1[k - 1];
+      A2[k] = A2[k - 1];
+      continue;
+    }
+    const unsigned long long o0 = X[k == 0 ? 1 : 0], o1 = X[k == 2 ? 1 : 2];
+    // A1: strings 0 and 1 hold the other components with head 0, string 2 = X_k c
+    const unsigned long long a1 = d3s_tail(o0, o1, X[k] << 1);
+    const longlong2 p = d3s_ld2<CG>(v1, a1);
+    A1[k] = p.x + p.y;
+    // A2: string 0 = 0 X_k, strings 1 and 2 hold the others, each followed by a letter
+    const unsigned long long a2 = d3s_tail(X[k], o0 << 1, o1 << 1);
+    const longlong2 q0 = d3s_ld2<CG>(v2, a2), q1 = d3s_ld2<CG>(v2, a2 + 2);
+    A2[k] = q0.x + q0.y + q1.x + q1.y;
+  }
+}
+
+template <bool CG>
+__device__ __forceinline__ long long d3s_block(const long long* v3, unsigned long long t) {
+  const unsigned long long b = 8 * t;
+  long long s = 0;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const longlong2 q = d3s_ld2<CG>(v3, b + 2 * i);
+    s += q.x + q.y;
+  }
+  return s;
+}
+
+// the six permutations of three components
+__device__ __forceinline__ int d3s_perm(int p, int j) {
+  // (0,1,2) (0,2,1) (1,0,2) (1,2,0) (2,0,1) (2,1,0)
+  constexpr unsigned char P[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+  return P[p][j];
+}
+
+template <bool INCR, bool CG>
+__device__ __forceinline__ void d3s_sweep_orbit(const SweepParams& p, const D3sOrbit& o, long long& best_v,
+                                                unsigned long long& best_x) {
+  const unsigned long long nt = p.n_tail;
+  long long A1t[3], A2t[3], A1c[3], A2c[3];
+  d3s_sums<CG>(p.prev[0], p.prev[1], o.T, A1t, A2t);
+  d3s_sums<CG>(p.prev[0], p.prev[1], o.C, A1c, A2c);
+  const long long B = d3s_block<CG>(p.prev[2], d3s_tail(o.T[0], o.T[1], o.T[2]));
+  const long long e000 = p.one + (B >> 3);
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const unsigned long long* X = side == 0 ? o.T : o.C;
+    const long long* A1s = side == 0 ? A1t : A1c;  // this side's sums
+    const long long* A2s = side == 0 ? A2t : A2c;
+    const long long* A1o = side == 0 ? A1c : A1t;  // the complement side's sums
+    const long long* A2o = side == 0 ? A2c : A2t;
+    unsigned long long seen[6];
+#pragma unroll
+    for (int q = 0; q < 6; ++q) {
+      const int p0 = d3s_perm(q, 0), p1 = d3s_perm(q, 1), p2 = d3s_perm(q, 2);
+      const unsigned long long ty = d3s_tail(X[p0], X[p1], X[p2]);
+      seen[q] = ty;
+      bool dup = false;
+#pragma unroll
+      for (int r = 0; r < q; ++r) dup |= seen[r] == ty;
+      if (dup) continue;
+      // heads 001 and 010: majority 0, minority string 2 resp. 1;
+      // heads 011: majority 1, minority string 0
+      const long long v001 = max(4 * A1s[p2], 2 * A2o[p2]) >> 3;
+      const long long v010 = max(4 * A1s[p1], 2 * A2o[p1]) >> 3;
+      const long long v011 = max(4 * A1o[p0], 2 * A2s[p0]) >> 3;
+      const unsigned long long x0 = ty, x1 = nt + ty, x2 = 2 * nt + ty, x3 = 3 * nt + ty;
+      p.out[x0] = e000;
+      p.out[x1] = v001;
+      p.out[x2] = v010;
+      p.out[x3] = v011;
+      if constexpr (INCR) {
+        const long long i0 = e000 - ld_vec<CG>(p.prev[0] + x0);
+        const long long i1 = v001 - ld_vec<CG>(p.prev[0] + x1);
+        const long long i2 = v010 - ld_vec<CG>(p.prev[0] + x2);
+        const long long i3 = v011 - ld_vec<CG>(p.prev[0] + x3);
+        if (red_better(i0, x0, best_v, best_x, p.r_mode)) best_v = i0, best_x = x0;
+        if (red_better(i1, x1, best_v, best_x, p.r_mode)) best_v = i1, best_x = x1;
+        if (red_better(i2, x2, best_v, best_x, p.r_mode)) best_v = i2, best_x = x2;
+        if (red_better(i3, x3, best_v, best_x, p.r_mode)) best_v = i3, best_x = x3;
+      }
+    }
+  }
+}
+
+// W = u + 3R - F(u + 2R, u + R, u) at the 8 heads of tau: every class of
+// equal values of the orbit pair has a member with tail tau
+template <bool CG>
+__device__ __forceinline__ void d3s_check_orbit(const CheckParams& p, const D3sOrbit& o, long long R,
+                                                long long& best) {
+  const unsigned long long nt = p.n_tail;
+  const unsigned long long n_total = 8 * nt;
+  long long A1t[3], A2t[3], A1c[3], A2c[3];
+  d3s_sums<CG>(p.u, p.u, o.T, A1t, A2t);
+  d3s_sums<CG>(p.u, p.u, o.C, A1c, A2c);
+  const unsigned long long ty = d3s_tail(o.T[0], o.T[1], o.T[2]);
+  const long long eq = p.one + (d3s_block<CG>(p.u, ty) >> 3);  // all three advance: shift 0
+#pragma unroll
+  for (int H = 0; H < 8; ++H) {
+    const int h0 = H >> 2, h1 = (H >> 1) & 1, h2 = H & 1;
+    long long F;
+    if (H == 0 || H == 7) {
+      F = eq;
+    } else {
+      const int m = (h0 + h1 + h2) >= 2 ? 1 : 0;
+      const int j = h0 != m ? 0 : (h1 != m ? 1 : 2);
+      // one string advances: mean of u + 2R; two advance: mean of u + R
+      const long long k1 = m == 0 ? A1t[j] : A1c[j];
+      const long long k2 = m == 0 ? A2c[j] : A2t[j];
+      F = max((k1 >> 1) + 2 * R, (k2 >> 2) + R);
+    }
+    const unsigned long long x = (unsigned long long)H * nt + ty;
+    const long long u = ld_vec<CG>(p.u + (x < n_total / 2 ? x : n_total - 1 - x));
+    best = max(best, u + 3 * R - F);
+  }
+}
+
+template <bool INCR>
+__global__ void __launch_bounds__(kBlock) sweep_d3s_kernel(SweepParams p) {
+  const int L = p.h - 1;
+  const unsigned long long M = (1ull << L) - 1;
+  const unsigned long long n_tiles = 1ull << (3 * L - 8);
+  long long best_v = p.r_mode ? LLONG_MIN : LLONG_MAX;
+  unsigned long long best_x = ULLONG_MAX;
+  for (unsigned long long k = blockIdx.x; k < n_tiles; k += gridDim.x) {
+    unsigned long long I0, I1, I2;
+    d3s_tile(k, L, I0, I1, I2);
+    if (!d3s_tile_live(I0, I1, I2, M)) continue;  // the whole CTA skips it
+    D3sOrbit o;
+    if (d3s_rep(I0, I1, I2, M, L, threadIdx.x, o)) d3s_sweep_orbit<INCR, false>(p, o, best_v, best_x);
+  }
+  if constexpr (INCR) block_reduce_arg(best_v, best_x, p.r_mode, p.partials);
+}
+
+template <int UNUSED = 0>
+__global__ void __launch_bounds__(kBlock) check_d3s_kernel(CheckParams p) {
+  const int L = p.h - 1;
+  const unsigned long long M = (1ull << L) - 1;
+  const unsigned long long n_tiles = 1ull << (3 * L - 8);
+  const long long R = p.R_from_state ? p.state->R : p.R;
+  long long best = LLONG_MIN;
+  for (unsigned long long k = blockIdx.x; k < n_tiles; k += gridDim.x) {
+    unsigned long long I0, I1, I2;
+    d3s_tile(k, L, I0, I1, I2);
+    if (!d3s_tile_live(I0, I1, I2, M)) continue;
+    D3sOrbit o;
+    if (d3s_rep(I0, I1, I2, M, L, threadIdx.x, o)) d3s_check_orbit<false>(p, o, R, best);
+  }
+  block_reduce_max(best, p.partials);
+}
+
+// are the stored values invariant under the string permutations?  (the
+// complement holds by construction of the storage; two transpositions
+// generate the permutations)
+template <int UNUSED = 0>
+__global__ void perm_check_d3s_kernel(const long long* __restrict__ v, unsigned long long n_stored,
+                                      unsigned long long n_total, DevState* st) {
+  constexpr unsigned long long S0 = 0x4924924924924924ull;  // bits of string 0 (positions 3i + 2)
+  constexpr unsigned long long S1 = S0 >> 1, S2 = S0 >> 2;
+  for (unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_stored;
+       x += (unsigned long long)gridDim.x * blockDim.x) {
+    // exchange strings 0 and 1, and strings 1 and 2
+    unsigned long long y = (x & S2) | ((x & S0) >> 1) | ((x & S1) << 1);
+    unsigned long long z = (x & S0) | ((x & S1) >> 1) | ((x & S2) << 1);
+    if (y >= n_stored) y = n_total - 1 - y;
+    if (z >= n_stored) z = n_total - 1 - z;
+    if (v[y] != v[x] || v[z] != v[x]) atomicExch((unsigned long long*)&st->swap_bad, 1ull);
+  }
+}
+
+template <int UNUSED = 0>
+void launch_sweep_d3s(const SweepParams& p, int grid, cudaStream_t s) {
+  if (p.incr)
+    sweep_d3s_kernel<true><<<grid, kBlock, 0, s>>>(p);
+  else
+    sweep_d3s_kernel<false><<<grid, kBlock, 0, s>>>(p);
+}
+
+template <int UNUSED = 0>
+void launch_check_d3s(const CheckParams& p, int grid, cudaStream_t s) {
+  check_d3s_kernel<><<<grid, kBlock, 0, s>>>(p);
+}
+
+template <int UNUSED = 0>
+KernelSet make_d3s_set() {
+  KernelSet k{};
+  k.sigma = 2;
+  k.d = 3;
+  k.f_mode = 0;
+  k.sym = 4;
+  k.sweep = &launch_sweep_d3s<>;
+  k.check = &launch_check_d3s<>;
+  k.sweep_fn = (const void*)&sweep_d3s_kernel<false>;  // the plain sweep sizes the grid
+  k.check_fn = (const void*)&check_d3s_kernel<>;
+  k.tails_per_thread = 12;
+  // per orbit pair (12 tails, 48 stored states): 12 + 24 + 8 values read, 48 written:
+  // 15.3 B per stored state, counted as 15
+  k.sweep_algo_bytes = 15;
+  k.check_algo_bytes = 8;
+  return k;
+}
+
+}  // namespace lcs

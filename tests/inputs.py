@@ -53,6 +53,31 @@ def symmetrize(v: np.ndarray, swap: bool = False) -> np.ndarray:
     return out
 
 
+def perm_index_d3(h: int, perm) -> np.ndarray:
+    """sigma = 2, d = 3: the index with string j moved to position perm[j]."""
+    n = 8 ** h
+    x = np.arange(n, dtype=np.int64)
+    y = np.zeros(n, dtype=np.int64)
+    for j in range(3):
+        for i in range(h):
+            y |= ((x >> (3 * i + 2 - j)) & 1) << (3 * i + 2 - perm[j])
+    return y
+
+
+def perm_symmetrize_d3(v: np.ndarray, h: int) -> np.ndarray:
+    """sigma = 2, d = 3: the smallest value over each orbit of the string
+    permutations and the complement (a vector with both symmetries)."""
+    import itertools
+
+    n = v.size
+    out = v.copy()
+    for perm in itertools.permutations(range(3)):
+        y = perm_index_d3(h, perm)
+        out = np.minimum(out, v[y])
+        out = np.minimum(out, v[n - 1 - y])
+    return out
+
+
 def swap_symmetrize(v: np.ndarray, sigma: int, h: int) -> np.ndarray:
     """d = 2, any sigma: the smaller value of each pair of states exchanged by the string swap."""
     return np.minimum(v, v[swap_index_d2(sigma, h)])
@@ -67,6 +92,8 @@ def random_fx(sigma, d, h, seed, base_units=200.0, spread_units=4.0, frac_bits=K
     v = (base_units + spread_units * rng.random(n)) * one
     v = v.astype(np.int64)
     v += rng.integers(0, 1 << 20, size=n, dtype=np.int64)  # low-order noise below the unit
+    if sigma == 2 and d == 3 and swap:
+        return perm_symmetrize_d3(v, h)
     if sigma != 2 and swap and not symmetric:
         if d != 2:
             raise ValueError("the swap needs d = 2")
@@ -87,7 +114,9 @@ def random_history(sigma, d, h, seed, step_units=0.4, frac_bits=K_DEFAULT, symme
     out = []
     for k in range(d):
         jitter = rng.integers(0, one // 16, size=n, dtype=np.int64)
-        if sigma != 2 and swap and not symmetric:
+        if sigma == 2 and d == 3 and swap:
+            jitter = perm_symmetrize_d3(jitter, h)
+        elif sigma != 2 and swap and not symmetric:
             jitter = swap_symmetrize(jitter, sigma, h)
         elif symmetric or swap:
             jitter = symmetrize(jitter, swap)

@@ -144,6 +144,28 @@ def test_d2_swap_zero_start_every_iteration_checked(lb, orc, s, h, r_mode):
     _check_run_against_oracle(lb, orc, s, 2, h, 12, 1, 0, r_mode)
 
 
+@pytest.mark.parametrize("h", [4, 5, 6])
+@pytest.mark.parametrize("perm", [False, True])
+def test_d3_permutation_paths_bit_exact(lb, orc, h, perm):
+    """sigma = 2, d = 3: starts symmetric under the string permutations (and
+    the complement) run the kernels that read each orbit's values once; starts
+    with the complement symmetry only run the generic kernels.  Both exact."""
+    hist = inputs.random_history(2, 3, h, seed=90 + h, symmetric=True, swap=perm)
+    start = [hist[2], hist[1], hist[0]]  # oldest first
+    _check_run_against_oracle(lb, orc, 2, 3, h, 8, 3, 1, 0, start=start)
+
+
+@pytest.mark.parametrize("h,r_mode", [(4, 0), (5, 1), (7, 0)])
+def test_d3_permutation_zero_start_every_iteration_checked(lb, orc, h, r_mode):
+    _check_run_against_oracle(lb, orc, 2, 3, h, 10, 1, 1, r_mode)
+
+
+def test_d3_permutation_kernel_is_used_and_counted(lb):
+    with lb.LcsBound(2, 3, 6, timing=1) as hnd:
+        hnd.iterate(4)
+        assert hnd.stats()["sweep_bytes"] == 4 * 15 * (8 ** 6 // 2)
+
+
 def test_d2_swap_kernel_is_used_and_counted(lb):
     with lb.LcsBound(3, 2, 6, timing=1) as hnd:
         hnd.iterate(5)
