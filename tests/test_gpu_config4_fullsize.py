@@ -1,0 +1,117 @@
+"""GPU parity at the float32 configuration's full sizes, in the kernels the
+benchmark runs there: (sigma, d, h) = (2, 3, 8) (2^24 states, the
+permutation-aware kernels on the complement half) and (3, 2, 8) (3^16 states,
+the swap-aware kernels).
+
+One sweep from a seeded start that has the symmetries: the start is drawn and
+symmetrised on the device with plain torch index arithmetic (input shaping,
+none of the method's arithmetic), copied to the host for the oracle, and the
+oracle evaluates F over sampled ranges of states (both ends and random
+ranges), bit for bit.  The zero start runs the configuration's 1500
+iterations and must reproduce Appendix C's bound.
+"""
+import itertools
+import math
+
+import numpy as np
+import pytest
+
+from conftest import load_golden
+
+pytestmark = pytest.mark.gpu
+
+K = 44
+
+
+@pytest.fixture(scope="module")
+def env():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2407_10925_gb300 as lb
+
+    lb.lib()
+    return torch, lb
+
+
+def _orbit_images(torch, s, d, h):
+    """Index maps of the symmetries the kernels use: the string swap for d = 2,
+    the string permutations and the complement for sigma = 2, d = 3."""
+    n = s ** (d * h)
+    x = torch.arange(n, dtype=torch.int64, device="cuda")
+    if d == 2:
+        y = torch.zeros_like(x)
+        r = x.clone()
+        m = 1
+        for _ in range(h):
+            pd = r % (s * s)
+            r = r // (s * s)
+            y += ((pd % s) * s + pd // s) * m
+            m *= s * s
+        return [y]
+    imgs = []
+    for perm in itertools.permutations(range(3)):
+        y = torch.zeros_like(x)
+        for j in range(3):
+            for i in range(h):
+                y |= ((x >> (3 * i + 2 - j)) & 1) << (3 * i + 2 - perm[j])
+        imgs.append(y)
+        imgs.append((n - 1) - y)
+    return imgs
+
+
+def _symmetric_history(torch, s, d, h, seed):
+    n = s ** (d * h)
+    gen = torch.Generator(device="cuda")
+    gen.manual_seed(seed)
+    imgs = _orbit_images(torch, s, d, h)
+
+    def sym(v):
+        out = v.clone()
+        for y in imgs:
+            out = torch.minimum(out, v[y])
+        return out
+
+    one = 1 << K
+    base = sym((200 << K) + torch.randint(0, 4 << K, (n,), device="cuda", generator=gen, dtype=torch.int64))
+    hist = []
+    for k in range(d):
+        jitter = sym(torch.randint(0, one // 16, (n,), device="cuda", generator=gen, dtype=torch.int64))
+        hist.append(base - int(k * 0.4 * one) - jitter)
+    for y in imgs:  # the start really has the symmetries
+        assert torch.equal(hist[0][y], hist[0])
+    return hist
+
+
+CASES = [(2, 3, 8, 1), (3, 2, 8, 0)]  # sigma, d, h, complement-symmetric storage
+
+
+@pytest.mark.parametrize("s,d,h,sym", CASES)
+def test_full_size_sweep_from_symmetric_start_sampled(env, orc, s, d, h, sym):
+    torch, lb = env
+    n = s ** (d * h)
+    hist = _symmetric_history(torch, s, d, h, seed=4000 + 10 * s + d)
+    with lb.LcsBound(s, d, h, check_every=0, symmetry=sym) as hnd:
+        hnd.set_start_fx(hist)  # hist[0] is the newest
+        hnd.iterate(1)
+        out = torch.empty(n, dtype=torch.int64, device="cuda")
+        hnd.export_fx(0, out)
+    got = out.cpu().numpy()
+    host = [v.cpu().numpy() for v in hist]
+    rng = np.random.default_rng(s * 100 + d)
+    ranges = [(0, 4096), (n - 4096, n)] + [(int(a), int(a) + 2048) for a in rng.integers(0, n - 2048, size=24)]
+    for a, b in ranges:
+        want = orc.F(s, d, h, host, arith="fx", x0=a, x1=b)
+        assert np.array_equal(got[a:b], want), (a, np.flatnonzero(got[a:b] != want)[:10])
+
+
+@pytest.mark.parametrize("s,d,h,sym", CASES)
+def test_full_size_zero_start_reaches_appendix_c(env, s, d, h, sym):
+    torch, lb = env
+    printed = {(int(r[0]), int(r[1]), int(r[2])): r[3] for r in load_golden("appendix_c.txt")}[(s, d, h)]
+    with lb.LcsBound(s, d, h, check_every=100, symmetry=sym) as hnd:
+        hnd.iterate(1500)
+        bound = hnd.read()[0]
+    assert math.floor(bound * 1e6) / 1e6 == pytest.approx(float(printed), abs=1e-12) or \
+        round(bound, 6) == pytest.approx(float(printed), abs=1e-12)
