@@ -9,7 +9,8 @@
 // string 0 is 0 and the prefix q = c >> 2 (h - np) is below 2^(2 np - 1).
 // The kernel evaluates the network once per prefix into a table T[q]; a
 // gather then writes a full-length vector by looking T up at each state's
-// canonical prefix.  For h >= 12 the table has 2^23 rows whatever h is.
+// canonical prefix.  For h >= 12 the table has 2^23 rows whatever h is, of
+// which about half can be canonical prefixes: tiles with none are skipped.
 //
 // One CTA per SM, persistent over tiles of 128 rows; 256 threads:
 //   layer 1 (SIMT, fp32): thread j holds the 48 one-hot weights of hidden
@@ -195,6 +196,16 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_table_tc_kernel(TcParams p)
   const uint32_t a_base = smem_u32(sA), b_base = smem_u32(sW2);
   uint32_t parity = 0;
   for (long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+    if (p.np == kHin) {
+      // A canonical form c is at most its swap and its complemented swap, so
+      // its prefix q is at most theirs; the 128 rows of a tile share positions
+      // 0..7 (the top 16 bits X of q), and when X already exceeds the swap or
+      // the complemented swap of X, no row of the tile is a canonical prefix:
+      // the gather never reads it, and the tile is skipped (about half of them).
+      const uint32_t X = (uint32_t)(tile * kTileRows) >> 8;
+      const uint32_t sw = ((X >> 1) & 0x5555u) | ((X & 0x5555u) << 1);
+      if (X > sw || X > 0xFFFFu - sw) continue;
+    }
     // ---- layer 1 into shared memory (bf16); the sum runs over the features in
     // order, position 0 first, as in the FP32 path
     if (p.np == kHin) {
