@@ -340,12 +340,14 @@ def run_warm(args, cfg, world, rank, local_rank):
             lb.lcs_bound_export_fx(hnd.hnd, 0, v)
             return v, hnd.read()
 
-    def run_to(target, start=None, limit=6000):
+    def run_to(target, start=None, limit=6000, stored=False):
         """iterations (a multiple of `chunk`) and seconds until the bound reaches target"""
         sync()
         t0 = time.perf_counter()
         with lb.LcsBound(2, 2, H, check_every=chunk) as hnd:
-            if start is not None:
+            if start is not None and stored:
+                hnd.set_start_stored_fx(start)
+            elif start is not None:
                 hnd.set_start(start)
             it, bound = 0, 0.0
             while it < limit:
@@ -375,11 +377,12 @@ def run_warm(args, cfg, world, rank, local_rank):
     loss = mlp.train([data[h][0] for h in train_h], train_h, steps=cfg["train_steps"], batch=4096, lr=1e-3)
     t_train = time.perf_counter() - t0
 
-    newest = torch.empty(4 ** H, dtype=torch.float64, device="cuda")
-    older = torch.empty(4 ** H, dtype=torch.float64, device="cuda")
+    # the learned start goes straight into the handle's stored form (fixed point)
+    newest_fx = torch.empty(4 ** H // 2, dtype=torch.int64, device="cuda")
+    older_fx = torch.empty(4 ** H // 2, dtype=torch.int64, device="cuda")
     sync()
     t0 = time.perf_counter()
-    mlp.start_vectors(H, r_hat, newest, older)
+    mlp.start_vectors_stored_fx(H, r_hat, newest_fx, older_fx)
     t_infer = time.perf_counter() - t0
     dummy = torch.empty(1, dtype=torch.float32, device="cuda")
     t_tab = []
@@ -388,7 +391,10 @@ def run_warm(args, cfg, world, rank, local_rank):
         t0 = time.perf_counter()
         mlp.predict_bf16(H, 0, 0, dummy)
         t_tab.append(time.perf_counter() - t0)
-    it_mlp, t_mlp, b_mlp = run_to(target, start=[newest, older])
+    it_mlp, t_mlp, b_mlp = run_to(target, start=[newest_fx, older_fx], stored=True)
+    del newest_fx, older_fx
+    newest = torch.empty(4 ** H, dtype=torch.float64, device="cuda")
+    older = torch.empty(4 ** H, dtype=torch.float64, device="cuda")
 
     sync()
     t0 = time.perf_counter()
@@ -408,6 +414,7 @@ def run_warm(args, cfg, world, rank, local_rank):
         "truncation_lift": {"iterations": it_lift, "seconds": t_lift + t_lift_run, "bound": b_lift},
         "mlp": {"iterations": it_mlp, "seconds_iterating": t_mlp, "seconds_inference_bf16": t_infer,
                 "seconds_table_kernel_min_of_3": min(t_tab), "table_rows": 2 ** (2 * min(H, 12) - 1),
+                "start_form": "stored half, fixed point (lcs_mlp_start_vectors_stored_fx + set_start_stored_fx)",
                 "seconds_total_with_inference": t_infer + t_mlp, "bound": b_mlp,
                 "train_seconds": t_train, "train_steps": cfg["train_steps"], "loss_before": loss0,
                 "loss_after": loss, "training_data_seconds": t_data},

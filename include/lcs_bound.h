@@ -337,6 +337,12 @@ lcs_status lcs_mlp_predict_bf16(lcs_mlp_t* m, int h, uint64_t base, int64_t n, f
  * from the same BF16 table: older = u_hat, newest = u_hat + r_hat.
  * Synchronous. */
 lcs_status lcs_mlp_start_vectors(lcs_mlp_t* m, int h, double r_hat, double* newest_dev, double* older_dev);
+/* The same start for lcs_bound_set_start_stored_fx of a complement-symmetric
+ * sigma = d = 2 handle: 4^h / 2 fixed-point values each (states x < 4^h / 2),
+ * converted as lcs_bound_set_start converts the doubles (rounded down, K =
+ * frac_bits, 0 = 44): a quarter of the bytes.  Device pointers; synchronous. */
+lcs_status lcs_mlp_start_vectors_stored_fx(lcs_mlp_t* m, int h, double r_hat, int frac_bits, int64_t* newest_dev,
+                                           int64_t* older_dev);
 void lcs_mlp_destroy(lcs_mlp_t* m);
 
 /* The non-learned control for the warm start (sigma = d = 2): a start for

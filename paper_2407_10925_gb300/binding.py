@@ -130,6 +130,7 @@ def lib():
                 "lcs_mlp_train": [vp, i32, vp, vp, i64, i32, ctypes.c_float, u64, i32, P(ctypes.c_float)],
                 "lcs_mlp_predict": [vp, i32, i64, vp, vp],
                 "lcs_mlp_start_vectors": [vp, i32, dbl, vp, vp],
+                "lcs_mlp_start_vectors_stored_fx": [vp, i32, dbl, i32, vp, vp],
                 "lcs_mlp_predict_bf16": [vp, i32, u64, i64, vp],
                 "lcs_lift_prefix": [i32, i32, vp, i32, dbl, vp, vp],
                 "lcs_fp32_experiment": [i32, i32, i32, i64, dbl, vp, P(dbl)],
@@ -563,6 +564,15 @@ class LcsMlp:
         if not (dn and do):
             raise TypeError("start vectors must be CUDA tensors")
         _check(lib().lcs_mlp_start_vectors(self.hnd, h, float(r_hat), pn, po), "lcs_mlp_start_vectors")
+
+    def start_vectors_stored_fx(self, h, r_hat, newest_dev, older_dev, frac_bits=44):
+        """The start in a complement-symmetric handle's stored form, fixed point (int64 CUDA tensors of 4^h / 2)."""
+        pn, a = _ptr_and_kind(newest_dev, np.int64)
+        po, b = _ptr_and_kind(older_dev, np.int64)
+        if not (a and b):
+            raise TypeError("start_vectors_stored_fx writes CUDA tensors")
+        _check(lib().lcs_mlp_start_vectors_stored_fx(self.hnd, h, float(r_hat), frac_bits, pn, po),
+               "lcs_mlp_start_vectors_stored_fx")
 
 
 # ---------------------------------------------------------------------------

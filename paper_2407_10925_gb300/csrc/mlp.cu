@@ -270,6 +270,19 @@ __global__ void mlp_table_start_kernel(const float* __restrict__ T, int h, int n
   }
 }
 
+// the same start in the handle's stored form (states x < 4^h / 2) and fixed
+// point, converted as set_start converts doubles (rounded down)
+__global__ void mlp_table_start_fx_kernel(const float* __restrict__ T, int h, int np, long long n_stored, double r_hat,
+                                          double scale, long long* __restrict__ newest, long long* __restrict__ older) {
+  const int shift = 2 * (h - np);
+  for (long long x = (long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_stored;
+       x += (long long)gridDim.x * blockDim.x) {
+    const double u = (double)T[mlp_canonical((unsigned long long)x, h) >> shift];
+    older[x] = __double2ll_rd(u * scale);
+    newest[x] = __double2ll_rd((u + r_hat) * scale);
+  }
+}
+
 __global__ void mlp_table_predict_kernel(const float* __restrict__ T, int h, int np, unsigned long long base,
                                          long long n, float* __restrict__ out) {
   const int shift = 2 * (h - np);
@@ -575,6 +588,21 @@ lcs_status lcs_mlp_start_vectors(lcs_mlp_t* M, int h, double r_hat, double* newe
   if (st) return st;
   mlp_table_start_kernel<<<4096, 256, 0, M->stream>>>(M->table, h, std::min(h, kHin), 1ll << (2 * h), r_hat,
                                                       newest_dev, older_dev);
+  M_CUDA(cudaGetLastError());
+  M_CUDA(cudaStreamSynchronize(M->stream));
+  return LCS_OK;
+}
+
+lcs_status lcs_mlp_start_vectors_stored_fx(lcs_mlp_t* M, int h, double r_hat, int frac_bits, int64_t* newest_dev,
+                                           int64_t* older_dev) {
+  if (!M || !newest_dev || !older_dev || h < 1 || h > 16) return mfail(LCS_EINVAL, "bad argument");
+  if (frac_bits == 0) frac_bits = 44;
+  if (frac_bits < 8 || frac_bits > 56) return mfail(LCS_EINVAL, "frac_bits %d outside 8..56", frac_bits);
+  lcs_status st = build_table(M, h);
+  if (st) return st;
+  mlp_table_start_fx_kernel<<<4096, 256, 0, M->stream>>>(M->table, h, std::min(h, kHin), 1ll << (2 * h - 1), r_hat,
+                                                         std::ldexp(1.0, frac_bits), (long long*)newest_dev,
+                                                         (long long*)older_dev);
   M_CUDA(cudaGetLastError());
   M_CUDA(cudaStreamSynchronize(M->stream));
   return LCS_OK;

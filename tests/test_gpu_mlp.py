@@ -180,3 +180,29 @@ def test_lift_prefix_cuts_tuples(lb):
     want = (src[x >> (2 * (h_to - h_from))] - src[0]).astype(np.float64) * 2.0 ** -44
     assert np.array_equal(older.cpu().numpy(), want)
     assert np.array_equal(newest.cpu().numpy(), want + r_hat)
+
+
+def test_stored_fixed_point_start_equals_the_double_start(lb):
+    """The stored-form fixed-point start is the double start converted as set_start converts it."""
+    import torch
+
+    h, r_hat = 10, 0.3906
+    n = 4 ** h
+    with lb.LcsMlp(seed=9) as m:
+        newest = torch.empty(n, dtype=torch.float64, device="cuda")
+        older = torch.empty(n, dtype=torch.float64, device="cuda")
+        m.start_vectors(h, r_hat, newest, older)
+        nf = torch.empty(n // 2, dtype=torch.int64, device="cuda")
+        of = torch.empty(n // 2, dtype=torch.int64, device="cuda")
+        m.start_vectors_stored_fx(h, r_hat, nf, of)
+        torch.cuda.synchronize()
+    scale = 2.0 ** 44
+    assert np.array_equal(nf.cpu().numpy(), np.floor(newest.cpu().numpy()[: n // 2] * scale).astype(np.int64))
+    assert np.array_equal(of.cpu().numpy(), np.floor(older.cpu().numpy()[: n // 2] * scale).astype(np.int64))
+    with lb.LcsBound(2, 2, h, check_every=10) as a, lb.LcsBound(2, 2, h, check_every=10) as b:
+        a.set_start([newest, older])
+        b.set_start_stored_fx([nf, of])
+        a.iterate(30)
+        b.iterate(30)
+        assert np.array_equal(a.export_fx(0), b.export_fx(0))
+        assert a.read() == b.read()
