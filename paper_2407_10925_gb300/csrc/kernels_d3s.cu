@@ -4,9 +4,10 @@
 
 namespace lcs {
 
-const KernelSet* kernels_d3s() {
-  static const KernelSet k = make_d3s_set<>();
-  return &k;
+const KernelSet* kernels_d3s(int f_mode) {
+  static const KernelSet k0 = make_d3s_set<false>();
+  static const KernelSet k1 = make_d3s_set<true>();
+  return f_mode ? &k1 : &k0;
 }
 
 // smallest h the 4 x 8 x 8 tiles fit (L = h - 1 >= 3)

@@ -138,6 +138,27 @@ __device__ __forceinline__ long long d3s_block(const long long* v3, unsigned lon
   return s;
 }
 
+// f_mode 1 also advances one string while the other two keep different
+// heads: B1(X, k, o) = sum over c of v_{t-1}[(0 X_o, 1 X_r, X_k c)], r the
+// third index (string 0 keeps head 0, string 1 head 1).  For ~X the same sum
+// is B1(X, k, r): complement every letter, then exchange strings 0 and 1.
+template <bool CG>
+__device__ __forceinline__ void d3s_b1(const long long* v1, const unsigned long long (&X)[3], int L,
+                                       long long (&B1)[3][3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k)
+#pragma unroll
+    for (int o = 0; o < 3; ++o) {
+      if (o == k) {
+        B1[k][o] = 0;
+        continue;
+      }
+      const int r = 3 - k - o;
+      const longlong2 q = d3s_ld2<CG>(v1, d3s_tail(X[o], (1ull << L) | X[r], X[k] << 1));
+      B1[k][o] = q.x + q.y;
+    }
+}
+
 // the six permutations of three components
 __device__ __forceinline__ int d3s_perm(int p, int j) {
   // (0,1,2) (0,2,1) (1,0,2) (1,2,0) (2,0,1) (2,1,0)
@@ -145,13 +166,15 @@ __device__ __forceinline__ int d3s_perm(int p, int j) {
   return P[p][j];
 }
 
-template <bool INCR, bool CG>
-__device__ __forceinline__ void d3s_sweep_orbit(const SweepParams& p, const D3sOrbit& o, long long& best_v,
+template <bool INCR, bool FALL, bool CG>
+__device__ __forceinline__ void d3s_sweep_orbit(const SweepParams& p, const D3sOrbit& o, int L, long long& best_v,
                                                 unsigned long long& best_x) {
   const unsigned long long nt = p.n_tail;
   long long A1t[3], A2t[3], A1c[3], A2c[3];
   d3s_sums<CG>(p.prev[0], p.prev[1], o.T, A1t, A2t);
   d3s_sums<CG>(p.prev[0], p.prev[1], o.C, A1c, A2c);
+  long long B1t[3][3];
+  if constexpr (FALL) d3s_b1<CG>(p.prev[0], o.T, L, B1t);
   const long long B = d3s_block<CG>(p.prev[2], d3s_tail(o.T[0], o.T[1], o.T[2]));
   const long long e000 = p.one + (B >> 3);
 #pragma unroll
@@ -171,18 +194,35 @@ __device__ __forceinline__ void d3s_sweep_orbit(const SweepParams& p, const D3sO
 #pragma unroll
       for (int r = 0; r < q; ++r) dup |= seen[r] == ty;
       if (dup) continue;
-      // heads 001 and 010: majority 0, minority string 2 resp. 1;
-      // heads 011: majority 1, minority string 0
-      const long long v001 = max(4 * A1s[p2], 2 * A2o[p2]) >> 3;
-      const long long v010 = max(4 * A1s[p1], 2 * A2o[p1]) >> 3;
-      const long long v011 = max(4 * A1o[p0], 2 * A2s[p0]) >> 3;
+      long long v000, v001, v010, v011;
+      if constexpr (!FALL) {
+        // heads 001 and 010: majority 0, minority string 2 resp. 1;
+        // heads 011: majority 1, minority string 0
+        v000 = e000;
+        v001 = max(4 * A1s[p2], 2 * A2o[p2]) >> 3;
+        v010 = max(4 * A1s[p1], 2 * A2o[p1]) >> 3;
+        v011 = max(4 * A1o[p0], 2 * A2s[p0]) >> 3;
+      } else {
+        // every non-empty advance set at the common denominator 8: one string
+        // (4 x its pair sum), two strings (2 x the quad sum), all three (the
+        // block, + 8 one when the heads agree)
+        auto b1 = [&](int k, int oo) { return side == 0 ? B1t[k][oo] : B1t[k][3 - k - oo]; };
+        v000 = max(max(4 * max(max(A1s[0], A1s[1]), A1s[2]), 2 * max(max(A2s[0], A2s[1]), A2s[2])),
+                   B + 8 * p.one) >> 3;
+        v001 = max(max(4 * max(max(b1(p0, p1), b1(p1, p0)), A1s[p2]),
+                       2 * max(max(A2s[p0], A2s[p1]), A2o[p2])), B) >> 3;
+        v010 = max(max(4 * max(max(b1(p0, p2), b1(p2, p0)), A1s[p1]),
+                       2 * max(max(A2s[p0], A2s[p2]), A2o[p1])), B) >> 3;
+        v011 = max(max(4 * max(max(A1o[p0], b1(p1, p0)), b1(p2, p0)),
+                       2 * max(max(A2s[p0], A2o[p1]), A2o[p2])), B) >> 3;
+      }
       const unsigned long long x0 = ty, x1 = nt + ty, x2 = 2 * nt + ty, x3 = 3 * nt + ty;
-      p.out[x0] = e000;
+      p.out[x0] = v000;
       p.out[x1] = v001;
       p.out[x2] = v010;
       p.out[x3] = v011;
       if constexpr (INCR) {
-        const long long i0 = e000 - ld_vec<CG>(p.prev[0] + x0);
+        const long long i0 = v000 - ld_vec<CG>(p.prev[0] + x0);
         const long long i1 = v001 - ld_vec<CG>(p.prev[0] + x1);
         const long long i2 = v010 - ld_vec<CG>(p.prev[0] + x2);
         const long long i3 = v011 - ld_vec<CG>(p.prev[0] + x3);
@@ -196,9 +236,10 @@ __device__ __forceinline__ void d3s_sweep_orbit(const SweepParams& p, const D3sO
 }
 
 // W = u + 3R - F(u + 2R, u + R, u) at the 8 heads of tau: every class of
-// equal values of the orbit pair has a member with tail tau
-template <bool CG>
-__device__ __forceinline__ void d3s_check_orbit(const CheckParams& p, const D3sOrbit& o, long long R,
+// equal values of the orbit pair has a member with tail tau.  (f_mode 1: at
+// the 4 stored heads of tau and of ~tau, the same classes.)
+template <bool FALL, bool CG>
+__device__ __forceinline__ void d3s_check_orbit(const CheckParams& p, const D3sOrbit& o, int L, long long R,
                                                 long long& best) {
   const unsigned long long nt = p.n_tail;
   const unsigned long long n_total = 8 * nt;
@@ -206,7 +247,35 @@ __device__ __forceinline__ void d3s_check_orbit(const CheckParams& p, const D3sO
   d3s_sums<CG>(p.u, p.u, o.T, A1t, A2t);
   d3s_sums<CG>(p.u, p.u, o.C, A1c, A2c);
   const unsigned long long ty = d3s_tail(o.T[0], o.T[1], o.T[2]);
-  const long long eq = p.one + (d3s_block<CG>(p.u, ty) >> 3);  // all three advance: shift 0
+  const long long Bs = d3s_block<CG>(p.u, ty);
+  if constexpr (FALL) {
+    // one string advances: mean of u + 2R; two: mean of u + R; three: mean of u
+    long long B1t[3][3];
+    d3s_b1<CG>(p.u, o.T, L, B1t);
+    const long long K3 = Bs >> 3;
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const long long* A1s = side == 0 ? A1t : A1c;
+      const long long* A2s = side == 0 ? A2t : A2c;
+      const long long* A1o = side == 0 ? A1c : A1t;
+      const long long* A2o = side == 0 ? A2c : A2t;
+      auto b1 = [&](int k, int oo) { return side == 0 ? B1t[k][oo] : B1t[k][3 - k - oo]; };
+      const unsigned long long t = side == 0 ? ty : d3s_tail(o.C[0], o.C[1], o.C[2]);
+      const long long F[4] = {
+          max(max((max(max(A1s[0], A1s[1]), A1s[2]) >> 1) + 2 * R, (max(max(A2s[0], A2s[1]), A2s[2]) >> 2) + R),
+              K3 + p.one),
+          max(max((max(max(b1(0, 1), b1(1, 0)), A1s[2]) >> 1) + 2 * R, (max(max(A2s[0], A2s[1]), A2o[2]) >> 2) + R),
+              K3),
+          max(max((max(max(b1(0, 2), b1(2, 0)), A1s[1]) >> 1) + 2 * R, (max(max(A2s[0], A2s[2]), A2o[1]) >> 2) + R),
+              K3),
+          max(max((max(max(A1o[0], b1(1, 0)), b1(2, 0)) >> 1) + 2 * R, (max(max(A2s[0], A2o[1]), A2o[2]) >> 2) + R),
+              K3)};
+#pragma unroll
+      for (int H = 0; H < 4; ++H) best = max(best, ld_vec<CG>(p.u + (unsigned long long)H * nt + t) + 3 * R - F[H]);
+    }
+    return;
+  }
+  const long long eq = p.one + (Bs >> 3);  // all three advance: shift 0
 #pragma unroll
   for (int H = 0; H < 8; ++H) {
     const int h0 = H >> 2, h1 = (H >> 1) & 1, h2 = H & 1;
@@ -227,7 +296,7 @@ __device__ __forceinline__ void d3s_check_orbit(const CheckParams& p, const D3sO
   }
 }
 
-template <bool INCR>
+template <bool INCR, bool FALL>
 __global__ void __launch_bounds__(kBlock) sweep_d3s_kernel(SweepParams p) {
   const int L = p.h - 1;
   const unsigned long long M = (1ull << L) - 1;
@@ -239,12 +308,12 @@ __global__ void __launch_bounds__(kBlock) sweep_d3s_kernel(SweepParams p) {
     d3s_tile(k, L, I0, I1, I2);
     if (!d3s_tile_live(I0, I1, I2, M)) continue;  // the whole CTA skips it
     D3sOrbit o;
-    if (d3s_rep(I0, I1, I2, M, L, threadIdx.x, o)) d3s_sweep_orbit<INCR, false>(p, o, best_v, best_x);
+    if (d3s_rep(I0, I1, I2, M, L, threadIdx.x, o)) d3s_sweep_orbit<INCR, FALL, false>(p, o, L, best_v, best_x);
   }
   if constexpr (INCR) block_reduce_arg(best_v, best_x, p.r_mode, p.partials);
 }
 
-template <int UNUSED = 0>
+template <bool FALL>
 __global__ void __launch_bounds__(kBlock) check_d3s_kernel(CheckParams p) {
   const int L = p.h - 1;
   const unsigned long long M = (1ull << L) - 1;
@@ -256,7 +325,7 @@ __global__ void __launch_bounds__(kBlock) check_d3s_kernel(CheckParams p) {
     d3s_tile(k, L, I0, I1, I2);
     if (!d3s_tile_live(I0, I1, I2, M)) continue;
     D3sOrbit o;
-    if (d3s_rep(I0, I1, I2, M, L, threadIdx.x, o)) d3s_check_orbit<false>(p, o, R, best);
+    if (d3s_rep(I0, I1, I2, M, L, threadIdx.x, o)) d3s_check_orbit<FALL, false>(p, o, L, R, best);
   }
   block_reduce_max(best, p.partials);
 }
@@ -280,34 +349,34 @@ __global__ void perm_check_d3s_kernel(const long long* __restrict__ v, unsigned 
   }
 }
 
-template <int UNUSED = 0>
+template <bool FALL>
 void launch_sweep_d3s(const SweepParams& p, int grid, cudaStream_t s) {
   if (p.incr)
-    sweep_d3s_kernel<true><<<grid, kBlock, 0, s>>>(p);
+    sweep_d3s_kernel<true, FALL><<<grid, kBlock, 0, s>>>(p);
   else
-    sweep_d3s_kernel<false><<<grid, kBlock, 0, s>>>(p);
+    sweep_d3s_kernel<false, FALL><<<grid, kBlock, 0, s>>>(p);
 }
 
-template <int UNUSED = 0>
+template <bool FALL>
 void launch_check_d3s(const CheckParams& p, int grid, cudaStream_t s) {
-  check_d3s_kernel<><<<grid, kBlock, 0, s>>>(p);
+  check_d3s_kernel<FALL><<<grid, kBlock, 0, s>>>(p);
 }
 
-template <int UNUSED = 0>
+template <bool FALL>
 KernelSet make_d3s_set() {
   KernelSet k{};
   k.sigma = 2;
   k.d = 3;
-  k.f_mode = 0;
+  k.f_mode = FALL ? 1 : 0;
   k.sym = 4;
-  k.sweep = &launch_sweep_d3s<>;
-  k.check = &launch_check_d3s<>;
-  k.sweep_fn = (const void*)&sweep_d3s_kernel<false>;  // the plain sweep sizes the grid
-  k.check_fn = (const void*)&check_d3s_kernel<>;
+  k.sweep = &launch_sweep_d3s<FALL>;
+  k.check = &launch_check_d3s<FALL>;
+  k.sweep_fn = (const void*)&sweep_d3s_kernel<false, FALL>;  // the plain sweep sizes the grid
+  k.check_fn = (const void*)&check_d3s_kernel<FALL>;
   k.tails_per_thread = 12;
-  // per orbit pair (12 tails, 48 stored states): 12 + 24 + 8 values read, 48 written:
-  // 15.3 B per stored state, counted as 15
-  k.sweep_algo_bytes = 15;
+  // per orbit pair (12 tails, 48 stored states): 12 + 24 + 8 values read (f_mode 1:
+  // 12 more), 48 written: 15.3 B (17.3 B) per stored state, counted as 15 (17)
+  k.sweep_algo_bytes = FALL ? 17 : 15;
   k.check_algo_bytes = 8;
   return k;
 }

@@ -73,9 +73,9 @@ RUN_CASES = [
 ]
 
 
-def _check_run_against_oracle(lb, orc, s, d, h, iters, check_every, symmetry, r_mode, start=None):
-    want = orc.run(s, d, h, iters, arith="fx", check_every=check_every, r_mode=r_mode, start=start)
-    with lb.LcsBound(s, d, h, check_every=check_every, symmetry=symmetry, r_mode=r_mode) as hnd:
+def _check_run_against_oracle(lb, orc, s, d, h, iters, check_every, symmetry, r_mode, start=None, f_mode=0):
+    want = orc.run(s, d, h, iters, arith="fx", check_every=check_every, r_mode=r_mode, start=start, f_mode=f_mode)
+    with lb.LcsBound(s, d, h, check_every=check_every, symmetry=symmetry, r_mode=r_mode, f_mode=f_mode) as hnd:
         if start is not None:
             # start[k] is v_k (oldest first); the library takes newest first
             hnd.set_start_fx([start[d - 1 - k] for k in range(d)])
@@ -160,10 +160,27 @@ def test_d3_permutation_zero_start_every_iteration_checked(lb, orc, h, r_mode):
     _check_run_against_oracle(lb, orc, 2, 3, h, 10, 1, 1, r_mode)
 
 
+@pytest.mark.parametrize("h,perm", [(4, True), (5, True), (5, False)])
+def test_d3_permutation_all_subsets_bit_exact(lb, orc, h, perm):
+    """f_mode 1 (every non-empty advance set) through the permutation-aware
+    kernels (symmetric starts) and the generic ones (complement only)."""
+    hist = inputs.random_history(2, 3, h, seed=95 + h, symmetric=True, swap=perm)
+    start = [hist[2], hist[1], hist[0]]
+    _check_run_against_oracle(lb, orc, 2, 3, h, 8, 3, 1, 0, start=start, f_mode=1)
+
+
+@pytest.mark.parametrize("h,r_mode", [(4, 0), (6, 1)])
+def test_d3_permutation_all_subsets_zero_start(lb, orc, h, r_mode):
+    _check_run_against_oracle(lb, orc, 2, 3, h, 10, 1, 1, r_mode, f_mode=1)
+
+
 def test_d3_permutation_kernel_is_used_and_counted(lb):
     with lb.LcsBound(2, 3, 6, timing=1) as hnd:
         hnd.iterate(4)
         assert hnd.stats()["sweep_bytes"] == 4 * 15 * (8 ** 6 // 2)
+    with lb.LcsBound(2, 3, 6, timing=1, f_mode=1) as hnd:
+        hnd.iterate(4)
+        assert hnd.stats()["sweep_bytes"] == 4 * 17 * (8 ** 6 // 2)
 
 
 def test_d2_swap_kernel_is_used_and_counted(lb):
