@@ -26,6 +26,7 @@ import multiprocessing as mp
 import os
 import statistics
 import subprocess
+import tempfile
 import sys
 import time
 
@@ -122,7 +123,9 @@ class ClockSampler:
     def __init__(self, gpu_index):
         self.gpu = gpu_index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_gpu{gpu_index}.csv")
+        # the raw samples go to LCS_CLOCKS_DIR (default: the temporary directory)
+        out_dir = os.environ.get("LCS_CLOCKS_DIR", tempfile.gettempdir())
+        self.path = os.path.join(out_dir, f"lcs_clocks_gpu{gpu_index}_{os.getpid()}.csv")
 
     def __enter__(self):
         try:

@@ -166,73 +166,78 @@ __device__ __forceinline__ int d3s_perm(int p, int j) {
   return P[p][j];
 }
 
+// the stored outputs of one side of an orbit pair: the distinct permutations
+// Y of X (tau or ~tau) at the 4 stored heads.  A1s/A2s are this side's sums,
+// A1o/A2o the complement side's; b1(k, o) is this side's B1 (f_mode 1).
+template <bool INCR, bool FALL, bool CG, class B1F>
+__device__ __forceinline__ void d3s_emit_side(const SweepParams& p, const unsigned long long (&X)[3],
+                                              const long long (&A1s)[3], const long long (&A2s)[3],
+                                              const long long (&A1o)[3], const long long (&A2o)[3], B1F&& b1,
+                                              long long B, long long& best_v, unsigned long long& best_x) {
+  const unsigned long long nt = p.n_tail;
+  const long long e000 = p.one + (B >> 3);
+  unsigned long long seen[6];
+#pragma unroll
+  for (int q = 0; q < 6; ++q) {
+    const int p0 = d3s_perm(q, 0), p1 = d3s_perm(q, 1), p2 = d3s_perm(q, 2);
+    const unsigned long long ty = d3s_tail(X[p0], X[p1], X[p2]);
+    seen[q] = ty;
+    bool dup = false;
+#pragma unroll
+    for (int r = 0; r < q; ++r) dup |= seen[r] == ty;
+    if (dup) continue;
+    long long v000, v001, v010, v011;
+    if constexpr (!FALL) {
+      // heads 001 and 010: majority 0, minority string 2 resp. 1;
+      // heads 011: majority 1, minority string 0
+      v000 = e000;
+      v001 = max(4 * A1s[p2], 2 * A2o[p2]) >> 3;
+      v010 = max(4 * A1s[p1], 2 * A2o[p1]) >> 3;
+      v011 = max(4 * A1o[p0], 2 * A2s[p0]) >> 3;
+    } else {
+      // every non-empty advance set at the common denominator 8: one string
+      // (4 x its pair sum), two strings (2 x the quad sum), all three (the
+      // block, + 8 one when the heads agree)
+      v000 = max(max(4 * max(max(A1s[0], A1s[1]), A1s[2]), 2 * max(max(A2s[0], A2s[1]), A2s[2])),
+                 B + 8 * p.one) >> 3;
+      v001 = max(max(4 * max(max(b1(p0, p1), b1(p1, p0)), A1s[p2]),
+                     2 * max(max(A2s[p0], A2s[p1]), A2o[p2])), B) >> 3;
+      v010 = max(max(4 * max(max(b1(p0, p2), b1(p2, p0)), A1s[p1]),
+                     2 * max(max(A2s[p0], A2s[p2]), A2o[p1])), B) >> 3;
+      v011 = max(max(4 * max(max(A1o[p0], b1(p1, p0)), b1(p2, p0)),
+                     2 * max(max(A2s[p0], A2o[p1]), A2o[p2])), B) >> 3;
+    }
+    const unsigned long long x0 = ty, x1 = nt + ty, x2 = 2 * nt + ty, x3 = 3 * nt + ty;
+    p.out[x0] = v000;
+    p.out[x1] = v001;
+    p.out[x2] = v010;
+    p.out[x3] = v011;
+    if constexpr (INCR) {
+      const long long i0 = v000 - ld_vec<CG>(p.prev[0] + x0);
+      const long long i1 = v001 - ld_vec<CG>(p.prev[0] + x1);
+      const long long i2 = v010 - ld_vec<CG>(p.prev[0] + x2);
+      const long long i3 = v011 - ld_vec<CG>(p.prev[0] + x3);
+      if (red_better(i0, x0, best_v, best_x, p.r_mode)) best_v = i0, best_x = x0;
+      if (red_better(i1, x1, best_v, best_x, p.r_mode)) best_v = i1, best_x = x1;
+      if (red_better(i2, x2, best_v, best_x, p.r_mode)) best_v = i2, best_x = x2;
+      if (red_better(i3, x3, best_v, best_x, p.r_mode)) best_v = i3, best_x = x3;
+    }
+  }
+}
+
 template <bool INCR, bool FALL, bool CG>
 __device__ __forceinline__ void d3s_sweep_orbit(const SweepParams& p, const D3sOrbit& o, int L, long long& best_v,
                                                 unsigned long long& best_x) {
-  const unsigned long long nt = p.n_tail;
   long long A1t[3], A2t[3], A1c[3], A2c[3];
   d3s_sums<CG>(p.prev[0], p.prev[1], o.T, A1t, A2t);
   d3s_sums<CG>(p.prev[0], p.prev[1], o.C, A1c, A2c);
   long long B1t[3][3];
   if constexpr (FALL) d3s_b1<CG>(p.prev[0], o.T, L, B1t);
   const long long B = d3s_block<CG>(p.prev[2], d3s_tail(o.T[0], o.T[1], o.T[2]));
-  const long long e000 = p.one + (B >> 3);
-#pragma unroll
-  for (int side = 0; side < 2; ++side) {
-    const unsigned long long* X = side == 0 ? o.T : o.C;
-    const long long* A1s = side == 0 ? A1t : A1c;  // this side's sums
-    const long long* A2s = side == 0 ? A2t : A2c;
-    const long long* A1o = side == 0 ? A1c : A1t;  // the complement side's sums
-    const long long* A2o = side == 0 ? A2c : A2t;
-    unsigned long long seen[6];
-#pragma unroll
-    for (int q = 0; q < 6; ++q) {
-      const int p0 = d3s_perm(q, 0), p1 = d3s_perm(q, 1), p2 = d3s_perm(q, 2);
-      const unsigned long long ty = d3s_tail(X[p0], X[p1], X[p2]);
-      seen[q] = ty;
-      bool dup = false;
-#pragma unroll
-      for (int r = 0; r < q; ++r) dup |= seen[r] == ty;
-      if (dup) continue;
-      long long v000, v001, v010, v011;
-      if constexpr (!FALL) {
-        // heads 001 and 010: majority 0, minority string 2 resp. 1;
-        // heads 011: majority 1, minority string 0
-        v000 = e000;
-        v001 = max(4 * A1s[p2], 2 * A2o[p2]) >> 3;
-        v010 = max(4 * A1s[p1], 2 * A2o[p1]) >> 3;
-        v011 = max(4 * A1o[p0], 2 * A2s[p0]) >> 3;
-      } else {
-        // every non-empty advance set at the common denominator 8: one string
-        // (4 x its pair sum), two strings (2 x the quad sum), all three (the
-        // block, + 8 one when the heads agree)
-        auto b1 = [&](int k, int oo) { return side == 0 ? B1t[k][oo] : B1t[k][3 - k - oo]; };
-        v000 = max(max(4 * max(max(A1s[0], A1s[1]), A1s[2]), 2 * max(max(A2s[0], A2s[1]), A2s[2])),
-                   B + 8 * p.one) >> 3;
-        v001 = max(max(4 * max(max(b1(p0, p1), b1(p1, p0)), A1s[p2]),
-                       2 * max(max(A2s[p0], A2s[p1]), A2o[p2])), B) >> 3;
-        v010 = max(max(4 * max(max(b1(p0, p2), b1(p2, p0)), A1s[p1]),
-                       2 * max(max(A2s[p0], A2s[p2]), A2o[p1])), B) >> 3;
-        v011 = max(max(4 * max(max(A1o[p0], b1(p1, p0)), b1(p2, p0)),
-                       2 * max(max(A2s[p0], A2o[p1]), A2o[p2])), B) >> 3;
-      }
-      const unsigned long long x0 = ty, x1 = nt + ty, x2 = 2 * nt + ty, x3 = 3 * nt + ty;
-      p.out[x0] = v000;
-      p.out[x1] = v001;
-      p.out[x2] = v010;
-      p.out[x3] = v011;
-      if constexpr (INCR) {
-        const long long i0 = v000 - ld_vec<CG>(p.prev[0] + x0);
-        const long long i1 = v001 - ld_vec<CG>(p.prev[0] + x1);
-        const long long i2 = v010 - ld_vec<CG>(p.prev[0] + x2);
-        const long long i3 = v011 - ld_vec<CG>(p.prev[0] + x3);
-        if (red_better(i0, x0, best_v, best_x, p.r_mode)) best_v = i0, best_x = x0;
-        if (red_better(i1, x1, best_v, best_x, p.r_mode)) best_v = i1, best_x = x1;
-        if (red_better(i2, x2, best_v, best_x, p.r_mode)) best_v = i2, best_x = x2;
-        if (red_better(i3, x3, best_v, best_x, p.r_mode)) best_v = i3, best_x = x3;
-      }
-    }
-  }
+  d3s_emit_side<INCR, FALL, CG>(p, o.T, A1t, A2t, A1c, A2c, [&](int k, int oo) { return B1t[k][oo]; }, B, best_v,
+                                best_x);
+  d3s_emit_side<INCR, FALL, CG>(p, o.C, A1c, A2c, A1t, A2t, [&](int k, int oo) { return B1t[k][3 - k - oo]; }, B,
+                                best_v, best_x);
 }
 
 // W = u + 3R - F(u + 2R, u + R, u) at the 8 heads of tau: every class of
@@ -296,19 +301,94 @@ __device__ __forceinline__ void d3s_check_orbit(const CheckParams& p, const D3sO
   }
 }
 
+// The sweep runs two threads per orbit pair: lanes 2i and 2i + 1 load the sums
+// of tau and of ~tau (and half of the block, and of the f_mode 1 sums each),
+// exchange them with one shuffle each, and write the outputs of their own
+// side: half the dependent loads per thread and twice the threads of the
+// one-thread form, which at (2, 3, 8) is about one wave of long threads.
+// Tiles of 4 x 4 x 8 representatives (128 per CTA); the thread bits above
+// the side bit are T1_0, T0_0, T2_0, T1_1, T0_1, T2_1, T2_2.
+__device__ __forceinline__ void d3s2_tile(unsigned long long k, int L, unsigned long long& I0,
+                                          unsigned long long& I1, unsigned long long& I2) {
+  I2 = k & ((1ull << (L - 3)) - 1);
+  I1 = (k >> (L - 3)) & ((1ull << (L - 2)) - 1);
+  I0 = k >> (2 * L - 5);
+}
+
+__device__ __forceinline__ bool d3s2_tile_live(unsigned long long I0, unsigned long long I1, unsigned long long I2,
+                                               unsigned long long M) {
+  return 4 * I0 <= 4 * I1 + 3 && 4 * I1 <= 8 * I2 + 7 && 4 * I0 + 8 * I2 <= M;
+}
+
+__device__ __forceinline__ bool d3s2_rep(unsigned long long I0, unsigned long long I1, unsigned long long I2,
+                                         unsigned long long M, int L, unsigned r, D3sOrbit& o) {
+  const unsigned t1 = (r & 1u) | (((r >> 3) & 1u) << 1);
+  const unsigned t0 = ((r >> 1) & 1u) | (((r >> 4) & 1u) << 1);
+  const unsigned t2 = ((r >> 2) & 1u) | (((r >> 5) & 1u) << 1) | (((r >> 6) & 1u) << 2);
+  const unsigned long long T0 = 4 * I0 + t0, T1 = 4 * I1 + t1, T2 = 8 * I2 + t2;
+  if (T0 > T1 || T1 > T2) return false;
+  if (T0 + T2 > M) return false;
+  if (T0 + T2 == M && T1 >= (1ull << (L - 1))) return false;
+  o.T[0] = T0, o.T[1] = T1, o.T[2] = T2;
+  o.C[0] = M - T0, o.C[1] = M - T1, o.C[2] = M - T2;
+  return true;
+}
+
 template <bool INCR, bool FALL>
 __global__ void __launch_bounds__(kBlock) sweep_d3s_kernel(SweepParams p) {
   const int L = p.h - 1;
   const unsigned long long M = (1ull << L) - 1;
-  const unsigned long long n_tiles = 1ull << (3 * L - 8);
+  const unsigned long long n_tiles = 1ull << (3 * L - 7);
+  const int side = threadIdx.x & 1;
   long long best_v = p.r_mode ? LLONG_MIN : LLONG_MAX;
   unsigned long long best_x = ULLONG_MAX;
   for (unsigned long long k = blockIdx.x; k < n_tiles; k += gridDim.x) {
     unsigned long long I0, I1, I2;
-    d3s_tile(k, L, I0, I1, I2);
-    if (!d3s_tile_live(I0, I1, I2, M)) continue;  // the whole CTA skips it
+    d3s2_tile(k, L, I0, I1, I2);
+    if (!d3s2_tile_live(I0, I1, I2, M)) continue;  // the whole CTA skips it
     D3sOrbit o;
-    if (d3s_rep(I0, I1, I2, M, L, threadIdx.x, o)) d3s_sweep_orbit<INCR, FALL, false>(p, o, L, best_v, best_x);
+    const bool ok = d3s2_rep(I0, I1, I2, M, L, threadIdx.x >> 1, o);  // the same for both lanes of a pair
+    unsigned long long X[3] = {0, 0, 0};
+    long long A1m[3] = {0, 0, 0}, A2m[3] = {0, 0, 0}, Bm[3] = {0, 0, 0}, Bs = 0;
+    if (ok) {
+#pragma unroll
+      for (int i = 0; i < 3; ++i) X[i] = side ? o.C[i] : o.T[i];
+      d3s_sums<false>(p.prev[0], p.prev[1], X, A1m, A2m);
+      if constexpr (FALL) {
+        // lane 0: (k, o) = (0, 1), (0, 2), (1, 0); lane 1: (1, 2), (2, 0), (2, 1)
+        const unsigned long long T0 = o.T[0], T1 = o.T[1], T2 = o.T[2], top = 1ull << L;
+        const unsigned long long a0 = side ? d3s_tail(T2, top | T0, T1 << 1) : d3s_tail(T1, top | T2, T0 << 1);
+        const unsigned long long a1 = side ? d3s_tail(T0, top | T1, T2 << 1) : d3s_tail(T2, top | T1, T0 << 1);
+        const unsigned long long a2 = side ? d3s_tail(T1, top | T0, T2 << 1) : d3s_tail(T0, top | T2, T1 << 1);
+        const longlong2 q0 = d3s_ld2<false>(p.prev[0], a0), q1 = d3s_ld2<false>(p.prev[0], a1),
+                        q2 = d3s_ld2<false>(p.prev[0], a2);
+        Bm[0] = q0.x + q0.y, Bm[1] = q1.x + q1.y, Bm[2] = q2.x + q2.y;
+      }
+      const unsigned long long b = 8 * d3s_tail(o.T[0], o.T[1], o.T[2]) + 4 * side;
+      const longlong2 q0 = d3s_ld2<false>(p.prev[2], b), q1 = d3s_ld2<false>(p.prev[2], b + 2);
+      Bs = q0.x + q0.y + q1.x + q1.y;
+    }
+    long long A1x[3], A2x[3], Bx[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+      A1x[i] = __shfl_xor_sync(0xffffffffu, A1m[i], 1);
+      A2x[i] = __shfl_xor_sync(0xffffffffu, A2m[i], 1);
+      Bx[i] = FALL ? __shfl_xor_sync(0xffffffffu, Bm[i], 1) : 0;
+    }
+    const long long B = Bs + __shfl_xor_sync(0xffffffffu, Bs, 1);
+    if (ok) {
+      long long B1t[3][3] = {{0, 0, 0}, {0, 0, 0}, {0, 0, 0}};
+      if constexpr (FALL) {
+        // lane 0's three sums and lane 1's, whichever lane this is
+        const long long l00 = side ? Bx[0] : Bm[0], l01 = side ? Bx[1] : Bm[1], l02 = side ? Bx[2] : Bm[2];
+        const long long l10 = side ? Bm[0] : Bx[0], l11 = side ? Bm[1] : Bx[1], l12 = side ? Bm[2] : Bx[2];
+        B1t[0][1] = l00, B1t[0][2] = l01, B1t[1][0] = l02;
+        B1t[1][2] = l10, B1t[2][0] = l11, B1t[2][1] = l12;
+      }
+      d3s_emit_side<INCR, FALL, false>(
+          p, X, A1m, A2m, A1x, A2x, [&](int kk, int oo) { return side ? B1t[kk][3 - kk - oo] : B1t[kk][oo]; }, B,
+          best_v, best_x);
+    }
   }
   if constexpr (INCR) block_reduce_arg(best_v, best_x, p.r_mode, p.partials);
 }
