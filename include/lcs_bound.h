@@ -165,6 +165,23 @@ lcs_status lcs_bound_set_start(lcs_bound_t* hnd, const double* const* v, int on_
 /* As lcs_bound_set_start with fixed-point values (units of 2^-K), exact. */
 lcs_status lcs_bound_set_start_fx(lcs_bound_t* hnd, const int64_t* const* v, int on_device);
 
+/* The check history: one record per check since creation (or since the last
+ * set_start / restore), the newest 4096 kept.  Fixed-point values in units
+ * of 2^-K.  No counterpart in the paper beyond Algorithm 2's own quantities. */
+typedef struct {
+  int64_t iter;        /* iteration count of the checked iterate */
+  int64_t R;           /* its increment */
+  uint64_t argmin;     /* a state attaining R (smallest index among ties) */
+  int64_t E;           /* the check's E */
+  int64_t kept;        /* 1 if this check replaced the kept triplet */
+  int64_t r, eps;      /* the kept triplet after the check */
+  int64_t kept_iter;
+} lcs_bound_check_record;
+/* Copy the newest min(count, 4096, max_records) records, oldest first, into
+ * out (host); *n_checks (may be NULL) receives the number of checks recorded.
+ * Synchronises the stream.  LCS_EINVAL for batch handles. */
+lcs_status lcs_bound_history(lcs_bound_t* hnd, lcs_bound_check_record* out, int64_t max_records, int64_t* n_checks);
+
 /* The STORED FORM of an iterate: the n_stored values the handle keeps
  * (lcs_bound_size).  Under complement-symmetric storage (sigma = 2 and
  * opts.symmetry) that is the states x < N/2, the rest following from
@@ -186,7 +203,8 @@ lcs_status lcs_bound_export_stored_fx(lcs_bound_t* hnd, int k, int64_t* dst, int
  * the sticky status) and the iteration count.  lcs_bound_restore reads such a
  * file into a handle created with the same shape and options (LCS_EINVAL
  * otherwise); iterate then continues exactly -- bit for bit -- as the saved
- * handle would have.  Binary, little-endian, for this library version.
+ * handle would have (the check history restarts empty).  Binary,
+ * little-endian, for this library version.
  * LCS_EIO when the file cannot be opened, written or is truncated.
  * Synchronous. */
 lcs_status lcs_bound_save(lcs_bound_t* hnd, const char* path);

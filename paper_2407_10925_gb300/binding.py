@@ -66,6 +66,19 @@ class lcs_bound_stats_t(ctypes.Structure):
     ]
 
 
+class lcs_bound_check_record(ctypes.Structure):
+    _fields_ = [
+        ("iter", ctypes.c_int64),
+        ("R", ctypes.c_int64),
+        ("argmin", ctypes.c_uint64),
+        ("E", ctypes.c_int64),
+        ("kept", ctypes.c_int64),
+        ("r", ctypes.c_int64),
+        ("eps", ctypes.c_int64),
+        ("kept_iter", ctypes.c_int64),
+    ]
+
+
 class lcs_bound_batch_info_t(ctypes.Structure):
     _fields_ = [
         ("n_instances", ctypes.c_int),
@@ -110,6 +123,7 @@ def lib():
                 "lcs_bound_set_start_stored_fx": [vp, vp, i32],
                 "lcs_bound_export_stored_fx": [vp, i32, vp, i32],
                 "lcs_bound_save": [vp, ctypes.c_char_p],
+                "lcs_bound_history": [vp, vp, i64, vp],
                 "lcs_bound_restore": [vp, ctypes.c_char_p],
                 "lcs_bound_export": [vp, i32, vp, i32],
                 "lcs_bound_export_fx": [vp, i32, vp, i32],
@@ -289,6 +303,15 @@ def lcs_bound_export_stored_fx(hnd, k: int, out):
     if on_dev:
         lcs_bound_synchronize(hnd)
     return out
+
+
+def lcs_bound_history(hnd, max_records=4096):
+    """(records, n_checks): the newest check records, oldest first, as dicts."""
+    buf = (lcs_bound_check_record * max(1, max_records))()
+    n = ctypes.c_int64()
+    _check(lib().lcs_bound_history(hnd, buf, max_records, ctypes.byref(n)), "lcs_bound_history")
+    got = min(n.value, 4096, max_records)
+    return [{f: getattr(buf[i], f) for f, _ in lcs_bound_check_record._fields_} for i in range(got)], n.value
 
 
 def lcs_bound_save(hnd, path):
@@ -650,6 +673,9 @@ class LcsBound:
         if out is None:
             out = np.empty(self.n_stored, dtype=np.int64)
         return lcs_bound_export_stored_fx(self.hnd, k, out)
+
+    def history(self, max_records=4096):
+        return lcs_bound_history(self.hnd, max_records)
 
     def save(self, path):
         lcs_bound_save(self.hnd, path)

@@ -94,9 +94,19 @@ __global__ void __launch_bounds__(kFinalBlock) finalize_incr_kernel(const RedPar
   }
 }
 
-// E = max(0, max W) and Algorithm 2's keep test "R - E >= r - eps".
+// One record of the check history (the layout of lcs_bound_check_record).
+struct CheckRecord {
+  long long iter, R;
+  unsigned long long argmin;
+  long long E, kept, r, eps, kept_iter;
+};
+constexpr int kHistCap = 4096;  // records kept (a ring: the newest overwrite the oldest)
+
+// E = max(0, max W) and Algorithm 2's keep test "R - E >= r - eps"; with a
+// history buffer, the check's record is appended to it.
 __global__ void __launch_bounds__(kFinalBlock) finalize_check_kernel(const RedPartial* parts, int n, DevState* st,
-                                                                      long long iter) {
+                                                                      long long iter, CheckRecord* hist = nullptr,
+                                                                      unsigned long long* hist_count = nullptr) {
   long long v = 0;  // E = max(0, ...)
   for (int i = threadIdx.x; i < n; i += blockDim.x) v = max(v, parts[i].v);
   __shared__ long long sv[kFinalBlock / 32];
@@ -121,6 +131,11 @@ __global__ void __launch_bounds__(kFinalBlock) finalize_check_kernel(const RedPa
         st->kept_flag = 1;
       } else {
         st->kept_flag = 0;
+      }
+      if (hist) {
+        const unsigned long long c = *hist_count;
+        hist[c % kHistCap] = CheckRecord{iter, R, st->argmin, E, st->kept_flag, st->r, st->eps, st->kept_iter};
+        *hist_count = c + 1;
       }
     }
   }
@@ -235,6 +250,8 @@ struct lcs_bound {
   long long* ubuf;
   DevState* dstate;
   RedPartial* partials;
+  CheckRecord* hist;               // the check history (kHistCap records)
+  unsigned long long* hist_count;  // checks recorded since creation or the last start
   int grid_sweep, grid_check, grid_sweep_swap, grid_check_swap, n_partials;
   void* staging;  // device staging for host transfers
   size_t staging_bytes;
@@ -351,6 +368,8 @@ void lcs_bound_destroy(lcs_bound_t* H) {
   dev_free(H, H->ubuf);
   dev_free(H, H->dstate);
   dev_free(H, H->partials);
+  dev_free(H, H->hist);
+  dev_free(H, H->hist_count);
   dev_free(H, H->staging);
   if (H->own_stream && H->stream) cudaStreamDestroy(H->stream);
   delete H;
@@ -459,9 +478,16 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   }
   H->dstate = (DevState*)dev_alloc(H, sizeof(DevState));
   H->partials = (RedPartial*)dev_alloc(H, sizeof(RedPartial) * (size_t)H->n_partials);
-  if (!H->dstate || !H->partials) {
+  H->hist = (CheckRecord*)dev_alloc(H, sizeof(CheckRecord) * kHistCap);
+  H->hist_count = (unsigned long long*)dev_alloc(H, sizeof(unsigned long long));
+  if (!H->dstate || !H->partials || !H->hist || !H->hist_count) {
     lcs_bound_destroy(H);
     return fail(LCS_ENOMEM, "state and reduction scratch");
+  }
+  e = cudaMemsetAsync(H->hist_count, 0, sizeof(unsigned long long), H->stream);
+  if (e != cudaSuccess) {
+    lcs_bound_destroy(H);
+    return fail(LCS_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
   }
   // zero start (Algorithm 2: v <- 0)
   for (int k = 0; k < d; ++k) {
@@ -556,7 +582,8 @@ static lcs_status run_check(lcs_bound* H, const long long* u, bool R_from_state,
   H->launches++;
   H->last_check_grid = grid;
   if (finalize) {
-    finalize_check_kernel<<<1, kFinalBlock, 0, H->stream>>>(H->partials, grid, H->dstate, iter);
+    finalize_check_kernel<<<1, kFinalBlock, 0, H->stream>>>(H->partials, grid, H->dstate, iter, H->hist,
+                                                            H->hist_count);
     LCS_CUDA(cudaGetLastError());
     H->launches++;
   }
@@ -715,6 +742,7 @@ static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_d
   if (!v) return fail(LCS_EINVAL, "NULL argument");
   const double scale = std::ldexp(1.0, H->opts.frac_bits);
   LCS_CUDA(cudaMemsetAsync(H->dstate, 0, sizeof(DevState), H->stream));
+  LCS_CUDA(cudaMemsetAsync(H->hist_count, 0, sizeof(unsigned long long), H->stream));
   for (int k = 0; k < H->d; ++k) {
     if (!v[k]) return fail(LCS_EINVAL, "start vector %d is NULL", k);
     long long* dst = H->ring[H->d - 1 - k];
@@ -795,6 +823,28 @@ lcs_status lcs_bound_export_stored_fx(lcs_bound_t* H, int k, int64_t* dst, int o
   LCS_CUDA(cudaMemcpyAsync(dst, src, H->n_stored * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                            H->stream));
   if (!on_device) LCS_CUDA(cudaStreamSynchronize(H->stream));
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_history(lcs_bound_t* H, lcs_bound_check_record* out, int64_t max_records, int64_t* n_checks) {
+  if (!H) return fail(LCS_EINVAL, "handle is NULL");
+  if (H->batch) return fail(LCS_EINVAL, "batch handles keep no history");
+  if (max_records < 0 || (max_records > 0 && !out)) return fail(LCS_EINVAL, "bad output buffer");
+  static_assert(sizeof(CheckRecord) == sizeof(lcs_bound_check_record), "record layouts differ");
+  unsigned long long count = 0;
+  LCS_CUDA(cudaMemcpyAsync(&count, H->hist_count, sizeof count, cudaMemcpyDeviceToHost, H->stream));
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
+  if (n_checks) *n_checks = (int64_t)count;
+  const unsigned long long kept = std::min<unsigned long long>(count, kHistCap);
+  const unsigned long long n = std::min<unsigned long long>(kept, (unsigned long long)max_records);
+  // the newest n records, oldest first: ring slots (count - n) .. (count - 1)
+  for (unsigned long long i = 0; i < n;) {
+    const unsigned long long slot = (count - n + i) % kHistCap;
+    const unsigned long long run = std::min<unsigned long long>(n - i, kHistCap - slot);
+    LCS_CUDA(cudaMemcpyAsync(out + i, H->hist + slot, run * sizeof(CheckRecord), cudaMemcpyDeviceToHost, H->stream));
+    i += run;
+  }
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
   return LCS_OK;
 }
 
@@ -919,6 +969,7 @@ lcs_status lcs_bound_restore(lcs_bound_t* H, const char* path) {
     if (st) return st;
   }
   LCS_CUDA(cudaMemcpyAsync(H->dstate, &ds, sizeof ds, cudaMemcpyHostToDevice, H->stream));
+  LCS_CUDA(cudaMemsetAsync(H->hist_count, 0, sizeof(unsigned long long), H->stream));
   LCS_CUDA(cudaStreamSynchronize(H->stream));
   H->newest = H->d - 1;
   H->iters_done = hd.iters_done;

@@ -109,3 +109,41 @@ def test_stored_form_round_trip(lb, s, d, h, sym):
             assert np.array_equal(c.export_fx(k), b.export_fx(k))
             assert np.array_equal(e.export_fx(k), b.export_fx(k))
         assert c.read() == b.read() == e.read()
+
+
+def _oracle_checks(orc, s, d, h, iters, check_every):
+    """Algorithm 2 one iteration at a time: the record of every check the handle's cadence runs."""
+    cur, kept, recs = None, {"r": 0, "eps": 0, "kept_iter": -1}, []
+    for it in range(1, iters + 1):
+        step = orc.run(s, d, h, 1, arith="fx", check_every=1, start=cur)
+        if (check_every > 0 and it % check_every == 0) or it == iters:
+            better = step["R"] - step["E"] >= kept["r"] - kept["eps"]
+            if better:
+                kept = {"r": step["R"], "eps": step["E"], "kept_iter": it}
+            recs.append({"iter": it, "R": step["R"], "argmin": step["argmin"], "E": step["E"],
+                         "kept": int(better), **kept})
+        its = step["iterates"]
+        cur = [its[d - 1 - k] for k in range(d)]
+    return recs
+
+
+@pytest.mark.parametrize("s,d,h", [(2, 2, 6), (3, 2, 3), (2, 3, 4)])
+def test_check_history_matches_oracle(lb, orc, s, d, h):
+    iters, ce = 23, 4
+    want = _oracle_checks(orc, s, d, h, iters, ce)
+    with lb.LcsBound(s, d, h, check_every=ce) as hnd:
+        hnd.iterate(iters)
+        recs, n = hnd.history()
+    assert n == len(want)
+    assert recs == want
+
+
+def test_check_history_ring_and_resets(lb):
+    with lb.LcsBound(2, 2, 3, check_every=1) as hnd:
+        hnd.iterate(4100)
+        recs, n = hnd.history(max_records=10)
+        assert n == 4100 and [r["iter"] for r in recs] == list(range(4091, 4101))
+        full, _ = hnd.history()
+        assert len(full) == 4096 and full[0]["iter"] == 5 and full[-1] == recs[-1]
+        hnd.set_start_fx([hnd.export_fx(0), hnd.export_fx(1)])
+        assert hnd.history() == ([], 0)
