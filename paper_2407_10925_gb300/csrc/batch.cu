@@ -670,7 +670,8 @@ static lcs_status autotune(BatchState* B, cudaStream_t s, int max_grid, int sms)
   B_CUDA(cudaEventCreate(&e1));
   const bool saved_graph = B->use_graph;
   B->use_graph = false;
-  const long long probe_iters = 8;
+  // short probes: the candidates differ by far more than the noise of 4 iterations
+  const long long probe_iters = 4;
   for (int gc : grid_choices) {
     const int grid = std::min(gc, max_grid);
     for (int uc : unit_choices) {
@@ -679,7 +680,7 @@ static lcs_status autotune(BatchState* B, cudaStream_t s, int max_grid, int sms)
       B_CUDA(cudaMemcpyAsync(B->d_inst, B->inst.data(), sizeof(BatchInst) * B->n, cudaMemcpyHostToDevice, s));
       lcs_status st = reset_zero(B, s);
       if (st) return st;
-      st = batch_iterate(B, s, 2);  // warm-up
+      st = batch_iterate(B, s, 1);  // warm-up
       if (st) return st;
       B_CUDA(cudaEventRecord(e0, s));
       st = batch_iterate(B, s, probe_iters);
@@ -703,7 +704,7 @@ static lcs_status autotune(BatchState* B, cudaStream_t s, int max_grid, int sms)
     lcs_status st = reset_zero(B, s);
     if (st) return st;
     B->mode = 1;
-    st = batch_iterate(B, s, 2);
+    st = batch_iterate(B, s, 1);
     if (st) return st;
     B_CUDA(cudaEventRecord(e0, s));
     st = batch_iterate(B, s, probe_iters);
