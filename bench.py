@@ -39,6 +39,7 @@ CONFIGS = {
     "warm": dict(sigma=2, d=2, h=14, train_h=[10, 11, 12], ref_iters=4000, train_steps=3000),
     "warm16": dict(sigma=2, d=2, h=16, train_h=[10, 11, 12], ref_iters=1000, train_steps=3000),
     "fp32": dict(sigma=0, d=0, h=0, shapes=[(2, 3, 8), (3, 2, 8)], iters=1500),
+    "h17": dict(sigma=2, d=2, h=17),  # 2^34 states: 3 x 64 GiB resident (Table 2's l = 17); use --no-e2e
     "h16": dict(sigma=2, d=2, h=16),
     "h14": dict(sigma=2, d=2, h=14),
     "h12": dict(sigma=2, d=2, h=12),
