@@ -115,3 +115,12 @@ def test_full_size_zero_start_reaches_appendix_c(env, s, d, h, sym):
         bound = hnd.read()[0]
     assert math.floor(bound * 1e6) / 1e6 == pytest.approx(float(printed), abs=1e-12) or \
         round(bound, 6) == pytest.approx(float(printed), abs=1e-12)
+
+
+def test_d3_l10_reaches_table3(env):
+    """(2, 3, 10), 2^30 states: Table 3's best bound for d = 3 (0.711548, l = 10)."""
+    torch, lb = env
+    with lb.LcsBound(2, 3, 10, check_every=100) as hnd:
+        hnd.iterate(500)
+        bound = hnd.read()[0]
+    assert math.floor(bound * 1e6 + 1e-9) / 1e6 == pytest.approx(0.711548, abs=1e-9)
