@@ -206,17 +206,26 @@ __global__ void maxabs_kernel(const long long* __restrict__ v, unsigned long lon
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&st->maxabs, m);
 }
 
-// sigma = d = 2: is v invariant under exchanging the two strings?  The swap
+// sigma = d = 2: max |v| (as maxabs_kernel) and whether v is invariant under
+// exchanging the two strings, in one pass over the stored values.  The swap
 // exchanges the two bits of every position in the interleaved index; a swapped
-// index in the upper half is read through the complement symmetry.
-__global__ void swap_check_kernel(const long long* __restrict__ v, unsigned long long n_stored,
-                                  unsigned long long n_total, DevState* st) {
+// index in the upper half is read through the complement symmetry.  A warp's
+// swapped indices fall in one 32-value block, so both reads are coalesced.
+__global__ void maxabs_swap_check_kernel(const long long* __restrict__ v, unsigned long long n_stored,
+                                         unsigned long long n_total, DevState* st) {
+  long long m = 0;
+  bool bad = false;
   for (unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_stored;
        x += (unsigned long long)gridDim.x * blockDim.x) {
+    const long long a = v[x];
+    m = max(m, a == LLONG_MIN ? LLONG_MAX : (a < 0 ? -a : a));
     unsigned long long y = ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
     if (y >= n_stored) y = n_total - 1 - y;
-    if (v[y] != v[x]) atomicExch((unsigned long long*)&st->swap_bad, 1ull);
+    bad |= v[y] != a;
   }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&st->maxabs, m);
+  if (bad) atomicExch((unsigned long long*)&st->swap_bad, 1ull);
 }
 
 __global__ void init_state_kernel(DevState* st) {
@@ -743,8 +752,9 @@ static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_d
   const double scale = std::ldexp(1.0, H->opts.frac_bits);
   LCS_CUDA(cudaMemsetAsync(H->dstate, 0, sizeof(DevState), H->stream));
   LCS_CUDA(cudaMemsetAsync(H->hist_count, 0, sizeof(unsigned long long), H->stream));
-  for (int k = 0; k < H->d; ++k) {
+  for (int k = 0; k < H->d; ++k)
     if (!v[k]) return fail(LCS_EINVAL, "start vector %d is NULL", k);
+  for (int k = 0; k < H->d; ++k) {
     long long* dst = H->ring[H->d - 1 - k];
     if (stored) {
       LCS_CUDA(cudaMemcpyAsync(dst, v[k], H->n_stored * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
@@ -763,13 +773,17 @@ static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_d
       }
     }
     const int grid = (int)std::min<unsigned long long>(4096, (H->n_stored + kBlock - 1) / kBlock);
+    if (H->ks_swap && H->ks_swap->sym == 2) {
+      maxabs_swap_check_kernel<<<grid, kBlock, 0, H->stream>>>(dst, H->n_stored, H->n_total, H->dstate);
+      LCS_CUDA(cudaGetLastError());
+      H->launches++;
+      continue;
+    }
     maxabs_kernel<<<grid, kBlock, 0, H->stream>>>(dst, H->n_stored, H->dstate);
     LCS_CUDA(cudaGetLastError());
     H->launches++;
     if (H->ks_swap) {
-      if (H->ks_swap->sym == 2)
-        swap_check_kernel<<<grid, kBlock, 0, H->stream>>>(dst, H->n_stored, H->n_total, H->dstate);
-      else if (H->ks_swap->sym == 3)
+      if (H->ks_swap->sym == 3)
         launch_swap_check_d2s(H->sigma, dst, H->n_stored, H->h, H->dstate, grid, H->stream);
       else
         launch_perm_check_d3s(dst, H->n_stored, H->n_total, H->dstate, grid, H->stream);
