@@ -496,7 +496,7 @@ static const KernelSet* conc_kernels(int kind, int h) {
   switch (kind) {
     case BK_S2D2: return find_kernels(2, 2, 2);
     case BK_G22S: return find_kernels(2, 2, 1);
-    case BK_G23S: return find_kernels(2, 3, h >= d3s_min_h() ? 4 : 1, 0);
+    case BK_G23S: return find_kernels(2, 3, h >= d3s_min_h() && h <= d3s_max_h() ? 4 : 1, 0);
     case BK_G24S: return find_kernels(2, 4, 1);
     case BK_G32: return find_kernels(3, 2, h >= d2s_min_h(3) ? 3 : 0);
     case BK_G42: return find_kernels(4, 2, h >= d2s_min_h(4) ? 3 : 0);

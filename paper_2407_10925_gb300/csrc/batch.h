@@ -40,6 +40,7 @@ void launch_swap_check_d2s(int sigma, const long long* v, unsigned long long n, 
 
 // provided by kernels_d3s.cu (sigma = 2, d = 3, permutation-aware)
 int d3s_min_h();
+int d3s_max_h();
 unsigned long long d3s_tiles(int h);
 void launch_perm_check_d3s(const long long* v, unsigned long long n_stored, unsigned long long n_total, DevState* st,
                            int grid, cudaStream_t s);

@@ -13,6 +13,9 @@ const KernelSet* kernels_d3s(int f_mode) {
 // smallest h the 4 x 8 x 8 tiles fit (L = h - 1 >= 3)
 int d3s_min_h() { return 4; }
 
+// largest h the sweep's 32-bit indices cover
+int d3s_max_h() { return kD3sMaxH; }
+
 // tiles of one sweep or check (every CTA step takes one)
 unsigned long long d3s_tiles(int h) { return 1ull << (3 * (h - 1) - 8); }
 

@@ -416,7 +416,7 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
     else if (!sym && sigma >= 3 && h >= d2s_min_h(sigma))
       ks_swap = find_kernels(sigma, d, 3);
   }
-  if (d == 3 && sigma == 2 && sym && h >= d3s_min_h()) ks_swap = find_kernels(sigma, d, 4, opts.f_mode);
+  if (d == 3 && sigma == 2 && sym && h >= d3s_min_h() && h <= d3s_max_h()) ks_swap = find_kernels(sigma, d, 4, opts.f_mode);
 
   lcs_bound* H = new (std::nothrow) lcs_bound();
   if (!H) return fail(LCS_ENOMEM, "host allocation");

@@ -49,6 +49,27 @@ __device__ __forceinline__ unsigned long long spread3(unsigned long long x) {
   return x;
 }
 
+// The sweep's indices in 32 bits: for h <= 11 every state of the stored half
+// is below 2^(3h - 1) <= 2^32, and a tail string has L = h - 1 <= 10 bits.
+// (h = 12 would hold 4 x 256 GiB.)
+constexpr int kD3sMaxH = 11;
+
+// bit i of x (i < 10) moved to bit 3i
+__device__ __forceinline__ unsigned spread3_32(unsigned x) {
+  x &= 0x3ffu;
+  x = (x | (x << 16)) & 0x030000ffu;
+  x = (x | (x << 8)) & 0x0300f00fu;
+  x = (x | (x << 4)) & 0x030c30c3u;
+  x = (x | (x << 2)) & 0x09249249u;
+  return x;
+}
+
+// the index of the tail tuple (a, b, c) from the spread strings; a string
+// followed by one more letter c is (its spread << 3) | c
+__device__ __forceinline__ unsigned d3s_tail32(unsigned sa, unsigned sb, unsigned sc) {
+  return (sa << 2) | (sb << 1) | sc;
+}
+
 // two adjacent values at an even index (16-byte aligned)
 template <bool CG>
 __device__ __forceinline__ longlong2 d3s_ld2(const long long* v, unsigned long long y) {
@@ -166,34 +187,65 @@ __device__ __forceinline__ int d3s_perm(int p, int j) {
   return P[p][j];
 }
 
+// the six sums of one side of an orbit pair from the spreads S of its tail
+// X; e01 / e12: X_0 = X_1 / X_1 = X_2 (the equal sums are reused)
+__device__ __forceinline__ void d3s_sums32(const long long* v1, const long long* v2, const unsigned (&S)[3], bool e01,
+                                           bool e12, long long (&A1)[3], long long (&A2)[3]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const bool reuse = (k == 1 && e01) || (k == 2 && e12);
+    if (reuse) {
+      A1[k] = A1[k - 1];
+      A2[k] = A2[k - 1];
+      continue;
+    }
+    const unsigned s0 = S[k == 0 ? 1 : 0], s1 = S[k == 2 ? 1 : 2];
+    // A1: strings 0 and 1 hold the other components with head 0, string 2 = X_k c
+    const longlong2 p = d3s_ld2<false>(v1, d3s_tail32(s0, s1, S[k] << 3));
+    A1[k] = p.x + p.y;
+    // A2: string 0 = 0 X_k, strings 1 and 2 hold the others, each followed by a letter
+    const unsigned a2 = d3s_tail32(S[k], s0 << 3, s1 << 3);
+    const longlong2 q0 = d3s_ld2<false>(v2, a2), q1 = d3s_ld2<false>(v2, a2 + 2);
+    A2[k] = q0.x + q0.y + q1.x + q1.y;
+  }
+}
+
+// which of the six permutations repeat an earlier one, for a tail whose
+// components are ordered (X_0 <= X_1 <= X_2, or >= for the complement)
+__device__ __forceinline__ unsigned d3s_dup_mask(bool e01, bool e12) {
+  // X_0 = X_1: (1,0,2) (1,2,0) (2,1,0) repeat (0,1,2) (0,2,1) (2,0,1);
+  // X_1 = X_2: (0,2,1) (2,0,1) (2,1,0) repeat (0,1,2) (1,0,2) (1,2,0)
+  return e01 && e12 ? 0x3eu : e01 ? 0x2cu : e12 ? 0x32u : 0u;
+}
+
 // the stored outputs of one side of an orbit pair: the distinct permutations
-// Y of X (tau or ~tau) at the 4 stored heads.  A1s/A2s are this side's sums,
-// A1o/A2o the complement side's; b1(k, o) is this side's B1 (f_mode 1).
-template <bool INCR, bool FALL, bool CG, class B1F>
-__device__ __forceinline__ void d3s_emit_side(const SweepParams& p, const unsigned long long (&X)[3],
+// of its tail (spreads S) at the 4 stored heads.  A1s/A2s are this side's
+// sums, A1o/A2o the complement side's; b1(k, o) is this side's B1 (f_mode 1).
+template <bool INCR, bool FALL, class B1F>
+__device__ __forceinline__ void d3s_emit_side(const SweepParams& p, unsigned nt, const unsigned (&S)[3], unsigned dup,
                                               const long long (&A1s)[3], const long long (&A2s)[3],
                                               const long long (&A1o)[3], const long long (&A2o)[3], B1F&& b1,
                                               long long B, long long& best_v, unsigned long long& best_x) {
-  const unsigned long long nt = p.n_tail;
   const long long e000 = p.one + (B >> 3);
-  unsigned long long seen[6];
+  // f_mode 0: heads 001 and 010 (majority 0, minority string 2 resp. 1) take
+  // m0 of the minority's component, heads 011 (majority 1, minority string 0) m1
+  long long m0[3], m1[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    m0[k] = max(4 * A1s[k], 2 * A2o[k]) >> 3;
+    m1[k] = max(4 * A1o[k], 2 * A2s[k]) >> 3;
+  }
 #pragma unroll
   for (int q = 0; q < 6; ++q) {
+    if ((dup >> q) & 1u) continue;
     const int p0 = d3s_perm(q, 0), p1 = d3s_perm(q, 1), p2 = d3s_perm(q, 2);
-    const unsigned long long ty = d3s_tail(X[p0], X[p1], X[p2]);
-    seen[q] = ty;
-    bool dup = false;
-#pragma unroll
-    for (int r = 0; r < q; ++r) dup |= seen[r] == ty;
-    if (dup) continue;
+    const unsigned x0 = d3s_tail32(S[p0], S[p1], S[p2]), x1 = nt + x0, x2 = 2 * nt + x0, x3 = 3 * nt + x0;
     long long v000, v001, v010, v011;
     if constexpr (!FALL) {
-      // heads 001 and 010: majority 0, minority string 2 resp. 1;
-      // heads 011: majority 1, minority string 0
       v000 = e000;
-      v001 = max(4 * A1s[p2], 2 * A2o[p2]) >> 3;
-      v010 = max(4 * A1s[p1], 2 * A2o[p1]) >> 3;
-      v011 = max(4 * A1o[p0], 2 * A2s[p0]) >> 3;
+      v001 = m0[p2];
+      v010 = m0[p1];
+      v011 = m1[p0];
     } else {
       // every non-empty advance set at the common denominator 8: one string
       // (4 x its pair sum), two strings (2 x the quad sum), all three (the
@@ -207,37 +259,21 @@ __device__ __forceinline__ void d3s_emit_side(const SweepParams& p, const unsign
       v011 = max(max(4 * max(max(A1o[p0], b1(p1, p0)), b1(p2, p0)),
                      2 * max(max(A2s[p0], A2o[p1]), A2o[p2])), B) >> 3;
     }
-    const unsigned long long x0 = ty, x1 = nt + ty, x2 = 2 * nt + ty, x3 = 3 * nt + ty;
     p.out[x0] = v000;
     p.out[x1] = v001;
     p.out[x2] = v010;
     p.out[x3] = v011;
     if constexpr (INCR) {
-      const long long i0 = v000 - ld_vec<CG>(p.prev[0] + x0);
-      const long long i1 = v001 - ld_vec<CG>(p.prev[0] + x1);
-      const long long i2 = v010 - ld_vec<CG>(p.prev[0] + x2);
-      const long long i3 = v011 - ld_vec<CG>(p.prev[0] + x3);
+      const long long i0 = v000 - ld_vec<false>(p.prev[0] + x0);
+      const long long i1 = v001 - ld_vec<false>(p.prev[0] + x1);
+      const long long i2 = v010 - ld_vec<false>(p.prev[0] + x2);
+      const long long i3 = v011 - ld_vec<false>(p.prev[0] + x3);
       if (red_better(i0, x0, best_v, best_x, p.r_mode)) best_v = i0, best_x = x0;
       if (red_better(i1, x1, best_v, best_x, p.r_mode)) best_v = i1, best_x = x1;
       if (red_better(i2, x2, best_v, best_x, p.r_mode)) best_v = i2, best_x = x2;
       if (red_better(i3, x3, best_v, best_x, p.r_mode)) best_v = i3, best_x = x3;
     }
   }
-}
-
-template <bool INCR, bool FALL, bool CG>
-__device__ __forceinline__ void d3s_sweep_orbit(const SweepParams& p, const D3sOrbit& o, int L, long long& best_v,
-                                                unsigned long long& best_x) {
-  long long A1t[3], A2t[3], A1c[3], A2c[3];
-  d3s_sums<CG>(p.prev[0], p.prev[1], o.T, A1t, A2t);
-  d3s_sums<CG>(p.prev[0], p.prev[1], o.C, A1c, A2c);
-  long long B1t[3][3];
-  if constexpr (FALL) d3s_b1<CG>(p.prev[0], o.T, L, B1t);
-  const long long B = d3s_block<CG>(p.prev[2], d3s_tail(o.T[0], o.T[1], o.T[2]));
-  d3s_emit_side<INCR, FALL, CG>(p, o.T, A1t, A2t, A1c, A2c, [&](int k, int oo) { return B1t[k][oo]; }, B, best_v,
-                                best_x);
-  d3s_emit_side<INCR, FALL, CG>(p, o.C, A1c, A2c, A1t, A2t, [&](int k, int oo) { return B1t[k][3 - k - oo]; }, B,
-                                best_v, best_x);
 }
 
 // W = u + 3R - F(u + 2R, u + R, u) at the 8 heads of tau: every class of
@@ -307,64 +343,66 @@ __device__ __forceinline__ void d3s_check_orbit(const CheckParams& p, const D3sO
 // side: half the dependent loads per thread and twice the threads of the
 // one-thread form, which at (2, 3, 8) is about one wave of long threads.
 // Tiles of 4 x 4 x 8 representatives (128 per CTA); the thread bits above
-// the side bit are T1_0, T0_0, T2_0, T1_1, T0_1, T2_1, T2_2.
-__device__ __forceinline__ void d3s2_tile(unsigned long long k, int L, unsigned long long& I0,
-                                          unsigned long long& I1, unsigned long long& I2) {
-  I2 = k & ((1ull << (L - 3)) - 1);
-  I1 = (k >> (L - 3)) & ((1ull << (L - 2)) - 1);
+// the side bit are T1_0, T0_0, T2_0, T1_1, T0_1, T2_1, T2_2.  Indices are
+// 32-bit (h <= 11); the complement's spreads are the representative's XOR
+// the spread of 2^L - 1.
+__device__ __forceinline__ void d3s2_tile(unsigned k, int L, unsigned& I0, unsigned& I1, unsigned& I2) {
+  I2 = k & ((1u << (L - 3)) - 1);
+  I1 = (k >> (L - 3)) & ((1u << (L - 2)) - 1);
   I0 = k >> (2 * L - 5);
 }
 
-__device__ __forceinline__ bool d3s2_tile_live(unsigned long long I0, unsigned long long I1, unsigned long long I2,
-                                               unsigned long long M) {
+__device__ __forceinline__ bool d3s2_tile_live(unsigned I0, unsigned I1, unsigned I2, unsigned M) {
   return 4 * I0 <= 4 * I1 + 3 && 4 * I1 <= 8 * I2 + 7 && 4 * I0 + 8 * I2 <= M;
 }
 
-__device__ __forceinline__ bool d3s2_rep(unsigned long long I0, unsigned long long I1, unsigned long long I2,
-                                         unsigned long long M, int L, unsigned r, D3sOrbit& o) {
+__device__ __forceinline__ bool d3s2_rep(unsigned I0, unsigned I1, unsigned I2, unsigned M, int L, unsigned r,
+                                         unsigned (&T)[3]) {
   const unsigned t1 = (r & 1u) | (((r >> 3) & 1u) << 1);
   const unsigned t0 = ((r >> 1) & 1u) | (((r >> 4) & 1u) << 1);
   const unsigned t2 = ((r >> 2) & 1u) | (((r >> 5) & 1u) << 1) | (((r >> 6) & 1u) << 2);
-  const unsigned long long T0 = 4 * I0 + t0, T1 = 4 * I1 + t1, T2 = 8 * I2 + t2;
-  if (T0 > T1 || T1 > T2) return false;
-  if (T0 + T2 > M) return false;
-  if (T0 + T2 == M && T1 >= (1ull << (L - 1))) return false;
-  o.T[0] = T0, o.T[1] = T1, o.T[2] = T2;
-  o.C[0] = M - T0, o.C[1] = M - T1, o.C[2] = M - T2;
+  T[0] = 4 * I0 + t0, T[1] = 4 * I1 + t1, T[2] = 8 * I2 + t2;
+  if (T[0] > T[1] || T[1] > T[2]) return false;
+  if (T[0] + T[2] > M) return false;
+  if (T[0] + T[2] == M && T[1] >= (1u << (L - 1))) return false;
   return true;
 }
 
 template <bool INCR, bool FALL>
 __global__ void __launch_bounds__(kBlock) sweep_d3s_kernel(SweepParams p) {
   const int L = p.h - 1;
-  const unsigned long long M = (1ull << L) - 1;
-  const unsigned long long n_tiles = 1ull << (3 * L - 7);
+  const unsigned M = (1u << L) - 1;
+  const unsigned SM = spread3_32(M);
+  const unsigned nt = 1u << (3 * L);
+  const unsigned n_tiles = 1u << (3 * L - 7);
   const int side = threadIdx.x & 1;
   long long best_v = p.r_mode ? LLONG_MIN : LLONG_MAX;
   unsigned long long best_x = ULLONG_MAX;
-  for (unsigned long long k = blockIdx.x; k < n_tiles; k += gridDim.x) {
-    unsigned long long I0, I1, I2;
+  for (unsigned k = blockIdx.x; k < n_tiles; k += gridDim.x) {
+    unsigned I0, I1, I2;
     d3s2_tile(k, L, I0, I1, I2);
     if (!d3s2_tile_live(I0, I1, I2, M)) continue;  // the whole CTA skips it
-    D3sOrbit o;
-    const bool ok = d3s2_rep(I0, I1, I2, M, L, threadIdx.x >> 1, o);  // the same for both lanes of a pair
-    unsigned long long X[3] = {0, 0, 0};
+    unsigned T[3];
+    const bool ok = d3s2_rep(I0, I1, I2, M, L, threadIdx.x >> 1, T);  // the same for both lanes of a pair
+    const unsigned ST[3] = {spread3_32(T[0]), spread3_32(T[1]), spread3_32(T[2])};
+    const unsigned flip = side ? SM : 0u;
+    const unsigned S[3] = {ST[0] ^ flip, ST[1] ^ flip, ST[2] ^ flip};  // this lane's side: tau or ~tau
+    const bool e01 = T[0] == T[1], e12 = T[1] == T[2];
     long long A1m[3] = {0, 0, 0}, A2m[3] = {0, 0, 0}, Bm[3] = {0, 0, 0}, Bs = 0;
     if (ok) {
-#pragma unroll
-      for (int i = 0; i < 3; ++i) X[i] = side ? o.C[i] : o.T[i];
-      d3s_sums<false>(p.prev[0], p.prev[1], X, A1m, A2m);
+      d3s_sums32(p.prev[0], p.prev[1], S, e01, e12, A1m, A2m);
       if constexpr (FALL) {
-        // lane 0: (k, o) = (0, 1), (0, 2), (1, 0); lane 1: (1, 2), (2, 0), (2, 1)
-        const unsigned long long T0 = o.T[0], T1 = o.T[1], T2 = o.T[2], top = 1ull << L;
-        const unsigned long long a0 = side ? d3s_tail(T2, top | T0, T1 << 1) : d3s_tail(T1, top | T2, T0 << 1);
-        const unsigned long long a1 = side ? d3s_tail(T0, top | T1, T2 << 1) : d3s_tail(T2, top | T1, T0 << 1);
-        const unsigned long long a2 = side ? d3s_tail(T1, top | T0, T2 << 1) : d3s_tail(T0, top | T2, T1 << 1);
-        const longlong2 q0 = d3s_ld2<false>(p.prev[0], a0), q1 = d3s_ld2<false>(p.prev[0], a1),
-                        q2 = d3s_ld2<false>(p.prev[0], a2);
+        // B1(T, k, o) at tail(T_o, 1 T_r, T_k c): lane 0 takes (k, o) = (0, 1),
+        // (0, 2), (1, 0); lane 1 (1, 2), (2, 0), (2, 1)
+        const unsigned top = 1u << (3 * L + 1);
+        const unsigned a0 = side ? d3s_tail32(ST[2], ST[0], ST[1] << 3) : d3s_tail32(ST[1], ST[2], ST[0] << 3);
+        const unsigned a1 = side ? d3s_tail32(ST[0], ST[1], ST[2] << 3) : d3s_tail32(ST[2], ST[1], ST[0] << 3);
+        const unsigned a2 = side ? d3s_tail32(ST[1], ST[0], ST[2] << 3) : d3s_tail32(ST[0], ST[2], ST[1] << 3);
+        const longlong2 q0 = d3s_ld2<false>(p.prev[0], a0 | top), q1 = d3s_ld2<false>(p.prev[0], a1 | top),
+                        q2 = d3s_ld2<false>(p.prev[0], a2 | top);
         Bm[0] = q0.x + q0.y, Bm[1] = q1.x + q1.y, Bm[2] = q2.x + q2.y;
       }
-      const unsigned long long b = 8 * d3s_tail(o.T[0], o.T[1], o.T[2]) + 4 * side;
+      const unsigned b = (d3s_tail32(ST[0], ST[1], ST[2]) << 3) + 4 * side;
       const longlong2 q0 = d3s_ld2<false>(p.prev[2], b), q1 = d3s_ld2<false>(p.prev[2], b + 2);
       Bs = q0.x + q0.y + q1.x + q1.y;
     }
@@ -385,9 +423,9 @@ __global__ void __launch_bounds__(kBlock) sweep_d3s_kernel(SweepParams p) {
         B1t[0][1] = l00, B1t[0][2] = l01, B1t[1][0] = l02;
         B1t[1][2] = l10, B1t[2][0] = l11, B1t[2][1] = l12;
       }
-      d3s_emit_side<INCR, FALL, false>(
-          p, X, A1m, A2m, A1x, A2x, [&](int kk, int oo) { return side ? B1t[kk][3 - kk - oo] : B1t[kk][oo]; }, B,
-          best_v, best_x);
+      d3s_emit_side<INCR, FALL>(
+          p, nt, S, d3s_dup_mask(e01, e12), A1m, A2m, A1x, A2x,
+          [&](int kk, int oo) { return side ? B1t[kk][3 - kk - oo] : B1t[kk][oo]; }, B, best_v, best_x);
     }
   }
   if constexpr (INCR) block_reduce_arg(best_v, best_x, p.r_mode, p.partials);
