@@ -555,10 +555,12 @@ def main():
 
     # end to end through the public API from pinned host memory: set the start
     # vectors from the host, run one check period, read the bound.  The start
-    # goes in the stored form the handle keeps (lcs_bound_set_start_stored_fx:
-    # the complement half under symmetry); the same step with full vectors
-    # (lcs_bound_set_start_fx, which also verifies the symmetry) is reported
-    # beside it.
+    # goes in the most compact form the handle takes: the orbit form (sigma =
+    # d = 2 with the complement and the swap: a quarter of the states) where
+    # it applies, else the stored form (lcs_bound_set_start_stored_fx: the
+    # complement half under symmetry).  The same step with the stored form and
+    # with full vectors (lcs_bound_set_start_fx, which also verifies the
+    # symmetry) is reported beside it.
     e2e = None
     if not args.no_e2e and args.e2e_steps > 0:
         def e2e_run(set_start):
@@ -575,22 +577,34 @@ def main():
                     times.append((time.perf_counter() - t0) * 1e3)
             return reduce_max(max(times), dist, "cuda")
 
+        def entry(ms, h2d, what):
+            return {"value": world * n * C / (ms / 1e3), "ms_per_step": ms, "h2d_bytes_per_step": h2d, "what": what}
+
+        read_what = " + lcs_bound_iterate(C) + lcs_bound_read"
+        try:
+            n_orb = hnd.n_orbit
+        except lb.LcsError:
+            n_orb = None
+        forms = {}
+        if n_orb:
+            start_orb = hnd.export_orbit_fx(0, out=torch.empty(n_orb, dtype=torch.int64, pin_memory=True))
+            forms["orbit_form"] = entry(e2e_run(lambda: hnd.set_start_orbit_fx([start_orb] * d)), d * n_orb * 8,
+                                        "lcs_bound_set_start_orbit_fx from pinned host (d vectors in orbit form)"
+                                        + read_what)
+            del start_orb
         n_st = hnd.n_stored
         start_st = hnd.export_stored_fx(0, out=torch.empty(n_st, dtype=torch.int64, pin_memory=True))
-        e2e_ms_step = e2e_run(lambda: hnd.set_start_stored_fx([start_st] * d))
+        forms["stored_form"] = entry(e2e_run(lambda: hnd.set_start_stored_fx([start_st] * d)), d * n_st * 8,
+                                     "lcs_bound_set_start_stored_fx from pinned host (d vectors in stored form)"
+                                     + read_what)
         del start_st
         start = hnd.export_fx(0, out=torch.empty(n, dtype=torch.int64, pin_memory=True))
-        full_ms_step = e2e_run(lambda: hnd.set_start_fx([start] * d))
+        forms["full_vectors"] = entry(e2e_run(lambda: hnd.set_start_fx([start] * d)), d * n * 8,
+                                      "lcs_bound_set_start_fx from pinned host (every state, symmetry verified on "
+                                      "the device)" + read_what)
         del start
-        e2e = {"value": world * n * C / (e2e_ms_step / 1e3), "unit": "state-updates/s",
-               "h2d_bytes_per_step": d * n_st * 8, "d2h_bytes_per_step": 80,
-               "ms_per_step": e2e_ms_step,
-               "what": "lcs_bound_set_start_stored_fx from pinned host (d vectors in stored form) + "
-                       "lcs_bound_iterate(C) + lcs_bound_read",
-               "full_vectors": {"value": world * n * C / (full_ms_step / 1e3), "ms_per_step": full_ms_step,
-                                "h2d_bytes_per_step": d * n * 8,
-                                "what": "the same step with lcs_bound_set_start_fx (every state, symmetry "
-                                        "verified on the device)"}}
+        head = "orbit_form" if n_orb else "stored_form"
+        e2e = {"unit": "state-updates/s", "d2h_bytes_per_step": 80, **forms.pop(head), "form": head, **forms}
 
     clocks = clk.summary()
     if rank == 0:

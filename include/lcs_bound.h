@@ -196,6 +196,35 @@ lcs_status lcs_bound_history(lcs_bound_t* hnd, lcs_bound_check_record* out, int6
 lcs_status lcs_bound_set_start_stored_fx(lcs_bound_t* hnd, const int64_t* const* v, int on_device);
 lcs_status lcs_bound_export_stored_fx(lcs_bound_t* hnd, int k, int64_t* dst, int on_device);
 
+/* The ORBIT FORM (sigma = d = 2, complement-symmetric storage, h >= 6; other
+ * handles get LCS_EUNSUPPORTED).  When an iterate is also symmetric under
+ * exchanging the two strings, as every iterate from the zero start is, the
+ * stored states of a tail t = (a, b) form one orbit of eight with those of
+ * ~t = (~a, ~b), t' = (~b, ~a) and ~t' = (b, a) (each with heads 00 and 01),
+ * holding at most four distinct values:
+ *   v(00, t) = v(00, ~t'),  v(00, ~t) = v(00, t'),
+ *   v(01, t) = v(01, t'),   v(01, ~t) = v(01, ~t').
+ * The orbit form keeps those four values, in this order, for one
+ * representative per orbit: (s, a, beta) with 0 <= a <= beta < K = 2^(h-2),
+ * b = beta (s = 0) or 2^(h-1) - 1 - beta (s = 1).  Strings are (h-1)-bit
+ * integers, most significant letter first; the representative's four values
+ * sit at 4 q .. 4 q + 3 with q = s K (K + 1) / 2 + beta (beta + 1) / 2 + a.
+ * v(g0 g1, (a, b)) is the value of the state whose strings are g0 a and g1 b
+ * (heads g0, g1; STATE INDEX above).  *n_orbit = 4 K (K + 1) = 4^(h-1) + 2^h
+ * values: about half of the stored form, a quarter of N.
+ * set_start_orbit_fx: as lcs_bound_set_start_stored_fx, each v[k] holding
+ * n_orbit values; the handle writes all eight states of every orbit, so the
+ * start has both symmetries by construction (where an orbit has fewer than
+ * eight distinct states its values must agree, as they do in any exported
+ * orbit form).  Device vectors must be 16-byte aligned (LCS_EINVAL).
+ * export_orbit_fx: as lcs_bound_export_stored_fx, n_orbit values; LCS_EINVAL
+ * if the handle's start was not swap-symmetric.  A device dst must be
+ * 16-byte aligned.  The paper has no counterpart of these calls beyond the
+ * two symmetries. */
+lcs_status lcs_bound_orbit_size(const lcs_bound_t* hnd, uint64_t* n_orbit);
+lcs_status lcs_bound_set_start_orbit_fx(lcs_bound_t* hnd, const int64_t* const* v, int on_device);
+lcs_status lcs_bound_export_orbit_fx(lcs_bound_t* hnd, int k, int64_t* dst, int on_device);
+
 /* Checkpoint and resume (no counterpart in the paper).  lcs_bound_save writes
  * the whole state of a single-instance handle to a file: shape and options,
  * the d most recent iterates in stored form (newest first), the retained u

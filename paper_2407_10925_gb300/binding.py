@@ -122,6 +122,9 @@ def lib():
                 "lcs_bound_set_start_fx": [vp, vp, i32],
                 "lcs_bound_set_start_stored_fx": [vp, vp, i32],
                 "lcs_bound_export_stored_fx": [vp, i32, vp, i32],
+                "lcs_bound_orbit_size": [vp, P(u64)],
+                "lcs_bound_set_start_orbit_fx": [vp, vp, i32],
+                "lcs_bound_export_orbit_fx": [vp, i32, vp, i32],
                 "lcs_bound_save": [vp, ctypes.c_char_p],
                 "lcs_bound_history": [vp, vp, i64, vp],
                 "lcs_bound_restore": [vp, ctypes.c_char_p],
@@ -300,6 +303,27 @@ def lcs_bound_set_start_stored_fx(hnd, vs):
 def lcs_bound_export_stored_fx(hnd, k: int, out):
     p, on_dev = _ptr_and_kind(out, np.int64)
     _check(lib().lcs_bound_export_stored_fx(hnd, k, p, on_dev), "lcs_bound_export_stored_fx")
+    if on_dev:
+        lcs_bound_synchronize(hnd)
+    return out
+
+
+def lcs_bound_orbit_size(hnd) -> int:
+    """values of the orbit form (sigma = d = 2 with the complement and the swap)."""
+    n = ctypes.c_uint64()
+    _check(lib().lcs_bound_orbit_size(hnd, ctypes.byref(n)), "lcs_bound_orbit_size")
+    return int(n.value)
+
+
+def lcs_bound_set_start_orbit_fx(hnd, vs):
+    """vs[k]: the orbit form (lcs_bound_orbit_size values) of the iterate k steps older than the newest."""
+    arr, on_dev = _vec_array(vs, np.int64)
+    _check(lib().lcs_bound_set_start_orbit_fx(hnd, arr, on_dev), "lcs_bound_set_start_orbit_fx")
+
+
+def lcs_bound_export_orbit_fx(hnd, k: int, out):
+    p, on_dev = _ptr_and_kind(out, np.int64)
+    _check(lib().lcs_bound_export_orbit_fx(hnd, k, p, on_dev), "lcs_bound_export_orbit_fx")
     if on_dev:
         lcs_bound_synchronize(hnd)
     return out
@@ -673,6 +697,18 @@ class LcsBound:
         if out is None:
             out = np.empty(self.n_stored, dtype=np.int64)
         return lcs_bound_export_stored_fx(self.hnd, k, out)
+
+    @property
+    def n_orbit(self):
+        return lcs_bound_orbit_size(self.hnd)
+
+    def set_start_orbit_fx(self, vs):
+        lcs_bound_set_start_orbit_fx(self.hnd, vs)
+
+    def export_orbit_fx(self, k=0, out=None):
+        if out is None:
+            out = np.empty(self.n_orbit, dtype=np.int64)
+        return lcs_bound_export_orbit_fx(self.hnd, k, out)
 
     def history(self, max_records=4096):
         return lcs_bound_history(self.hnd, max_records)

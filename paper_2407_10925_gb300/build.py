@@ -25,6 +25,7 @@ SOURCES = [
     "kernels_s4.cu",
     "noalloc.cu",
     "kernels_s2d2.cu",
+    "kernels_orbit.cu",
     "kernels_d2s.cu",
     "kernels_d3s.cu",
     "batch.cu",

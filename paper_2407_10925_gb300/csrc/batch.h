@@ -38,6 +38,12 @@ unsigned long long d2s_slots(int sigma, int h);
 void launch_swap_check_d2s(int sigma, const long long* v, unsigned long long n, int h, DevState* st, int grid,
                            cudaStream_t s);
 
+// provided by kernels_orbit.cu (sigma = d = 2 orbit form)
+unsigned long long orbit_len(int h);
+void launch_orbit_unpack(const long long* orb, long long* out, int h, unsigned long long n_tail, DevState* st,
+                         cudaStream_t s);
+void launch_orbit_pack(const long long* v, long long* orb, int h, unsigned long long n_tail, cudaStream_t s);
+
 // provided by kernels_d3s.cu (sigma = 2, d = 3, permutation-aware)
 int d3s_min_h();
 int d3s_max_h();

@@ -743,6 +743,27 @@ static lcs_status ingest_range(lcs_bound* H, const void* src, unsigned long long
   return LCS_OK;
 }
 
+// the end of every start: read the checks of the start vectors, reset the
+// results (the kept triplet returns to the initial (v_0, 0, 0)) and the ring
+static lcs_status finish_start(lcs_bound* H) {
+  DevState s;
+  LCS_CUDA(cudaMemcpyAsync(&s, H->dstate, sizeof s, cudaMemcpyDeviceToHost, H->stream));
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
+  init_state_kernel<<<1, 32, 0, H->stream>>>(H->dstate);
+  LCS_CUDA(cudaGetLastError());
+  if (H->ubuf) LCS_CUDA(cudaMemcpyAsync(H->ubuf, H->ring[0], H->n_stored * 8, cudaMemcpyDeviceToDevice, H->stream));
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
+  H->newest = H->d - 1;
+  H->iters_done = 0;
+  if (s.status == LCS_EINVAL)
+    return fail(LCS_EINVAL, "start vectors are not complement-symmetric (v[N-1-x] != v[x])");
+  if (s.status == LCS_EOVERFLOW) return fail(LCS_EOVERFLOW, "start values outside the fixed-point range");
+  H->vbound = (double)s.maxabs;
+  H->swap_ok = H->ks_swap != nullptr && s.swap_bad == 0;
+  if (!headroom_ok(H, H->vbound)) return fail(LCS_EOVERFLOW, "start values too large for the fixed-point headroom");
+  return LCS_OK;
+}
+
 // stored = true: v[k] holds the n_stored stored values (the storage form), copied as they are
 static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_device, bool from_double,
                                     bool stored = false) {
@@ -791,23 +812,7 @@ static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_d
       H->launches++;
     }
   }
-  DevState s;
-  LCS_CUDA(cudaMemcpyAsync(&s, H->dstate, sizeof s, cudaMemcpyDeviceToHost, H->stream));
-  LCS_CUDA(cudaStreamSynchronize(H->stream));
-  // reset the results: the kept triplet returns to the initial (v_0, 0, 0)
-  init_state_kernel<<<1, 32, 0, H->stream>>>(H->dstate);
-  LCS_CUDA(cudaGetLastError());
-  if (H->ubuf) LCS_CUDA(cudaMemcpyAsync(H->ubuf, H->ring[0], H->n_stored * 8, cudaMemcpyDeviceToDevice, H->stream));
-  LCS_CUDA(cudaStreamSynchronize(H->stream));
-  H->newest = H->d - 1;
-  H->iters_done = 0;
-  if (s.status == LCS_EINVAL)
-    return fail(LCS_EINVAL, "start vectors are not complement-symmetric (v[N-1-x] != v[x])");
-  if (s.status == LCS_EOVERFLOW) return fail(LCS_EOVERFLOW, "start values outside the fixed-point range");
-  H->vbound = (double)s.maxabs;
-  H->swap_ok = H->ks_swap != nullptr && s.swap_bad == 0;
-  if (!headroom_ok(H, H->vbound)) return fail(LCS_EOVERFLOW, "start values too large for the fixed-point headroom");
-  return LCS_OK;
+  return finish_start(H);
 }
 
 lcs_status lcs_bound_set_start(lcs_bound_t* H, const double* const* v, int on_device) {
@@ -837,6 +842,81 @@ lcs_status lcs_bound_export_stored_fx(lcs_bound_t* H, int k, int64_t* dst, int o
   LCS_CUDA(cudaMemcpyAsync(dst, src, H->n_stored * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
                            H->stream));
   if (!on_device) LCS_CUDA(cudaStreamSynchronize(H->stream));
+  return LCS_OK;
+}
+
+// the orbit form (kernels_orbit.cu): sigma = d = 2 with the sweep that uses
+// the complement and the swap
+static lcs_status orbit_supported(const lcs_bound* H) {
+  if (!H) return fail(LCS_EINVAL, "handle is NULL");
+  if (H->batch) return fail(LCS_EINVAL, "a batch handle: use the lcs_bound_batch_* calls");
+  if (!H->ks_swap || H->ks_swap->sym != 2)
+    return fail(LCS_EUNSUPPORTED, "the orbit form needs sigma = d = 2, complement-symmetric storage and h >= 6");
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_orbit_size(const lcs_bound_t* H, uint64_t* n_orbit) {
+  if (lcs_status st = orbit_supported(H)) return st;
+  if (!n_orbit) return fail(LCS_EINVAL, "NULL argument");
+  *n_orbit = orbit_len(H->h);
+  return LCS_OK;
+}
+
+lcs_status lcs_bound_set_start_orbit_fx(lcs_bound_t* H, const int64_t* const* v, int on_device) {
+  if (lcs_status st = orbit_supported(H)) return st;
+  if (!v) return fail(LCS_EINVAL, "NULL argument");
+  for (int k = 0; k < H->d; ++k) {
+    if (!v[k]) return fail(LCS_EINVAL, "start vector %d is NULL", k);
+    if (on_device && ((uintptr_t)v[k] & 15)) return fail(LCS_EINVAL, "device vector %d is not 16-byte aligned", k);
+  }
+  const unsigned long long n_orb = orbit_len(H->h);
+  LCS_CUDA(cudaMemsetAsync(H->dstate, 0, sizeof(DevState), H->stream));
+  LCS_CUDA(cudaMemsetAsync(H->hist_count, 0, sizeof(unsigned long long), H->stream));
+  // host vectors pass through the ring row the start does not fill
+  // (n_orb = 4^(h-1) + 2^h <= n_stored = 2 4^(h-1))
+  long long* scratch = H->ring[H->d];
+  for (int k = 0; k < H->d; ++k) {
+    const long long* src = reinterpret_cast<const long long*>(v[k]);
+    if (!on_device) {
+      LCS_CUDA(cudaMemcpyAsync(scratch, v[k], n_orb * 8, cudaMemcpyHostToDevice, H->stream));
+      src = scratch;
+    }
+    launch_orbit_unpack(src, H->ring[H->d - 1 - k], H->h, H->n_tail, H->dstate, H->stream);
+    LCS_CUDA(cudaGetLastError());
+    H->launches++;
+  }
+  return finish_start(H);  // symmetric by construction: swap_bad stays 0
+}
+
+lcs_status lcs_bound_export_orbit_fx(lcs_bound_t* H, int k, int64_t* dst, int on_device) {
+  if (lcs_status st = orbit_supported(H)) return st;
+  if (!dst) return fail(LCS_EINVAL, "NULL argument");
+  if (k < -1 || k >= H->d) return fail(LCS_EINVAL, "k=%d outside -1..d-1", k);
+  if (!H->swap_ok) return fail(LCS_EINVAL, "the iterates are not swap-symmetric (the start lacked the symmetry)");
+  if (on_device && ((uintptr_t)dst & 15)) return fail(LCS_EINVAL, "device destination is not 16-byte aligned");
+  const int rows = H->d + 1;
+  const long long* src;
+  if (k == -1) {
+    if (!H->ubuf) return fail(LCS_EINVAL, "u is not retained (opts.keep_u = 0)");
+    src = H->ubuf;
+  } else {
+    src = H->ring[(H->newest - k + rows) % rows];
+  }
+  const unsigned long long n_orb = orbit_len(H->h);
+  if (on_device) {
+    launch_orbit_pack(src, reinterpret_cast<long long*>(dst), H->h, H->n_tail, H->stream);
+    LCS_CUDA(cudaGetLastError());
+    H->launches++;
+    return LCS_OK;
+  }
+  // host: pack into the row the next sweep overwrites (it holds v_{t-d}, which
+  // no export and no later sweep reads), then copy out
+  long long* scratch = H->ring[(H->newest + 1) % rows];
+  launch_orbit_pack(src, scratch, H->h, H->n_tail, H->stream);
+  LCS_CUDA(cudaGetLastError());
+  H->launches++;
+  LCS_CUDA(cudaMemcpyAsync(dst, scratch, n_orb * 8, cudaMemcpyDeviceToHost, H->stream));
+  LCS_CUDA(cudaStreamSynchronize(H->stream));
   return LCS_OK;
 }
 

@@ -90,5 +90,8 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.lcs_bound_save(None, b"/nonexistent/x") == binding.LCS_EINVAL
     assert L.lcs_bound_restore(None, b"/nonexistent/x") == binding.LCS_EINVAL
     assert L.lcs_bound_export_stored_fx(None, 0, None, 0) == binding.LCS_EINVAL
+    assert L.lcs_bound_orbit_size(None, None) == binding.LCS_EINVAL
+    assert L.lcs_bound_set_start_orbit_fx(None, None, 0) == binding.LCS_EINVAL
+    assert L.lcs_bound_export_orbit_fx(None, 0, None, 0) == binding.LCS_EINVAL
     assert L.lcs_bound_read(None, None, None, None, None, None) == binding.LCS_EINVAL
     L.lcs_bound_destroy(None)

@@ -147,3 +147,82 @@ def test_check_history_ring_and_resets(lb):
         assert len(full) == 4096 and full[0]["iter"] == 5 and full[-1] == recs[-1]
         hnd.set_start_fx([hnd.export_fx(0), hnd.export_fx(1)])
         assert hnd.history() == ([], 0)
+
+
+def _orbit_reference(full, h):
+    """The orbit form as the header defines it, rebuilt from a full vector
+    with plain index arithmetic (the STATE INDEX of sigma = d = 2)."""
+    K, M = 1 << (h - 2), (1 << (h - 1)) - 1
+
+    def idx(g0, g1, a, b):
+        x = (g0 << (2 * h - 1)) | (g1 << (2 * h - 2))
+        for i in range(h - 1):
+            x |= ((a >> i) & 1) << (2 * i + 1) | ((b >> i) & 1) << (2 * i)
+        return x
+
+    out = np.zeros(4 * K * (K + 1), dtype=np.int64)
+    for s in (0, 1):
+        for beta in range(K):
+            b = beta if s == 0 else M - beta
+            for a in range(beta + 1):
+                q = s * (K * (K + 1) // 2) + beta * (beta + 1) // 2 + a
+                out[4 * q:4 * q + 4] = [full[idx(0, 0, a, b)], full[idx(0, 0, M - a, M - b)],
+                                        full[idx(0, 1, a, b)], full[idx(0, 1, M - a, M - b)]]
+    return out
+
+
+@pytest.mark.parametrize("h", [6, 7])
+def test_orbit_form_layout_and_round_trip(lb, h):
+    import torch
+
+    d = 2
+    with lb.LcsBound(2, d, h, check_every=10) as a:
+        a.iterate(30)
+        full = [a.export_fx(k) for k in range(d)]
+        orb = [a.export_orbit_fx(k) for k in range(d)]
+        orb_dev = [torch.empty(a.n_orbit, dtype=torch.int64, device="cuda") for _ in range(d)]
+        for k in range(d):
+            a.export_orbit_fx(k, orb_dev[k])
+        assert a.n_orbit == 4 ** (h - 1) + 2 ** h
+        for k in range(d):
+            assert np.array_equal(orb[k], _orbit_reference(full[k], h)), k
+            assert np.array_equal(orb_dev[k].cpu().numpy(), orb[k])
+    with lb.LcsBound(2, d, h, check_every=10) as b, lb.LcsBound(2, d, h, check_every=10) as c, \
+            lb.LcsBound(2, d, h, check_every=10) as e:
+        b.set_start_fx(full)
+        c.set_start_orbit_fx(orb)
+        e.set_start_orbit_fx(orb_dev)
+        for k in range(d):  # the start itself, all N states
+            assert np.array_equal(c.export_fx(k), full[k])
+            assert np.array_equal(e.export_fx(k), full[k])
+        for hnd in (b, c, e):
+            hnd.iterate(25)
+        for k in range(d):
+            assert np.array_equal(c.export_fx(k), b.export_fx(k))
+            assert np.array_equal(e.export_fx(k), b.export_fx(k))
+        assert c.read() == b.read() == e.read()
+
+
+def test_orbit_form_errors(lb):
+    import torch
+
+    for shape, kw in [((2, 2, 5), {}), ((3, 2, 4), {}), ((2, 2, 7), {"symmetry": 0}), ((2, 3, 4), {})]:
+        with lb.LcsBound(*shape, **kw) as hnd:
+            with pytest.raises(lb.LcsError) as e:
+                hnd.n_orbit
+            assert e.value.status == lb.LCS_EUNSUPPORTED
+    with lb.LcsBound(2, 2, 6) as hnd:
+        n = hnd.n_orbit
+        # a complement-symmetric start without the swap symmetry runs, but has no orbit form
+        rng = np.random.default_rng(5)
+        N = hnd.n_states
+        v = rng.integers(0, 1 << 40, size=N, dtype=np.int64)
+        v = np.minimum(v, v[::-1])
+        hnd.set_start_fx([v, v])
+        with pytest.raises(lb.LcsError) as e:
+            hnd.export_orbit_fx(0)
+        assert e.value.status == lb.LCS_EINVAL
+        buf = torch.zeros(n + 2, dtype=torch.int64, device="cuda")
+        with pytest.raises(lb.LcsError) as e:
+            hnd.set_start_orbit_fx([buf[1:], buf[1:]])  # 8-byte aligned only
+        assert e.value.status == lb.LCS_EINVAL
