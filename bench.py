@@ -40,7 +40,7 @@ CONFIGS = {
     "warm16": dict(sigma=2, d=2, h=16, train_h=[10, 11, 12], ref_iters=1000, train_steps=3000),
     "fp32": dict(sigma=0, d=0, h=0, shapes=[(2, 3, 8), (3, 2, 8)], iters=1500),
     "h17": dict(sigma=2, d=2, h=17),  # 2^34 states: 3 x 64 GiB resident (Table 2's l = 17); use --no-e2e
-    "h16": dict(sigma=2, d=2, h=16),
+    "h16": dict(sigma=2, d=2, h=16, bound_iters=2000),
     "d3h11": dict(sigma=2, d=3, h=11),  # 2^33 states, 4 x 32 GiB: beyond Table 3's l = 10 for d = 3
     "d3h9": dict(sigma=2, d=3, h=9),  # 2^27 states (2 GiB resident): profiling size of the d = 3 kernels
     "h14": dict(sigma=2, d=2, h=14),
@@ -62,6 +62,8 @@ def parse():
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--bound-iters", type=int, default=None,
+                    help="iterations of the wall-time-to-bound run (default: the config's, 2000 for h16; 0 skips)")
     ap.add_argument("--symmetry", type=int, default=1)
     ap.add_argument("--batch-mode", choices=["auto", "0", "1"], default="auto",
                     help="batch config: the autotuner's mode, or force 0 (persistent launch) / 1 (concurrent)")
@@ -470,7 +472,7 @@ def run_fp32(args, cfg, world, rank, local_rank):
                 st = hnd.stats()
                 results[f"({s_},{d_},{h_})"][name] = {
                     "ms_per_sweep": st["sweep_ms"] / max(1, st["sweep_launches"]), "bound": hnd.read()[0],
-                    "stored_states": hnd.n_stored, **kw}
+                    "stored_states": n_stored, **kw}
     if rank == 0:
         print(json.dumps({"metric": "float32 storage experiment: error vs exact iterates and sweep time",
                           "config": {"workload": "zero start, 1500 iterations; float32 vs fixed point with full "
@@ -606,6 +608,23 @@ def main():
         head = "orbit_form" if n_orb else "stored_form"
         e2e = {"unit": "state-updates/s", "d2h_bytes_per_step": 80, **forms.pop(head), "form": head, **forms}
 
+    # wall time to the rigorous bound: a fresh handle from the zero start,
+    # create .. iterate(bound_iters) .. read, checks every 100 iterations
+    n_stored = hnd.n_stored
+    hnd.close()
+    bound_iters = args.bound_iters if args.bound_iters is not None else cfg.get("bound_iters", 0)
+    to_bound = None
+    if bound_iters > 0:
+        torch.cuda.synchronize()
+        barrier()
+        t0 = time.perf_counter()
+        with lb.LcsBound(sigma, d, h, check_every=100, symmetry=args.symmetry, stream=stream.cuda_stream) as hb:
+            hb.iterate(bound_iters)
+            b_rd = hb.read()[0]
+        t_bound = reduce_max(time.perf_counter() - t0, dist, "cuda")
+        to_bound = {"iterations": bound_iters, "check_every": 100, "seconds": t_bound, "bound_rd": b_rd,
+                    "what": "wall time from lcs_bound_create to lcs_bound_read (zero start), allocation included"}
+
     clocks = clk.summary()
     if rank == 0:
         line = {
@@ -624,10 +643,10 @@ def main():
             "config": {
                 "workload": workload_name(cfg, args),
                 "states": n,
-                "stored_states": hnd.n_stored,
+                "stored_states": n_stored,
                 "sweeps_per_step": C,
-                "symmetry": bool(args.symmetry and hnd.n_stored < n),
-                "l2": "inputs larger than L2 (each iterate vector is %.1f GiB)" % (hnd.n_stored * 8 / 2 ** 30),
+                "symmetry": bool(args.symmetry and n_stored < n),
+                "l2": "inputs larger than L2 (each iterate vector is %.1f GiB)" % (n_stored * 8 / 2 ** 30),
                 "parallelism": f"replicas x{world}",
             },
             "roofline": {
@@ -649,6 +668,7 @@ def main():
             "clocks": clocks,
             "result": {"bound_rd": bound, "r": r, "eps": eps, "kept_iter": at_iter, "argmin_state": argmin,
                        "iterations": rep["iters_done"]},
+            "time_to_bound": to_bound,
         }
         print(json.dumps(line), flush=True)
     hnd.close()
