@@ -467,12 +467,22 @@ def run_fp32(args, cfg, world, rank, local_rank):
         if d_ >= 3:
             variants.append(("all_advance_sets", {"f_mode": 1}))
         for name, kw in variants:
+            # wall time to the rigorous bound without per-launch events, then
+            # the same run with them for the per-sweep time
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with lb.LcsBound(s_, d_, h_, check_every=100, **kw) as hnd:
+                hnd.iterate(iters)
+                b_rd = hnd.read()[0]
+            seconds = time.perf_counter() - t0
             with lb.LcsBound(s_, d_, h_, check_every=100, timing=1, **kw) as hnd:
                 hnd.iterate(iters)
                 st = hnd.stats()
+                bound = hnd.read()[0]
+                assert bound == b_rd
                 results[f"({s_},{d_},{h_})"][name] = {
-                    "ms_per_sweep": st["sweep_ms"] / max(1, st["sweep_launches"]), "bound": hnd.read()[0],
-                    "stored_states": n_stored, **kw}
+                    "ms_per_sweep": st["sweep_ms"] / max(1, st["sweep_launches"]), "bound": bound,
+                    "seconds_to_bound": seconds, "stored_states": hnd.n_stored, **kw}
     if rank == 0:
         print(json.dumps({"metric": "float32 storage experiment: error vs exact iterates and sweep time",
                           "config": {"workload": "zero start, 1500 iterations; float32 vs fixed point with full "
