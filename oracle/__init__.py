@@ -260,8 +260,9 @@ def F_generated(sigma: int, d: int, h: int, seeds, bases, spread: int, xs,
                 frac_bits: int = DEFAULT_FRAC_BITS, symmetric: int = 0) -> np.ndarray:
     """F (fx) at the states xs, argument k being bases[k-1] + (SplitMix64(seeds[k-1], c(y)) mod spread).
 
-    c(y) = y (symmetric = 0), min(y, N-1-y) (1), or the smallest index of y's
-    orbit under complement and string swap (2; sigma = d = 2).
+    c(y) = y (symmetric = 0), min(y, N-1-y) (1), the smallest index of y's
+    orbit under complement and string swap (2; sigma = d = 2), or under
+    complement and the orders of the three strings (3; sigma = 2, d = 3).
     """
     seeds = np.ascontiguousarray(seeds, dtype=np.uint64)
     bases = np.ascontiguousarray(bases, dtype=np.int64)

@@ -371,7 +371,9 @@ uint64_t orc_splitmix64_at(uint64_t seed, uint64_t i) { return splitmix64_at(see
 
 /* canonical index of y for generated inputs: symmetric = 0: y; 1: the smaller
  * of y and its complement N-1-y; 2 (sigma = d = 2): the smallest of y, its
- * complement, its swap (the two strings exchanged) and the swapped complement */
+ * complement, its swap (the two strings exchanged) and the swapped complement;
+ * 3 (sigma = 2, d = 3): the smallest of the images of y under the six
+ * orders of the three strings, each with and without the complement */
 static uint64_t canonical_index(const shape_t* s, uint64_t y, int symmetric) {
   if (symmetric == 0) return y;
   uint64_t c = s->n - 1 - y, best = y < c ? y : c;
@@ -381,23 +383,38 @@ static uint64_t canonical_index(const shape_t* s, uint64_t y, int symmetric) {
     if (w < best) best = w;
     if (wc < best) best = wc;
   }
+  if (symmetric == 3) {
+    /* string j's letter at position p sits at bit 3 (h-1-p) + 2 - j */
+    static const int order[6][3] = {{0, 1, 2}, {0, 2, 1}, {1, 0, 2}, {1, 2, 0}, {2, 0, 1}, {2, 1, 0}};
+    for (int q = 0; q < 6; ++q) {
+      uint64_t w = 0;
+      for (int j = 0; j < 3; ++j)      /* the new string j is the old string order[q][j] */
+        for (int i = 0; i < s->h; ++i) /* bit i of string order[q][j] */
+          w |= ((y >> (3 * i + 2 - order[q][j])) & 1ull) << (3 * i + 2 - j);
+      uint64_t wc = s->n - 1 - w;
+      if (w < best) best = w;
+      if (wc < best) best = wc;
+    }
+  }
   return best;
 }
 
 /* F (fx) at the states xs[0..m) with argument k (1-based) given by
  * base[k-1] + (splitmix64_at(seed[k-1], canonical_index(y)) mod spread), so
  * that symmetric = 1 gives inputs invariant under the complement map of
- * sigma = 2 and symmetric = 2 inputs also invariant under exchanging the two
- * strings (sigma = d = 2).  Each state is evaluated exactly as F_state_fx
+ * sigma = 2, symmetric = 2 inputs also invariant under exchanging the two
+ * strings (sigma = d = 2) and symmetric = 3 inputs under every order of the
+ * three strings (sigma = 2, d = 3).  Each state is evaluated exactly as F_state_fx
  * does, reading through the generator. */
 int orc_F_fx_generated(int sigma, int d, int h, int frac_bits, const uint64_t* seed, const int64_t* base, uint64_t spread,
                        int symmetric, const uint64_t* xs, uint64_t m, int64_t* out) {
   shape_t s;
   int st = make_shape(sigma, d, h, &s);
   if (st) return st;
-  if (frac_bits < 0 || frac_bits > 60 || spread == 0 || symmetric < 0 || symmetric > 2) return ORC_EINVAL;
+  if (frac_bits < 0 || frac_bits > 60 || spread == 0 || symmetric < 0 || symmetric > 3) return ORC_EINVAL;
   if (symmetric && sigma != 2) return ORC_EINVAL;
   if (symmetric == 2 && d != 2) return ORC_EINVAL;
+  if (symmetric == 3 && d != 3) return ORC_EINVAL;
   int X[ORC_MAXD * ORC_MAXH], Y[ORC_MAXD * ORC_MAXH];
   int sets[ORC_MAXSETS][ORC_MAXD];
   int sizes[ORC_MAXSETS];
