@@ -220,16 +220,28 @@ __global__ void __launch_bounds__(kTcThreads, 1) mlp_table_tc_kernel(TcParams p)
         zf += (pair & 1u) ? w[pp][3] : w[pp][2];
       }
       zf += (q0 & 128u) ? w[8][1] : w[8][0];
-#pragma unroll 4
-      for (int r = 0; r < kTileRows; ++r) {
-        float z = zf + ((r & 64) ? w[8][3] : w[8][2]);
+      // row r = (b8, pair 9, pair 10, pair 11) in bits 6, 5..4, 3..2, 1..0:
+      // the loops are unrolled, so every weight is chosen at compile time and
+      // rows that share a prefix share its partial sum (the same additions,
+      // in the same order, as one running sum per row)
+      unsigned char* const a_col = sA + cm_off(0, tid);
 #pragma unroll
-        for (int pp = 9; pp < kHin; ++pp) {
-          const uint32_t pair = ((uint32_t)r >> (2 * (kHin - 1 - pp))) & 3u;
-          z += (pair & 2u) ? w[pp][1] : w[pp][0];
-          z += (pair & 1u) ? w[pp][3] : w[pp][2];
+      for (int b8 = 0; b8 < 2; ++b8) {
+        const float z8 = zf + w[8][2 + b8];
+#pragma unroll
+        for (int p9 = 0; p9 < 4; ++p9) {
+          const float z9 = (z8 + w[9][p9 >> 1]) + w[9][2 + (p9 & 1)];
+#pragma unroll
+          for (int p10 = 0; p10 < 4; ++p10) {
+            const float z10 = (z9 + w[10][p10 >> 1]) + w[10][2 + (p10 & 1)];
+#pragma unroll
+            for (int p11 = 0; p11 < 4; ++p11) {
+              const float z = (z10 + w[11][p11 >> 1]) + w[11][2 + (p11 & 1)];
+              const int r = (b8 << 6) | (p9 << 4) | (p10 << 2) | p11;
+              *reinterpret_cast<__nv_bfloat16*>(a_col + cm_off(r, 0)) = __float2bfloat16_rn(gelu_as(z));
+            }
+          }
         }
-        *reinterpret_cast<__nv_bfloat16*>(sA + cm_off(r, tid)) = __float2bfloat16_rn(gelu_as(z));
       }
     } else {
       for (int r = 0; r < kTileRows; ++r) {
