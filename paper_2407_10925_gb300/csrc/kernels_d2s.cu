@@ -25,9 +25,7 @@ int d2s_min_h(int sigma) {
 template <int SIG>
 static unsigned long long slots_of(int h) {
   using G = D2sGeo<SIG>;
-  const int L = h - 1;
-  const unsigned long long tiles = d2s_pow<SIG>(L - G::KA) * d2s_pow<SIG>(L - G::KB);
-  return (tiles + G::TPB - 1) / G::TPB;
+  return (d2s_live_tiles<SIG>(h - 1) + G::TPB - 1) / G::TPB;
 }
 
 // CTAs' worth of work in one sweep or check (one tile slot per CTA and step)

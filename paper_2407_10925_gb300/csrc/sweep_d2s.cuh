@@ -26,8 +26,12 @@
 // Tiles.  A tile covers sigma^KA values of A by sigma^KB values of B
 // (KA = KB or KB + 1), one pair per thread; inside a tile the thread index
 // interleaves the digits A0, B0, A1, B1, ..., which is the digit order of the
-// addresses of P(t, g): a warp's reads of v_{t-1} are contiguous.  Tiles with
-// every A above every B are skipped; threads with A > B have no pair.
+// addresses of P(t, g): a warp's reads of v_{t-1} are contiguous.  Tile
+// (TA, TB) holds a pair (some A <= B) iff TB >= RHO TA with RHO =
+// sigma^(KA - KB), so row TA holds nTB - RHO TA live tiles; the kernels walk
+// the live tiles only, numbered row by row, and CTAs take every grid-th one:
+// the work splits evenly over the CTAs and the tiles in flight are
+// neighbours.  Threads with A > B have no pair.
 #pragma once
 
 #include <climits>
@@ -43,6 +47,7 @@ struct D2sGeo {
   static constexpr int KB = SIG == 5 ? 1 : 2;
   static constexpr int T = (int)cpow(SIG, KA + KB);  // threads of one tile
   static constexpr int TPB = kBlock / T;             // tiles per CTA
+  static constexpr unsigned long long RHO = cpow(SIG, KA - KB);
   static constexpr unsigned long long S2 = (unsigned long long)SIG * SIG;
   static_assert(TPB >= 1, "a tile must fit a CTA");
 };
@@ -67,17 +72,47 @@ __device__ __forceinline__ unsigned long long d2s_spread(unsigned long long x, i
   return r;
 }
 
+// live tiles before row TA: P(TA) = TA nTB - RHO TA (TA - 1) / 2
+template <int SIG>
+__host__ __device__ inline unsigned long long d2s_live_before(unsigned long long TA, unsigned long long nTB) {
+  return TA * nTB - D2sGeo<SIG>::RHO * (TA * (TA - 1) / 2);
+}
+
+// live tiles of one sweep (every row TA < nTA holds at least RHO of them)
+template <int SIG>
+__host__ __device__ inline unsigned long long d2s_live_tiles(int L) {
+  using G = D2sGeo<SIG>;
+  return d2s_live_before<SIG>(d2s_pow<SIG>(L - G::KA), d2s_pow<SIG>(L - G::KB));
+}
+
+// live tile j -> (TA, TB): TA is the row with P(TA) <= j < P(TA + 1), the
+// root of the quadratic P(TA) = j estimated in float and corrected exactly
+template <int SIG>
+__device__ __forceinline__ void d2s_live_tile(unsigned long long j, unsigned long long nTB, unsigned long long& TA,
+                                              unsigned long long& TB) {
+  constexpr float rho = (float)D2sGeo<SIG>::RHO;
+  const float b = (float)nTB + 0.5f * rho;
+  const float disc = fmaxf(b * b - 2.0f * rho * (float)j, 0.0f);
+  long long t = (long long)((b - sqrtf(disc)) / rho);
+  if (t < 0) t = 0;
+  while (t > 0 && d2s_live_before<SIG>((unsigned long long)t, nTB) > j) --t;
+  while (d2s_live_before<SIG>((unsigned long long)t + 1, nTB) <= j) ++t;
+  TA = (unsigned long long)t;
+  TB = D2sGeo<SIG>::RHO * TA + (j - d2s_live_before<SIG>(TA, nTB));
+}
+
 struct D2sPair {
   unsigned long long t, ts;  // tail indices of (a, b) and (b, a)
   unsigned long long eA, eB;  // spread digits of A and B
 };
 
-// The pair owned by thread r of tile k; false if it has none.
+// The pair owned by thread r of live tile j; false if it has none.
 template <int SIG>
-__device__ __forceinline__ bool d2s_pair(unsigned long long k, int L, unsigned r, D2sPair& o) {
+__device__ __forceinline__ bool d2s_pair(unsigned long long j, int L, unsigned r, D2sPair& o) {
   using G = D2sGeo<SIG>;
   const unsigned long long nTB = d2s_pow<SIG>(L - G::KB);
-  const unsigned long long TA = k / nTB, TB = k - TA * nTB;
+  unsigned long long TA, TB;
+  d2s_live_tile<SIG>(j, nTB, TA, TB);
   // digits of r: A0, B0, A1, B1, ... (A first); A has KA digits, B has KB
   unsigned long long ia = 0, ib = 0, wa = 1, wb = 1;
   unsigned rr = r;
@@ -217,7 +252,7 @@ template <int SIG, bool INCR>
 __global__ void __launch_bounds__(kBlock) sweep_d2s_kernel(SweepParams p) {
   using G = D2sGeo<SIG>;
   const int L = p.h - 1;
-  const unsigned long long n_tiles = d2s_pow<SIG>(L - G::KA) * d2s_pow<SIG>(L - G::KB);
+  const unsigned long long n_tiles = d2s_live_tiles<SIG>(L);
   const unsigned long long n_slots = (n_tiles + G::TPB - 1) / G::TPB;
   const unsigned sub = threadIdx.x / G::T, r = threadIdx.x % G::T;
   long long best_v = p.r_mode ? LLONG_MIN : LLONG_MAX;
@@ -236,7 +271,7 @@ template <int SIG>
 __global__ void __launch_bounds__(kBlock) check_d2s_kernel(CheckParams p) {
   using G = D2sGeo<SIG>;
   const int L = p.h - 1;
-  const unsigned long long n_tiles = d2s_pow<SIG>(L - G::KA) * d2s_pow<SIG>(L - G::KB);
+  const unsigned long long n_tiles = d2s_live_tiles<SIG>(L);
   const unsigned long long n_slots = (n_tiles + G::TPB - 1) / G::TPB;
   const unsigned sub = threadIdx.x / G::T, r = threadIdx.x % G::T;
   const long long R = p.R_from_state ? p.state->R : p.R;
