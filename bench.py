@@ -39,9 +39,9 @@ CONFIGS = {
     "warm": dict(sigma=2, d=2, h=14, train_h=[10, 11, 12], ref_iters=4000, train_steps=3000),
     "warm16": dict(sigma=2, d=2, h=16, train_h=[10, 11, 12], ref_iters=1000, train_steps=3000),
     "fp32": dict(sigma=0, d=0, h=0, shapes=[(2, 3, 8), (3, 2, 8)], iters=1500),
-    "h17": dict(sigma=2, d=2, h=17),  # 2^34 states: 3 x 64 GiB resident (Table 2's l = 17); use --no-e2e
+    "h17": dict(sigma=2, d=2, h=17, bound_iters=400),  # 2^34 states: 3 x 64 GiB resident (Table 2's l = 17); use --no-e2e
     "h16": dict(sigma=2, d=2, h=16, bound_iters=2000),
-    "d3h11": dict(sigma=2, d=3, h=11),  # 2^33 states, 4 x 32 GiB: beyond Table 3's l = 10 for d = 3
+    "d3h11": dict(sigma=2, d=3, h=11, bound_iters=400),  # 2^33 states, 4 x 32 GiB: beyond Table 3's l = 10 for d = 3
     "d3h9": dict(sigma=2, d=3, h=9),  # 2^27 states (2 GiB resident): profiling size of the d = 3 kernels
     "h14": dict(sigma=2, d=2, h=14),
     "h12": dict(sigma=2, d=2, h=12),
