@@ -720,6 +720,18 @@ static lcs_status ensure_staging(lcs_bound* H, size_t bytes) {
 
 static const size_t kChunk = (size_t)32 << 20;  // elements per host transfer chunk (256 MiB)
 
+// a host <-> device copy of n values in kChunk pieces: single copies of tens
+// of GiB were seen to run at a third of the link's rate while 256 MiB pieces
+// kept it, and the pieces cost nothing measurable where single copies are fast
+static lcs_status copy_chunked(void* dst, const void* src, unsigned long long n, cudaMemcpyKind kind,
+                               cudaStream_t stream) {
+  for (unsigned long long off = 0; off < n; off += kChunk) {
+    const unsigned long long len = std::min<unsigned long long>(kChunk, n - off);
+    LCS_CUDA(cudaMemcpyAsync((char*)dst + off * 8, (const char*)src + off * 8, len * 8, kind, stream));
+  }
+  return LCS_OK;
+}
+
 // Ingest [off, off+len) of an input vector.  Under complement-symmetric
 // storage the part below n_stored is written before the part above it is
 // compared with its mirror: two launches, ordered on the stream.
@@ -778,8 +790,11 @@ static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_d
   for (int k = 0; k < H->d; ++k) {
     long long* dst = H->ring[H->d - 1 - k];
     if (stored) {
-      LCS_CUDA(cudaMemcpyAsync(dst, v[k], H->n_stored * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice,
-                               H->stream));
+      if (on_device) {
+        LCS_CUDA(cudaMemcpyAsync(dst, v[k], H->n_stored * 8, cudaMemcpyDeviceToDevice, H->stream));
+      } else if (lcs_status st = copy_chunked(dst, v[k], H->n_stored, cudaMemcpyHostToDevice, H->stream)) {
+        return st;
+      }
     } else if (on_device) {
       lcs_status st = ingest_range(H, v[k], 0, H->n_total, dst, from_double, scale);
       if (st) return st;
@@ -839,8 +854,11 @@ lcs_status lcs_bound_export_stored_fx(lcs_bound_t* H, int k, int64_t* dst, int o
     const int rows = H->d + 1;
     src = H->ring[(H->newest - k + rows) % rows];
   }
-  LCS_CUDA(cudaMemcpyAsync(dst, src, H->n_stored * 8, on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost,
-                           H->stream));
+  if (on_device) {
+    LCS_CUDA(cudaMemcpyAsync(dst, src, H->n_stored * 8, cudaMemcpyDeviceToDevice, H->stream));
+  } else if (lcs_status st = copy_chunked(dst, src, H->n_stored, cudaMemcpyDeviceToHost, H->stream)) {
+    return st;
+  }
   if (!on_device) LCS_CUDA(cudaStreamSynchronize(H->stream));
   return LCS_OK;
 }
@@ -878,7 +896,7 @@ lcs_status lcs_bound_set_start_orbit_fx(lcs_bound_t* H, const int64_t* const* v,
   for (int k = 0; k < H->d; ++k) {
     const long long* src = reinterpret_cast<const long long*>(v[k]);
     if (!on_device) {
-      LCS_CUDA(cudaMemcpyAsync(scratch, v[k], n_orb * 8, cudaMemcpyHostToDevice, H->stream));
+      if (lcs_status st = copy_chunked(scratch, v[k], n_orb, cudaMemcpyHostToDevice, H->stream)) return st;
       src = scratch;
     }
     launch_orbit_unpack(src, H->ring[H->d - 1 - k], H->h, H->n_tail, H->dstate, H->stream);
@@ -915,7 +933,7 @@ lcs_status lcs_bound_export_orbit_fx(lcs_bound_t* H, int k, int64_t* dst, int on
   launch_orbit_pack(src, scratch, H->h, H->n_tail, H->stream);
   LCS_CUDA(cudaGetLastError());
   H->launches++;
-  LCS_CUDA(cudaMemcpyAsync(dst, scratch, n_orb * 8, cudaMemcpyDeviceToHost, H->stream));
+  if (lcs_status st = copy_chunked(dst, scratch, n_orb, cudaMemcpyDeviceToHost, H->stream)) return st;
   LCS_CUDA(cudaStreamSynchronize(H->stream));
   return LCS_OK;
 }

@@ -226,3 +226,19 @@ def test_orbit_form_errors(lb):
         with pytest.raises(lb.LcsError) as e:
             hnd.set_start_orbit_fx([buf[1:], buf[1:]])  # 8-byte aligned only
         assert e.value.status == lb.LCS_EINVAL
+
+
+def test_orbit_form_of_the_kept_u(lb):
+    h = 6
+    with lb.LcsBound(2, 2, h, check_every=5, keep_u=1) as a:
+        a.iterate(23)
+        u_full = a.export_fx(-1)
+        u_orb = a.export_orbit_fx(-1)
+        assert np.array_equal(u_orb, _orbit_reference(u_full, h))
+        with pytest.raises(lb.LcsError) as e:
+            a.export_orbit_fx(2)  # k outside -1..d-1
+        assert e.value.status == lb.LCS_EINVAL
+    with lb.LcsBound(2, 2, h, check_every=5) as b:
+        with pytest.raises(lb.LcsError) as e:
+            b.export_orbit_fx(-1)  # u is not retained
+        assert e.value.status == lb.LCS_EINVAL
