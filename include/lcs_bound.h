@@ -107,11 +107,17 @@ typedef struct {
 /* Fill *opts with the defaults listed above. */
 lcs_status lcs_bound_default_opts(lcs_bound_opts* opts);
 
-/* Create a handle for the shape (sigma, d, h): sigma >= 2, d >= 2, h >= 1,
- * sigma^(d h) < 2^40 states.  Allocates d+1 iterate vectors (d+2 with keep_u)
- * on the current device and sets v_0 = .. = v_{d-1} = 0 (Algorithm 2's zero
- * start).  opts may be NULL (defaults).  On failure *out is NULL.
- * Synchronous. */
+/* Create a handle for the shape (sigma, d, h): sigma >= 2, 2 <= d <= 16,
+ * h >= 1, sigma^(d h) < 2^40 states (LCS_EINVAL otherwise).  Allocates d+1
+ * iterate vectors (d+2 with keep_u) on the current device and sets v_0 = .. =
+ * v_{d-1} = 0 (Algorithm 2's zero start).  opts may be NULL (defaults).  On
+ * failure *out is NULL.  Synchronous.
+ * Kernels: specialised ones for sigma = 2 (d = 2..5), sigma = 3 (d = 2, 3)
+ * and sigma = 4, 5 (d = 2); every other shape with sigma <= 10 runs the
+ * general kernels (f_mode 0 only, full storage whatever opts.symmetry says,
+ * one CTA per tail tuple).  Larger sigma, or f_mode 1 without a specialised
+ * kernel: LCS_EUNSUPPORTED.  Sums of sigma^d values must stay inside int64:
+ * large sigma^d needs fewer fractional bits (LCS_EOVERFLOW otherwise). */
 lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts, lcs_bound_t** out);
 
 /* Number of states sigma^(d h) of the handle's shape, and the number the

@@ -26,6 +26,7 @@ SOURCES = [
     "noalloc.cu",
     "kernels_s2d2.cu",
     "kernels_orbit.cu",
+    "kernels_rt.cu",
     "kernels_d2s.cu",
     "kernels_d3s.cu",
     "batch.cu",

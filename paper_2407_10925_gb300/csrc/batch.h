@@ -38,6 +38,9 @@ unsigned long long d2s_slots(int sigma, int h);
 void launch_swap_check_d2s(int sigma, const long long* v, unsigned long long n, int h, DevState* st, int grid,
                            cudaStream_t s);
 
+// provided by kernels_rt.cu: the general kernels (any d, full storage, f_mode 0)
+const KernelSet* kernels_rt(int sigma);
+
 // provided by kernels_orbit.cu (sigma = d = 2 orbit form)
 unsigned long long orbit_len(int h);
 void launch_orbit_unpack(const long long* orb, long long* out, int h, unsigned long long n_tail, DevState* st,

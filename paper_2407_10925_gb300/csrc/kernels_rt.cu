@@ -1,0 +1,14 @@
+// Instantiation of the general sweep and check (any d up to kMaxD, full
+// storage, f_mode 0) for sigma = 2 .. 10.
+#include "sweep_rt.cuh"
+
+namespace lcs {
+
+const KernelSet* kernels_rt(int sigma) {
+  static const KernelSet k[] = {make_rt_set<2>(), make_rt_set<3>(), make_rt_set<4>(), make_rt_set<5>(),
+                                make_rt_set<6>(), make_rt_set<7>(), make_rt_set<8>(), make_rt_set<9>(),
+                                make_rt_set<10>()};
+  return sigma >= 2 && sigma <= 10 ? &k[sigma - 2] : nullptr;
+}
+
+}  // namespace lcs

@@ -405,8 +405,13 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
     n *= (unsigned long long)sigma;
     if (n >= (1ull << 40)) return fail(LCS_EINVAL, "sigma^(d h) must be below 2^40");
   }
-  const int sym = (sigma == 2 && opts.symmetry && h >= 2) ? 1 : 0;
+  int sym = (sigma == 2 && opts.symmetry && h >= 2) ? 1 : 0;
   const KernelSet* ks = find_kernels(sigma, d, sym, opts.f_mode);
+  if (!ks && opts.f_mode == 0) {
+    // no specialised kernel: the general one, with full storage
+    ks = kernels_rt(sigma);
+    sym = 0;
+  }
   if (!ks) return fail(LCS_EUNSUPPORTED, "no kernel compiled for sigma=%d d=%d f_mode=%d", sigma, d, opts.f_mode);
   // kernels that also use the swap symmetry (used while the iterates have it)
   const KernelSet* ks_swap = nullptr;
@@ -455,7 +460,9 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H->device);
   if (sms < 1) sms = 1;
-  const unsigned long long thread_items = sym ? H->n_tail / 2 : H->n_tail;
+  // the general kernels take one tail tuple per CTA
+  const unsigned long long thread_items =
+      ks->tails_per_thread == 0 ? H->n_tail * kBlock : (sym ? H->n_tail / 2 : H->n_tail);
   H->grid_sweep = grid_for(ks->sweep_fn, sms, thread_items);
   H->grid_check = grid_for(ks->check_fn, sms, thread_items);
   H->n_partials = std::max(H->grid_sweep, H->grid_check);
@@ -642,7 +649,9 @@ lcs_status lcs_bound_iterate(lcs_bound_t* H, int64_t n_iters) {
     st = timed_end(H, a, true);
     if (st) return st;
     H->sweep_n++;
-    H->sweep_bytes += (unsigned long long)K->sweep_algo_bytes * H->n_stored;
+    // the general kernels: every output written once, each of the d inputs read once
+    const int algo = K->tails_per_thread == 0 ? 8 * (H->d + 1) : K->sweep_algo_bytes;
+    H->sweep_bytes += (unsigned long long)algo * H->n_stored;
     H->launches++;
     if (check) {
       finalize_incr_kernel<<<1, kFinalBlock, 0, H->stream>>>(H->partials, grid, H->opts.r_mode, H->dstate, it);
@@ -1311,6 +1320,7 @@ lcs_status lcs_sweep_fx(int sigma, int d, int h, int f_mode, int frac_bits, cons
   }
   for (int i = 0; i < d; ++i) sd *= (unsigned long long)sigma;
   const KernelSet* ks = find_kernels(sigma, d, 0, f_mode);
+  if (!ks && f_mode == 0) ks = kernels_rt(sigma);
   if (!ks) return fail(LCS_EUNSUPPORTED, "no kernel for sigma=%d d=%d f_mode=%d", sigma, d, f_mode);
   SweepParams p{};
   for (int k = 0; k < d; ++k) {
@@ -1327,7 +1337,7 @@ lcs_status lcs_sweep_fx(int sigma, int d, int h, int f_mode, int frac_bits, cons
   int dev = 0, sms = 1;
   LCS_CUDA(cudaGetDevice(&dev));
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = grid_for(ks->sweep_fn, std::max(sms, 1), p.n_tail);
+  const int grid = grid_for(ks->sweep_fn, std::max(sms, 1), ks->tails_per_thread == 0 ? p.n_tail * kBlock : p.n_tail);
   ks->sweep(p, grid, (cudaStream_t)stream);
   LCS_CUDA(cudaGetLastError());
   return LCS_OK;

@@ -7,7 +7,7 @@
 
 namespace lcs {
 
-constexpr int kMaxD = 8;          // largest d with a compiled kernel
+constexpr int kMaxD = 16;         // largest d (the general kernel takes any d up to it)
 constexpr int kBlock = 256;       // threads per CTA of the sweep and check kernels
 constexpr int kFinalBlock = 1024; // threads of the single-CTA finalize kernels
 

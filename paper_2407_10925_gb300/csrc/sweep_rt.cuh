@@ -1,0 +1,259 @@
+// sweep_rt.cuh -- the sweep and check for every shape without a specialised
+// kernel: d only known at run time (2 .. kMaxD), sigma a template parameter,
+// full storage, the paper's F (f_mode 0).
+//
+// Algorithm 1 and Eq. ineq3 for a state with heads H and tail tuple t (the
+// h - 1 non-head positions of the d strings): for every letter z whose set
+// N_z = {j : H_j != z} of strings to advance is not empty, the candidate is
+//   M(z, S) / sigma^|N|,   S = {j : H_j = z},  N = the other strings,
+//   M(z, S) = sum over c in Sigma^|N| of v_{t-|N|}[state with string j = z t_j
+//             for j in S and string j = t_j c_j for j in N],
+// and v = [all heads equal] + max of the candidates, every mean rounded down.
+// M depends on the heads only through (z, S), and M(z, {}) (every string
+// advances) not on z.  One CTA takes one tail tuple at a time: it forms the
+// table of every M(z, S) in shared memory, then its threads take the sigma^d
+// head combinations and read their sigma candidates from the table.  An
+// entry serves the (sigma - 1)^|N| head combinations with heads z on S and
+// other letters on N.  Where the table would not fit (sigma = 2 with d >= 12,
+// where no entry serves two states anyway) each thread forms its own
+// candidates.
+//
+// Index arithmetic (the STATE INDEX of the interface): the tail tuple t is the
+// low d (h-1) base-sigma digits of a state's index and the heads the top d, so
+// state (H, t) is Hidx n_tail + t with Hidx = sum_j H_j sigma^(d-1-j).  With
+// tp_j the digits of string j in t (at their weights in t), string j = z t_j
+// contributes z n_tail sigma^(d-1-j) + tp_j, and string j = t_j c contributes
+// sigma^d tp_j + c sigma^(d-1-j): advancing shifts its digits up one position.
+#pragma once
+
+#include <climits>
+
+#include "lcs_common.h"
+#include "sweep_generic.cuh"
+
+namespace lcs {
+
+constexpr int kRtTable = 6000;  // entries of the shared table (47 KiB; the static limit is 48 KiB)
+
+template <int SIG>
+struct RtGeo {
+  int d;
+  unsigned full;                  // the set of all d strings
+  unsigned long long sd;          // sigma^d head combinations
+  unsigned long long n_tail;
+  unsigned long long pw[kMaxD + 1];  // sigma^k
+  bool table;                     // the table fits in shared memory
+};
+
+template <int SIG>
+__device__ __forceinline__ RtGeo<SIG> rt_geo(unsigned long long n_stored, int h, unsigned long long n_tail) {
+  RtGeo<SIG> g;
+  int dh = 0;
+  for (unsigned long long m = n_stored; m > 1; m /= SIG) ++dh;
+  g.d = dh / h;
+  g.full = (1u << g.d) - 1;
+  g.pw[0] = 1;
+  for (int k = 1; k <= kMaxD; ++k) g.pw[k] = g.pw[k - 1] * (k <= g.d ? SIG : 1);
+  g.sd = g.pw[g.d];
+  g.n_tail = n_tail;
+  g.table = (unsigned long long)SIG << g.d <= (unsigned long long)kRtTable;
+  return g;
+}
+
+// floor(a / m) for m > 0
+__device__ __forceinline__ long long rt_floor_div(long long a, unsigned long long m) {
+  const long long mm = (long long)m;
+  long long q = a / mm;
+  return q - ((a - q * mm) < 0);
+}
+
+// tp[j]: the digits of string j in tail tuple t
+template <int SIG>
+__device__ __forceinline__ void rt_tail_parts(const RtGeo<SIG>& g, int h, unsigned long long t,
+                                              unsigned long long (&tp)[kMaxD]) {
+  for (int j = 0; j < g.d; ++j) tp[j] = 0;
+  unsigned long long w = 1;
+  for (int q = 0; q < g.d * (h - 1); ++q) {
+    tp[g.d - 1 - q % g.d] += (t % SIG) * w;
+    t /= SIG;
+    w *= SIG;
+  }
+}
+
+// M(z, S) from vector v: strings in S keep head z and their tail, the others
+// advance and take every letter c
+template <int SIG>
+__device__ __forceinline__ long long rt_sum(const RtGeo<SIG>& g, const unsigned long long (&tp)[kMaxD], int z,
+                                            unsigned S, const long long* __restrict__ v) {
+  unsigned long long base = 0;
+  unsigned long long w[kMaxD];
+  int n = 0;
+  for (int j = 0; j < g.d; ++j) {
+    if ((S >> j) & 1u) {
+      base += (unsigned long long)z * g.n_tail * g.pw[g.d - 1 - j] + tp[j];
+    } else {
+      base += g.sd * tp[j];
+      w[n++] = g.pw[g.d - 1 - j];
+    }
+  }
+  // every c in Sigma^n: a base-sigma counter over the advanced strings
+  int c[kMaxD];
+  for (int i = 0; i < n; ++i) c[i] = 0;
+  unsigned long long off = 0;
+  long long s = 0;
+  for (;;) {
+    s += ld_vec<false>(v + base + off);
+    int i = 0;
+    for (; i < n; ++i) {
+      if (++c[i] < SIG) {
+        off += w[i];
+        break;
+      }
+      c[i] = 0;
+      off -= (unsigned long long)(SIG - 1) * w[i];
+    }
+    if (i == n) break;
+  }
+  return s;
+}
+
+// the table entry of (z, S): S = {} is shared by every z
+__device__ __forceinline__ int rt_entry(int z, unsigned S, int d) { return S ? (z << d) | (int)S : 0; }
+
+template <int SIG>
+__device__ __forceinline__ void rt_fill_table(const RtGeo<SIG>& g, const unsigned long long (&tp)[kMaxD],
+                                              const long long* const* vs, long long* table) {
+  const int entries = SIG << g.d;
+  for (int e = threadIdx.x; e < entries; e += blockDim.x) {
+    const int z = e >> g.d;
+    const unsigned S = (unsigned)e & g.full;
+    if (S == g.full || (S == 0 && z > 0)) continue;  // no candidate / shared entry
+    const int k = g.d - __popc(S);
+    table[e] = rt_sum<SIG>(g, tp, z, S, vs[k - 1]);
+  }
+}
+
+// the heads of combination Hidx as the sets S_z = {j : H_j = z}
+template <int SIG>
+__device__ __forceinline__ void rt_head_sets(const RtGeo<SIG>& g, unsigned long long Hidx, unsigned (&sets)[SIG]) {
+#pragma unroll
+  for (int z = 0; z < SIG; ++z) sets[z] = 0;
+  for (int j = g.d - 1; j >= 0; --j) {
+    const int hz = (int)(Hidx % SIG);
+    Hidx /= SIG;
+#pragma unroll
+    for (int z = 0; z < SIG; ++z)
+      if (hz == z) sets[z] |= 1u << j;
+  }
+}
+
+template <int SIG, bool INCR>
+__global__ void __launch_bounds__(kBlock) sweep_rt_kernel(SweepParams p) {
+  __shared__ long long table[kRtTable];
+  const RtGeo<SIG> g = rt_geo<SIG>(p.n_stored, p.h, p.n_tail);
+  long long best_v = p.r_mode ? LLONG_MIN : LLONG_MAX;
+  unsigned long long best_x = ULLONG_MAX;
+  for (unsigned long long t = blockIdx.x; t < g.n_tail; t += gridDim.x) {
+    unsigned long long tp[kMaxD];
+    rt_tail_parts<SIG>(g, p.h, t, tp);
+    if (g.table) rt_fill_table<SIG>(g, tp, p.prev, table);
+    __syncthreads();
+    for (unsigned long long Hidx = threadIdx.x; Hidx < g.sd; Hidx += blockDim.x) {
+      unsigned sets[SIG];
+      rt_head_sets<SIG>(g, Hidx, sets);
+      bool equal = false;
+      long long best = LLONG_MIN;
+#pragma unroll
+      for (int z = 0; z < SIG; ++z) {
+        if (sets[z] == g.full) {
+          equal = true;
+          continue;
+        }
+        const int k = g.d - __popc(sets[z]);
+        const long long M = g.table ? table[rt_entry(z, sets[z], g.d)] : rt_sum<SIG>(g, tp, z, sets[z], p.prev[k - 1]);
+        best = max(best, rt_floor_div(M, g.pw[k]));
+      }
+      const long long v = best + (equal ? p.one : 0);
+      const unsigned long long x = Hidx * g.n_tail + t;
+      p.out[x] = v;
+      if constexpr (INCR) {
+        const long long inc = v - ld_vec<false>(p.prev[0] + x);
+        if (red_better(inc, x, best_v, best_x, p.r_mode)) best_v = inc, best_x = x;
+      }
+    }
+    __syncthreads();  // the table is rewritten for the next tuple
+  }
+  if constexpr (INCR) block_reduce_arg(best_v, best_x, p.r_mode, p.partials);
+}
+
+// W = u + dR - F(u + (d-1)R, .., u): a candidate advancing k strings reads
+// argument k = u + (d - k)R, whose mean is the mean of u plus (d - k)R
+template <int SIG>
+__global__ void __launch_bounds__(kBlock) check_rt_kernel(CheckParams q) {
+  __shared__ long long table[kRtTable];
+  const RtGeo<SIG> g = rt_geo<SIG>(q.n_stored, q.h, q.n_tail);
+  const long long R = q.R_from_state ? q.state->R : q.R;
+  const long long* us[kMaxD];
+  for (int k = 0; k < kMaxD; ++k) us[k] = q.u;
+  long long best_w = LLONG_MIN;
+  for (unsigned long long t = blockIdx.x; t < g.n_tail; t += gridDim.x) {
+    unsigned long long tp[kMaxD];
+    rt_tail_parts<SIG>(g, q.h, t, tp);
+    if (g.table) rt_fill_table<SIG>(g, tp, us, table);
+    __syncthreads();
+    for (unsigned long long Hidx = threadIdx.x; Hidx < g.sd; Hidx += blockDim.x) {
+      unsigned sets[SIG];
+      rt_head_sets<SIG>(g, Hidx, sets);
+      bool equal = false;
+      long long best = LLONG_MIN;
+#pragma unroll
+      for (int z = 0; z < SIG; ++z) {
+        if (sets[z] == g.full) {
+          equal = true;
+          continue;
+        }
+        const int k = g.d - __popc(sets[z]);
+        const long long M = g.table ? table[rt_entry(z, sets[z], g.d)] : rt_sum<SIG>(g, tp, z, sets[z], q.u);
+        best = max(best, rt_floor_div(M, g.pw[k]) + (long long)(g.d - k) * R);
+      }
+      const unsigned long long x = Hidx * g.n_tail + t;
+      const long long F = best + (equal ? q.one : 0);
+      best_w = max(best_w, ld_vec<false>(q.u + x) + (long long)g.d * R - F);
+    }
+    __syncthreads();
+  }
+  block_reduce_max(best_w, q.partials);
+}
+
+template <int SIG>
+void launch_sweep_rt(const SweepParams& p, int grid, cudaStream_t s) {
+  if (p.incr)
+    sweep_rt_kernel<SIG, true><<<grid, kBlock, 0, s>>>(p);
+  else
+    sweep_rt_kernel<SIG, false><<<grid, kBlock, 0, s>>>(p);
+}
+
+template <int SIG>
+void launch_check_rt(const CheckParams& q, int grid, cudaStream_t s) {
+  check_rt_kernel<SIG><<<grid, kBlock, 0, s>>>(q);
+}
+
+// tails_per_thread = 0 marks a set that takes one tail tuple per CTA
+template <int SIG>
+KernelSet make_rt_set() {
+  KernelSet k{};
+  k.sigma = SIG;
+  k.d = 0;  // any d
+  k.f_mode = 0;
+  k.sym = 0;
+  k.sweep = &launch_sweep_rt<SIG>;
+  k.check = &launch_check_rt<SIG>;
+  k.sweep_fn = (const void*)&sweep_rt_kernel<SIG, true>;
+  k.check_fn = (const void*)&check_rt_kernel<SIG>;
+  k.tails_per_thread = 0;
+  k.sweep_algo_bytes = 0;  // set per handle: 8 (d + 1)
+  k.check_algo_bytes = 8;
+  return k;
+}
+
+}  // namespace lcs

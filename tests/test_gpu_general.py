@@ -1,0 +1,110 @@
+"""GPU parity of the general kernels (shapes without a specialised kernel: d up
+to 16, sigma up to 10, full storage, the paper's F) against the CPU oracle,
+bit for bit: the stateless sweep on random arguments, whole runs of Algorithm
+2 (iterates, R and its state, E, the kept triplet, the bound) from the zero
+start and from random starts, and the feasibility check of a given vector.
+
+The shapes cover both ways the kernel forms its candidates: from the shared
+table of sums (sigma * 2^d <= 6000 entries) and, for sigma = 2 with d >= 12,
+each thread on its own.  A small number of fractional bits keeps the sums of
+sigma^d terms inside int64 (the library checks that headroom for its handles).
+"""
+import numpy as np
+import pytest
+
+import inputs
+
+pytestmark = pytest.mark.gpu
+
+K = 30
+
+SWEEP_SHAPES = [(2, 6, 2), (2, 7, 1), (2, 12, 1), (2, 13, 1), (3, 4, 2), (3, 5, 1), (4, 3, 2), (5, 3, 1),
+                (6, 2, 2), (7, 3, 1), (8, 2, 3), (10, 2, 2), (9, 4, 1)]
+
+
+@pytest.fixture(scope="module")
+def lb():
+    import torch
+
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import paper_2407_10925_gb300 as lb
+
+    lb.lib()
+    return lb
+
+
+@pytest.mark.parametrize("s,d,h", SWEEP_SHAPES)
+def test_general_stateless_sweep_bit_exact(lb, orc, s, d, h):
+    import torch
+
+    vs = inputs.random_history(s, d, h, seed=300 + 11 * s + 3 * d + h, frac_bits=K)
+    want = orc.F(s, d, h, vs, arith="fx", frac_bits=K)
+    dev = [torch.from_numpy(v).cuda() for v in vs]
+    out = torch.empty(want.size, dtype=torch.int64, device="cuda")
+    lb.lcs_sweep_fx(s, d, h, dev, out, frac_bits=K)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy()
+    assert np.array_equal(got, want), np.flatnonzero(got != want)[:10]
+
+
+RUN_CASES = [
+    # s, d, h, iters, check_every, r_mode, random start
+    (2, 6, 2, 20, 5, 0, False),
+    (2, 12, 1, 12, 0, 0, False),
+    (2, 7, 1, 25, 3, 1, True),
+    (3, 4, 2, 15, 3, 0, False),
+    (3, 5, 1, 20, 4, 0, True),
+    (4, 3, 2, 12, 4, 0, False),
+    (6, 2, 2, 20, 5, 1, False),
+    (10, 2, 2, 12, 0, 0, True),
+    (5, 3, 1, 20, 1, 0, False),
+]
+
+
+@pytest.mark.parametrize("case", RUN_CASES, ids=lambda c: "s%d_d%d_h%d_it%d_ce%d_r%d_rand%d" % c)
+def test_general_run_bit_exact(lb, orc, case):
+    s, d, h, iters, check_every, r_mode, rand = case
+    start = None
+    if rand:
+        hist = inputs.random_history(s, d, h, seed=900 + s + d + h, frac_bits=K)
+        start = [hist[d - 1 - k] for k in range(d)]  # oldest first
+    want = orc.run(s, d, h, iters, arith="fx", check_every=check_every, r_mode=r_mode, frac_bits=K, start=start)
+    with lb.LcsBound(s, d, h, check_every=check_every, r_mode=r_mode, frac_bits=K) as hnd:
+        assert hnd.n_stored == hnd.n_states  # full storage
+        if start is not None:
+            hnd.set_start_fx([start[d - 1 - k] for k in range(d)])
+        hnd.iterate(iters)
+        rep = hnd.report()
+        for k in range(d):
+            got = hnd.export_fx(k)
+            assert np.array_equal(got, want["iterates"][k]), (k, np.flatnonzero(got != want["iterates"][k])[:10])
+        assert (rep["R"], rep["argmin"], rep["E"]) == (want["R"], want["argmin"], want["E"])
+        assert (rep["r"], rep["eps"], rep["kept_iter"]) == (want["r"], want["eps"], want["kept_iter"])
+        assert rep["status"] == 0
+        assert hnd.read()[0] == want["bound_rd"]
+
+
+@pytest.mark.parametrize("s,d,h", [(3, 4, 2), (2, 12, 1), (10, 2, 2), (7, 3, 1)])
+def test_general_check_vector_matches_oracle(lb, orc, s, d, h):
+    import torch
+
+    u = inputs.random_fx(s, d, h, seed=77 + s + d + h, frac_bits=K)
+    one = 1 << K
+    for R in [int(0.3 * one), int(0.45 * one), -(1 << 20)]:
+        E_want, _ = orc.check(s, d, h, u, R, arith="fx", frac_bits=K)
+        with lb.LcsBound(s, d, h, frac_bits=K) as hnd:
+            E_got = hnd.check_vector(torch.from_numpy(u).cuda(), R)
+        assert E_got == E_want, R
+
+
+def test_general_kernel_is_counted(lb):
+    with lb.LcsBound(3, 4, 2, timing=1, frac_bits=K) as hnd:
+        hnd.iterate(3)
+        assert hnd.stats()["sweep_bytes"] == 3 * 8 * (4 + 1) * 3 ** 8
+
+
+def test_all_advance_sets_stay_unsupported_without_a_kernel(lb):
+    with pytest.raises(lb.LcsError) as e:
+        lb.LcsBound(3, 4, 2, f_mode=1)
+    assert e.value.status == lb.LCS_EUNSUPPORTED
