@@ -40,6 +40,7 @@ void launch_swap_check_d2s(int sigma, const long long* v, unsigned long long n, 
 
 // provided by kernels_rt.cu: the general kernels (any d, full storage, f_mode 0)
 const KernelSet* kernels_rt(int sigma);
+unsigned long long rt_work_items(int sigma, int d, unsigned long long n_states, unsigned long long n_tail);
 
 // provided by kernels_orbit.cu (sigma = d = 2 orbit form)
 unsigned long long orbit_len(int h);

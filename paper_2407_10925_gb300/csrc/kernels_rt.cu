@@ -11,4 +11,10 @@ const KernelSet* kernels_rt(int sigma) {
   return sigma >= 2 && sigma <= 10 ? &k[sigma - 2] : nullptr;
 }
 
+// threads' worth of work of one general sweep or check, for sizing its grid:
+// one CTA per tail tuple, or one warp per state (sigma = 2, d >= kRtWarpD)
+unsigned long long rt_work_items(int sigma, int d, unsigned long long n_states, unsigned long long n_tail) {
+  return sigma == 2 && d >= kRtWarpD ? n_states * 32 : n_tail * kBlock;
+}
+
 }  // namespace lcs

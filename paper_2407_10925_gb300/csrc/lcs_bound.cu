@@ -462,7 +462,7 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   if (sms < 1) sms = 1;
   // the general kernels take one tail tuple per CTA
   const unsigned long long thread_items =
-      ks->tails_per_thread == 0 ? H->n_tail * kBlock : (sym ? H->n_tail / 2 : H->n_tail);
+      ks->tails_per_thread == 0 ? rt_work_items(sigma, d, n, H->n_tail) : (sym ? H->n_tail / 2 : H->n_tail);
   H->grid_sweep = grid_for(ks->sweep_fn, sms, thread_items);
   H->grid_check = grid_for(ks->check_fn, sms, thread_items);
   H->n_partials = std::max(H->grid_sweep, H->grid_check);
@@ -1370,7 +1370,8 @@ lcs_status lcs_sweep_fx(int sigma, int d, int h, int f_mode, int frac_bits, cons
   int dev = 0, sms = 1;
   LCS_CUDA(cudaGetDevice(&dev));
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int grid = grid_for(ks->sweep_fn, std::max(sms, 1), ks->tails_per_thread == 0 ? p.n_tail * kBlock : p.n_tail);
+  const int grid =
+      grid_for(ks->sweep_fn, std::max(sms, 1), ks->tails_per_thread == 0 ? rt_work_items(sigma, d, n, p.n_tail) : p.n_tail);
   ks->sweep(p, grid, (cudaStream_t)stream);
   LCS_CUDA(cudaGetLastError());
   return LCS_OK;

@@ -16,7 +16,12 @@
 // entry serves the (sigma - 1)^|N| head combinations with heads z on S and
 // other letters on N.  Where the table would not fit (sigma = 2 with d >= 12,
 // where no entry serves two states anyway) each thread forms its own
-// candidates.
+// candidates.  For sigma = 2 from d = kRtWarpD on, one warp takes one state
+// instead (grid-stride over all states): its lanes split each candidate's
+// 2^|N| terms, lane bits filling the five lowest offset bits and each lane
+// walking the remaining ones as submasks, so a state's cost (2^#ones +
+// 2^#zeros terms, from 2 2^(d/2) to 2^d) no longer decides a thread's, and an
+// h = 1 sweep (one tail tuple) spreads over the whole GPU.
 //
 // Index arithmetic (the STATE INDEX of the interface): the tail tuple t is the
 // low d (h-1) base-sigma digits of a state's index and the heads the top d, so
@@ -34,6 +39,7 @@
 namespace lcs {
 
 constexpr int kRtTable = 6000;  // entries of the shared table (47 KiB; the static limit is 48 KiB)
+constexpr int kRtWarpD = 9;     // sigma = 2: one warp per state from this d on
 
 template <int SIG>
 struct RtGeo {
@@ -225,8 +231,136 @@ __global__ void __launch_bounds__(kBlock) check_rt_kernel(CheckParams q) {
   block_reduce_max(best_w, q.partials);
 }
 
+// ---------------------------------------------------------------------------
+// sigma = 2, d >= kRtWarpD: one warp per state
+
+// the offsets of the terms of a candidate: bit d-1-j for every advanced string j
+__device__ __forceinline__ unsigned rt2_offset_bits(unsigned N, int d) {
+  return __brev(N) >> (32 - d);
+}
+
+// the deposit of the low bits of v into the set bits of mask
+__device__ __forceinline__ unsigned rt2_deposit(unsigned v, unsigned mask) {
+  unsigned out = 0;
+  for (int i = 0; mask; ++i) {
+    const unsigned b = mask & (0u - mask);
+    if ((v >> i) & 1u) out |= b;
+    mask ^= b;
+  }
+  return out;
+}
+
+// M(z, S) summed by the whole warp; every lane returns it
+__device__ __forceinline__ long long rt2_warp_sum(const RtGeo<2>& g, const unsigned long long (&tp)[kMaxD], int z,
+                                                  unsigned S, const long long* __restrict__ v, int lane) {
+  unsigned long long base = 0;
+  for (int j = 0; j < g.d; ++j)
+    base += ((S >> j) & 1u) ? (unsigned long long)z * g.n_tail * g.pw[g.d - 1 - j] + tp[j] : g.sd * tp[j];
+  const unsigned bits = rt2_offset_bits(g.full ^ S, g.d);
+  unsigned low = 0, rest = bits;
+  for (int i = 0; i < 5 && rest; ++i) {
+    const unsigned b = rest & (0u - rest);
+    low |= b;
+    rest ^= b;
+  }
+  long long s = 0;
+  if (lane < (1 << __popc(low))) {
+    const unsigned long long lo = rt2_deposit((unsigned)lane, low);
+    unsigned sub = 0;
+    do {
+      s += ld_vec<false>(v + base + sub + lo);
+      sub = (sub - rest) & rest;
+    } while (sub);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  return s;
+}
+
+template <bool INCR>
+__global__ void __launch_bounds__(kBlock) sweep_rt2_kernel(SweepParams p) {
+  const RtGeo<2> g = rt_geo<2>(p.n_stored, p.h, p.n_tail);
+  const int lane = threadIdx.x & 31;
+  const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  long long best_v = p.r_mode ? LLONG_MIN : LLONG_MAX;
+  unsigned long long best_x = ULLONG_MAX;
+  for (unsigned long long x = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < p.n_stored;
+       x += warps) {
+    const unsigned long long t = x % g.n_tail, Hidx = x / g.n_tail;
+    unsigned long long tp[kMaxD];
+    rt_tail_parts<2>(g, p.h, t, tp);
+    const unsigned ones = __brev((unsigned)Hidx) >> (32 - g.d);  // bit j: string j's head is 1
+    bool equal = false;
+    long long best = LLONG_MIN;
+#pragma unroll
+    for (int z = 0; z < 2; ++z) {
+      const unsigned S = z ? ones : (g.full ^ ones);
+      if (S == g.full) {
+        equal = true;
+        continue;
+      }
+      const int k = g.d - __popc(S);
+      best = max(best, rt2_warp_sum(g, tp, z, S, p.prev[k - 1], lane) >> k);  // floor of the mean
+    }
+    const long long v = best + (equal ? p.one : 0);
+    if (lane == 0) {
+      p.out[x] = v;
+      if constexpr (INCR) {
+        const long long inc = v - ld_vec<false>(p.prev[0] + x);
+        if (red_better(inc, x, best_v, best_x, p.r_mode)) best_v = inc, best_x = x;
+      }
+    }
+  }
+  if constexpr (INCR) block_reduce_arg(best_v, best_x, p.r_mode, p.partials);
+}
+
+__global__ void __launch_bounds__(kBlock) check_rt2_kernel(CheckParams q) {
+  const RtGeo<2> g = rt_geo<2>(q.n_stored, q.h, q.n_tail);
+  const long long R = q.R_from_state ? q.state->R : q.R;
+  const int lane = threadIdx.x & 31;
+  const unsigned long long warps = ((unsigned long long)gridDim.x * blockDim.x) >> 5;
+  long long best_w = LLONG_MIN;
+  for (unsigned long long x = ((unsigned long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; x < q.n_stored;
+       x += warps) {
+    const unsigned long long t = x % g.n_tail, Hidx = x / g.n_tail;
+    unsigned long long tp[kMaxD];
+    rt_tail_parts<2>(g, q.h, t, tp);
+    const unsigned ones = __brev((unsigned)Hidx) >> (32 - g.d);
+    bool equal = false;
+    long long best = LLONG_MIN;
+#pragma unroll
+    for (int z = 0; z < 2; ++z) {
+      const unsigned S = z ? ones : (g.full ^ ones);
+      if (S == g.full) {
+        equal = true;
+        continue;
+      }
+      const int k = g.d - __popc(S);
+      best = max(best, (rt2_warp_sum(g, tp, z, S, q.u, lane) >> k) + (long long)(g.d - k) * R);
+    }
+    const long long F = best + (equal ? q.one : 0);
+    if (lane == 0) best_w = max(best_w, ld_vec<false>(q.u + x) + (long long)g.d * R - F);
+  }
+  block_reduce_max(best_w, q.partials);
+}
+
+// d of a general-kernel launch: sigma^(d h) states are stored
+template <int SIG>
+inline int rt_d_of(unsigned long long n_stored, int h) {
+  int dh = 0;
+  for (unsigned long long m = n_stored; m > 1; m /= SIG) ++dh;
+  return dh / h;
+}
+
 template <int SIG>
 void launch_sweep_rt(const SweepParams& p, int grid, cudaStream_t s) {
+  if (SIG == 2 && rt_d_of<SIG>(p.n_stored, p.h) >= kRtWarpD) {
+    if (p.incr)
+      sweep_rt2_kernel<true><<<grid, kBlock, 0, s>>>(p);
+    else
+      sweep_rt2_kernel<false><<<grid, kBlock, 0, s>>>(p);
+    return;
+  }
   if (p.incr)
     sweep_rt_kernel<SIG, true><<<grid, kBlock, 0, s>>>(p);
   else
@@ -235,6 +369,10 @@ void launch_sweep_rt(const SweepParams& p, int grid, cudaStream_t s) {
 
 template <int SIG>
 void launch_check_rt(const CheckParams& q, int grid, cudaStream_t s) {
+  if (SIG == 2 && rt_d_of<SIG>(q.n_stored, q.h) >= kRtWarpD) {
+    check_rt2_kernel<<<grid, kBlock, 0, s>>>(q);
+    return;
+  }
   check_rt_kernel<SIG><<<grid, kBlock, 0, s>>>(q);
 }
 

@@ -4,9 +4,9 @@ bit for bit: the stateless sweep on random arguments, whole runs of Algorithm
 2 (iterates, R and its state, E, the kept triplet, the bound) from the zero
 start and from random starts, and the feasibility check of a given vector.
 
-The shapes cover both ways the kernel forms its candidates: from the shared
-table of sums (sigma * 2^d <= 6000 entries) and, for sigma = 2 with d >= 12,
-each thread on its own.  A small number of fractional bits keeps the sums of
+The shapes cover every way the kernels form candidates: from the shared table
+of sums (sigma * 2^d <= 6000 entries) and, for sigma = 2 from d = 9 on, one
+warp per state.  A small number of fractional bits keeps the sums of
 sigma^d terms inside int64 (the library checks that headroom for its handles).
 """
 import numpy as np
@@ -18,8 +18,8 @@ pytestmark = pytest.mark.gpu
 
 K = 30
 
-SWEEP_SHAPES = [(2, 6, 2), (2, 7, 1), (2, 12, 1), (2, 13, 1), (3, 4, 2), (3, 5, 1), (4, 3, 2), (5, 3, 1),
-                (6, 2, 2), (7, 3, 1), (8, 2, 3), (10, 2, 2), (9, 4, 1)]
+SWEEP_SHAPES = [(2, 6, 2), (2, 7, 1), (2, 9, 2), (2, 10, 1), (2, 12, 1), (2, 13, 1), (3, 4, 2), (3, 5, 1),
+                (4, 3, 2), (5, 3, 1), (6, 2, 2), (7, 3, 1), (8, 2, 3), (10, 2, 2), (9, 4, 1)]
 
 
 @pytest.fixture(scope="module")
@@ -52,6 +52,7 @@ RUN_CASES = [
     # s, d, h, iters, check_every, r_mode, random start
     (2, 6, 2, 20, 5, 0, False),
     (2, 12, 1, 12, 0, 0, False),
+    (2, 9, 2, 10, 5, 0, True),
     (2, 7, 1, 25, 3, 1, True),
     (3, 4, 2, 15, 3, 0, False),
     (3, 5, 1, 20, 4, 0, True),
@@ -85,7 +86,7 @@ def test_general_run_bit_exact(lb, orc, case):
         assert hnd.read()[0] == want["bound_rd"]
 
 
-@pytest.mark.parametrize("s,d,h", [(3, 4, 2), (2, 12, 1), (10, 2, 2), (7, 3, 1)])
+@pytest.mark.parametrize("s,d,h", [(3, 4, 2), (2, 12, 1), (2, 9, 2), (10, 2, 2), (7, 3, 1)])
 def test_general_check_vector_matches_oracle(lb, orc, s, d, h):
     import torch
 
