@@ -63,7 +63,7 @@ typedef enum {
   LCS_ETIMEOUT = 4,     /* a bounded device-side wait gave up */
   LCS_ENOBOUND = 5,     /* no feasibility check has run yet */
   LCS_EOVERFLOW = 6,    /* fixed-point headroom would be exceeded */
-  LCS_EUNSUPPORTED = 7, /* (sigma, d, f_mode) has no kernel in this build */
+  LCS_EUNSUPPORTED = 7, /* (sigma, d, f_mode) has no kernel in the library */
   LCS_EIO = 8           /* a checkpoint file could not be written or read */
 } lcs_status;
 

@@ -1,5 +1,5 @@
 """The paper's printed bounds from the GPU path, for every (sigma, d, l) of
-Table 2, Table 3 and Appendix C that this build has kernels for, that fits
+Table 2, Table 3 and Appendix C that the specialised kernels serve, that fits
 one GB300 and that the CPU oracle's own pins do not reach (those run in
 tests/test_oracle_pins.py).
 
