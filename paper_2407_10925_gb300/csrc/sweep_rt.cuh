@@ -86,15 +86,18 @@ __device__ __forceinline__ void rt_tail_parts(const RtGeo<SIG>& g, int h, unsign
   }
 }
 
-// M(z, S) from vector v: strings in S keep head z and their tail, the others
-// advance and take every letter c
+// the terms m0 .. m1-1 of M(z, S) from vector v: strings in S keep head z and
+// their tail, the others advance and take every letter c; term m is the c
+// whose base-sigma digits, least significant first, are the letters of the
+// advanced strings from the last one back
 template <int SIG>
-__device__ __forceinline__ long long rt_sum(const RtGeo<SIG>& g, const unsigned long long (&tp)[kMaxD], int z,
-                                            unsigned S, const long long* __restrict__ v) {
+__device__ __forceinline__ long long rt_sum_range(const RtGeo<SIG>& g, const unsigned long long (&tp)[kMaxD], int z,
+                                                  unsigned S, const long long* __restrict__ v, unsigned long long m0,
+                                                  unsigned long long m1) {
   unsigned long long base = 0;
   unsigned long long w[kMaxD];
   int n = 0;
-  for (int j = 0; j < g.d; ++j) {
+  for (int j = g.d - 1; j >= 0; --j) {
     if ((S >> j) & 1u) {
       base += (unsigned long long)z * g.n_tail * g.pw[g.d - 1 - j] + tp[j];
     } else {
@@ -102,15 +105,18 @@ __device__ __forceinline__ long long rt_sum(const RtGeo<SIG>& g, const unsigned 
       w[n++] = g.pw[g.d - 1 - j];
     }
   }
-  // every c in Sigma^n: a base-sigma counter over the advanced strings
+  // the counter's digits at term m0
   int c[kMaxD];
-  for (int i = 0; i < n; ++i) c[i] = 0;
-  unsigned long long off = 0;
+  unsigned long long off = 0, m = m0;
+  for (int i = 0; i < n; ++i) {
+    c[i] = (int)(m % SIG);
+    m /= SIG;
+    off += (unsigned long long)c[i] * w[i];
+  }
   long long s = 0;
-  for (;;) {
+  for (unsigned long long t = m0; t < m1; ++t) {
     s += ld_vec<false>(v + base + off);
-    int i = 0;
-    for (; i < n; ++i) {
+    for (int i = 0; i < n; ++i) {
       if (++c[i] < SIG) {
         off += w[i];
         break;
@@ -118,14 +124,24 @@ __device__ __forceinline__ long long rt_sum(const RtGeo<SIG>& g, const unsigned 
       c[i] = 0;
       off -= (unsigned long long)(SIG - 1) * w[i];
     }
-    if (i == n) break;
   }
   return s;
+}
+
+// every term of M(z, S)
+template <int SIG>
+__device__ __forceinline__ long long rt_sum(const RtGeo<SIG>& g, const unsigned long long (&tp)[kMaxD], int z,
+                                            unsigned S, const long long* __restrict__ v) {
+  return rt_sum_range<SIG>(g, tp, z, S, v, 0, g.pw[g.d - __popc(S)]);
 }
 
 // the table entry of (z, S): S = {} is shared by every z
 __device__ __forceinline__ int rt_entry(int z, unsigned S, int d) { return S ? (z << d) | (int)S : 0; }
 
+// The table of one tail tuple.  An entry's terms are loads that mostly miss
+// the caches, and the largest entry (every string advances) has sigma^d of
+// them: entries of 32 terms or more go to a whole warp, each lane summing a
+// contiguous block, the rest to single threads.
 template <int SIG>
 __device__ __forceinline__ void rt_fill_table(const RtGeo<SIG>& g, const unsigned long long (&tp)[kMaxD],
                                               const long long* const* vs, long long* table) {
@@ -135,7 +151,22 @@ __device__ __forceinline__ void rt_fill_table(const RtGeo<SIG>& g, const unsigne
     const unsigned S = (unsigned)e & g.full;
     if (S == g.full || (S == 0 && z > 0)) continue;  // no candidate / shared entry
     const int k = g.d - __popc(S);
-    table[e] = rt_sum<SIG>(g, tp, z, S, vs[k - 1]);
+    if (g.pw[k] < 32) table[e] = rt_sum<SIG>(g, tp, z, S, vs[k - 1]);
+  }
+  const int lane = threadIdx.x & 31;
+  for (int e = threadIdx.x >> 5; e < entries; e += blockDim.x >> 5) {  // uniform over the warp
+    const int z = e >> g.d;
+    const unsigned S = (unsigned)e & g.full;
+    if (S == g.full || (S == 0 && z > 0)) continue;
+    const int k = g.d - __popc(S);
+    const unsigned long long terms = g.pw[k];
+    if (terms < 32) continue;
+    const unsigned long long per = (terms + 31) / 32;
+    const unsigned long long m0 = min(terms, (unsigned long long)lane * per), m1 = min(terms, m0 + per);
+    long long sum = rt_sum_range<SIG>(g, tp, z, S, vs[k - 1], m0, m1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) table[e] = sum;
   }
 }
 
