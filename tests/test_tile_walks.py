@@ -1,0 +1,124 @@
+"""The tile walks of two symmetric sweeps, restated from their kernels with
+plain integer (and float32) arithmetic and checked against brute-force
+enumerations.  The GPU parity tests check the kernels' outputs; these check
+that the walks visit every live tile exactly once, for every size the
+kernels accept.
+
+* d = 2, sigma = 3, 4, 5 (sweep_d2s.cuh): tile (TA, TB) holds a pair (some
+  A <= B) iff TB >= RHO TA, RHO = sigma^(KA - KB); live tile j maps back to
+  its row through the root of P(TA) = TA nTB - RHO TA (TA - 1) / 2, estimated
+  in float32 and corrected exactly.
+* sigma = 2, d = 3 (sweep_d3s.cuh): the sheared box J0 < 2^max(L-3,1),
+  J1 < 2^(L-2), J2 < 2^(L-3) with I0 = J0, I1 = J0 + J1, I2 = I1 / 2 +
+  ((J2 + 37 row) mod 2^(L-3)) and the live test I1 < 2^(L-2), 4 I0 + 8 I2 <=
+  2^L - 1 visits each tile of the 4 x 4 x 8 grid that passes the corner test
+  (I0 <= I1, I1 / 2 <= I2, 4 I0 + 8 I2 <= 2^L - 1) exactly once, and every
+  orbit representative lies in one of those tiles.
+"""
+import numpy as np
+import pytest
+
+D2S_GEO = {3: (3, 2), 4: (2, 2), 5: (2, 1)}  # sigma: (KA, KB)
+
+
+def d2s_live_tiles_bruteforce(s, L):
+    KA, KB = D2S_GEO[s]
+    nTA, nTB = s ** (L - KA), s ** (L - KB)
+    out = []
+    for TA in range(nTA):
+        for TB in range(nTB):
+            # some A <= B with A in [TA s^KA, +s^KA), B in [TB s^KB, +s^KB)
+            if TA * s ** KA <= TB * s ** KB + s ** KB - 1:
+                out.append((TA, TB))
+    return out
+
+
+def d2s_live_tile(s, L, j):
+    KA, KB = D2S_GEO[s]
+    rho, nTB = s ** (KA - KB), s ** (L - KB)
+
+    def P(t):
+        return t * nTB - rho * (t * (t - 1) // 2)
+
+    b = np.float32(nTB) + np.float32(0.5) * np.float32(rho)
+    disc = max(b * b - np.float32(2.0) * np.float32(rho) * np.float32(j), np.float32(0.0))
+    t = max(int((b - np.sqrt(np.float32(disc))) / np.float32(rho)), 0)
+    while t > 0 and P(t) > j:
+        t -= 1
+    while P(t + 1) <= j:
+        t += 1
+    return t, rho * t + (j - P(t))
+
+
+@pytest.mark.parametrize("s,L", [(3, 3), (3, 4), (3, 5), (3, 6), (3, 7), (4, 2), (4, 3), (4, 4), (4, 5),
+                                 (5, 2), (5, 3), (5, 4)])
+def test_d2s_live_tile_walk(s, L):
+    want = d2s_live_tiles_bruteforce(s, L)
+    KA, KB = D2S_GEO[s]
+    nTA, nTB, rho = s ** (L - KA), s ** (L - KB), s ** (KA - KB)
+    count = nTA * nTB - rho * (nTA * (nTA - 1) // 2)
+    assert count == len(want)
+    assert [d2s_live_tile(s, L, j) for j in range(count)] == want  # row order, each once
+
+
+@pytest.mark.parametrize("s,L", [(3, 11), (4, 9), (5, 7)])
+def test_d2s_live_tile_inverse_at_the_largest_sizes(s, L):
+    """The float32 estimate plus correction at the largest shapes (sampled)."""
+    KA, KB = D2S_GEO[s]
+    nTA, nTB, rho = s ** (L - KA), s ** (L - KB), s ** (KA - KB)
+    count = nTA * nTB - rho * (nTA * (nTA - 1) // 2)
+    rng = np.random.default_rng(L)
+    for j in list(range(64)) + list(range(count - 64, count)) + [int(x) for x in rng.integers(0, count, 2000)]:
+        TA, TB = d2s_live_tile(s, L, j)
+        P = TA * nTB - rho * (TA * (TA - 1) // 2)
+        assert 0 <= TA < nTA and rho * TA <= TB < nTB and P <= j < P + (nTB - rho * TA)
+
+
+def d3s_live_tiles_bruteforce(L):
+    M = (1 << L) - 1
+    out = set()
+    for I0 in range(1 << (L - 2)):
+        for I1 in range(1 << (L - 2)):
+            for I2 in range(1 << (L - 3)):
+                if 4 * I0 <= 4 * I1 + 3 and 4 * I1 <= 8 * I2 + 7 and 4 * I0 + 8 * I2 <= M:
+                    out.add((I0, I1, I2))
+    return out
+
+
+def d3s_walk(L):
+    M = (1 << L) - 1
+    n = 1 << (max(L - 3, 1) + 2 * L - 5)
+    out = []
+    for k in range(n):
+        row = k >> (L - 3)
+        I0 = k >> (2 * L - 5)
+        I1 = I0 + (row & ((1 << (L - 2)) - 1))
+        I2 = (I1 >> 1) + ((k + 37 * row) & ((1 << (L - 3)) - 1))
+        if I1 < (1 << (L - 2)) and 4 * I0 + 8 * I2 <= M:
+            out.append((I0, I1, I2))
+    return out
+
+
+@pytest.mark.parametrize("L", [3, 4, 5, 6, 7, 8])
+def test_d3s_sheared_rotated_walk(L):
+    walk = d3s_walk(L)
+    assert len(walk) == len(set(walk))
+    assert set(walk) == d3s_live_tiles_bruteforce(L)
+
+
+@pytest.mark.parametrize("L", [3, 4, 5, 6])
+def test_d3s_every_representative_lies_in_a_live_tile(L):
+    """No representative is missed: T0 <= T1 <= T2 and (T0, T1, T2) <= (~T2,
+    ~T1, ~T0), i.e. T0 + T2 < 2^L - 1, or T0 + T2 = 2^L - 1 and T1 < 2^(L-1),
+    always lies in a live tile (live tiles may also hold none: the kernel's
+    per-thread test drops those)."""
+    M = (1 << L) - 1
+    live = d3s_live_tiles_bruteforce(L)
+    n_rep = 0
+    for T0 in range(1 << L):
+        for T1 in range(T0, 1 << L):
+            for T2 in range(T1, 1 << L):
+                if T0 + T2 < M or (T0 + T2 == M and T1 < (1 << (L - 1))):
+                    n_rep += 1
+                    assert (T0 // 4, T1 // 4, T2 // 8) in live
+    assert n_rep > 0
