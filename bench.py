@@ -589,8 +589,24 @@ def main():
                     times.append((time.perf_counter() - t0) * 1e3)
             return reduce_max(max(times), dist, "cuda")
 
-        def entry(ms, h2d, what):
-            return {"value": world * n * C / (ms / 1e3), "ms_per_step": ms, "h2d_bytes_per_step": h2d, "what": what}
+        def entry(ms, h2d, what, host):
+            return {"value": world * n * C / (ms / 1e3), "ms_per_step": ms, "h2d_bytes_per_step": h2d, "what": what,
+                    "host_buffer_h2d_gbs": buffer_rate(host)}
+
+        def buffer_rate(host):
+            # the plain copy rate of this pinned buffer (its first GiB, twice),
+            # so that a slow e2e step can be told from a slow host buffer
+            m = min(host.numel(), 1 << 27)
+            dev = torch.empty(m, dtype=torch.int64, device="cuda")
+            best = 0.0
+            for _ in range(2):
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                dev.copy_(host[:m], non_blocking=True)
+                torch.cuda.synchronize()
+                best = max(best, m * 8 / (time.perf_counter() - t0) / 1e9)
+            del dev
+            return best
 
         read_what = " + lcs_bound_iterate(C) + lcs_bound_read"
         try:
@@ -602,18 +618,18 @@ def main():
             start_orb = hnd.export_orbit_fx(0, out=torch.empty(n_orb, dtype=torch.int64, pin_memory=True))
             forms["orbit_form"] = entry(e2e_run(lambda: hnd.set_start_orbit_fx([start_orb] * d)), d * n_orb * 8,
                                         "lcs_bound_set_start_orbit_fx from pinned host (d vectors in orbit form)"
-                                        + read_what)
+                                        + read_what, start_orb)
             del start_orb
         n_st = hnd.n_stored
         start_st = hnd.export_stored_fx(0, out=torch.empty(n_st, dtype=torch.int64, pin_memory=True))
         forms["stored_form"] = entry(e2e_run(lambda: hnd.set_start_stored_fx([start_st] * d)), d * n_st * 8,
                                      "lcs_bound_set_start_stored_fx from pinned host (d vectors in stored form)"
-                                     + read_what)
+                                     + read_what, start_st)
         del start_st
         start = hnd.export_fx(0, out=torch.empty(n, dtype=torch.int64, pin_memory=True))
         forms["full_vectors"] = entry(e2e_run(lambda: hnd.set_start_fx([start] * d)), d * n * 8,
                                       "lcs_bound_set_start_fx from pinned host (every state, symmetry verified on "
-                                      "the device)" + read_what)
+                                      "the device)" + read_what, start)
         del start
         head = "orbit_form" if n_orb else "stored_form"
         e2e = {"unit": "state-updates/s", "d2h_bytes_per_step": 80, **forms.pop(head), "form": head, **forms}
