@@ -594,19 +594,23 @@ def main():
                     "host_buffer_h2d_gbs": buffer_rate(host)}
 
         def buffer_rate(host):
-            # the plain copy rate of this pinned buffer (its first GiB, twice),
-            # so that a slow e2e step can be told from a slow host buffer
-            m = min(host.numel(), 1 << 27)
+            # the plain copy rate of this pinned buffer, 1 GiB segment by
+            # segment (min and median over the whole buffer), so that a slow
+            # e2e step can be told from a slow host buffer
+            m = 1 << 27
             dev = torch.empty(m, dtype=torch.int64, device="cuda")
-            best = 0.0
-            for _ in range(2):
-                torch.cuda.synchronize()
-                t0 = time.perf_counter()
-                dev.copy_(host[:m], non_blocking=True)
-                torch.cuda.synchronize()
-                best = max(best, m * 8 / (time.perf_counter() - t0) / 1e9)
+            rates = []
+            for a in range(0, host.numel() - m + 1, m):  # whole segments; each the better of two copies
+                best = 0.0
+                for _ in range(2):
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    dev.copy_(host[a:a + m], non_blocking=True)
+                    torch.cuda.synchronize()
+                    best = max(best, m * 8 / (time.perf_counter() - t0) / 1e9)
+                rates.append(best)
             del dev
-            return best
+            return {"min": min(rates), "median": statistics.median(rates), "segments": len(rates)}
 
         read_what = " + lcs_bound_iterate(C) + lcs_bound_read"
         try:
