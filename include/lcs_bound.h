@@ -427,8 +427,9 @@ lcs_status lcs_fp32_experiment(int sigma, int d, int h, int64_t n_iters, double 
  * steps older than the one being computed (the k-th argument v_k of F).
  * All vectors are device pointers of sigma^(d h) fixed-point int64 values in
  * state-index order (no symmetry).  v_out must not alias any input.
- * f_mode and frac_bits as in lcs_bound_opts.  stream: cudaStream_t or NULL
- * (legacy default stream).  Asynchronous; no allocation. */
+ * f_mode and frac_bits as in lcs_bound_opts.  Shapes as lcs_bound_create
+ * (the general kernels serve those without a specialised one).  stream:
+ * cudaStream_t or NULL (legacy default stream).  Asynchronous; no allocation. */
 lcs_status lcs_sweep_fx(int sigma, int d, int h, int f_mode, int frac_bits, const int64_t* const* v_prev, int64_t* v_out,
                         void* stream);
 
@@ -446,6 +447,8 @@ lcs_status lcs_sweep_fx(int sigma, int d, int h, int f_mode, int frac_bits, cons
  * r_mode = 1) and *argmin_out = the smallest state index attaining it.
  * R_out and argmin_out are device pointers owned by the caller.  frac_bits as
  * in lcs_bound_opts (0 -> 44).  stream: cudaStream_t or NULL.  Asynchronous.
+ * The shapes with a specialised kernel only (see lcs_bound_create); others
+ * return LCS_EUNSUPPORTED.
  *
  * Scratch: the per-CTA partials of the reduction live in a fixed 64 KiB
  * array inside the library (4096 partials), reserved on every device that
