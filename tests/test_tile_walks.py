@@ -13,8 +13,12 @@ kernels accept.
   ((J2 + 37 row) mod 2^(L-3)) and the live test I1 < 2^(L-2), 4 I0 + 8 I2 <=
   2^L - 1 visits each tile of the 4 x 4 x 8 grid that passes the corner test
   (I0 <= I1, I1 / 2 <= I2, 4 I0 + 8 I2 <= 2^L - 1) exactly once, and every
-  orbit representative lies in one of those tiles.
+  orbit representative lies in one of those tiles.  Its 32-bit indices stay
+  inside the stored half for every h up to the kernel's limit.
 """
+import pathlib
+import re
+
 import numpy as np
 import pytest
 
@@ -122,3 +126,52 @@ def test_d3s_every_representative_lies_in_a_live_tile(L):
                     n_rep += 1
                     assert (T0 // 4, T1 // 4, T2 // 8) in live
     assert n_rep > 0
+
+
+
+def _spread3(x):
+    """bit i of x (i < 10, as spread3_32 keeps) moved to bit 3i"""
+    assert 0 <= x < 1 << 10
+    y = 0
+    for i in range(10):
+        y |= ((x >> i) & 1) << (3 * i)
+    return y
+
+
+def _tail32(sa, sb, sc):
+    return (sa << 2) | (sb << 1) | sc
+
+
+def _d3s_max_h():
+    src = (pathlib.Path(__file__).resolve().parents[1] / "paper_2407_10925_gb300" / "csrc" / "sweep_d3s.cuh").read_text()
+    return int(re.search(r"kD3sMaxH\s*=\s*(\d+)", src).group(1))
+
+
+def test_d3s_sweep_indices_stay_in_the_stored_half():
+    """The d = 3 sweep (sweep_d3s.cuh) forms its indices in 32 bits.  Each index
+    it reads or writes, up to the last value of a two- or four-value load, lies
+    in the stored half (2^(3h-1) = 4 nt states), and that half has at most 2^32
+    states for every h up to the kernel's limit.  Spreads and tails are
+    monotone in each argument, so the largest index comes from the largest
+    components: T0 <= 2^(L-1) - 1 (T0 + T2 <= 2^L - 1 with T0 <= T2), T1 and T2
+    up to 2^L - 1, and a complement side's spread at most spread(2^L - 1)."""
+    h_max = _d3s_max_h()
+    for h in range(4, h_max + 1):
+        L = h - 1
+        M = (1 << L) - 1
+        S_any = _spread3(M)
+        S_T0 = _spread3((1 << (L - 1)) - 1)
+        nt = 1 << (3 * L)
+        top = 1 << (3 * L + 1)
+        last = {
+            "pair sum, one string advanced": _tail32(S_any, S_any, S_any << 3) + 1,
+            "quad sum, two strings advanced": _tail32(S_any, S_any << 3, S_any << 3) + 2 + 1,
+            "pair sum at string 1 head 1": (_tail32(S_any, S_any, S_any << 3) | top) + 1,
+            "block of eight, both sides": (_tail32(S_T0, S_any, S_any) << 3) + 4 + 2 + 1,
+            "output at head 011": 3 * nt + _tail32(S_any, S_any, S_any),
+        }
+        for name, x in last.items():
+            assert x < 4 * nt, (h, name, x)
+        assert 4 * nt == 2 ** (3 * h - 1) <= 2 ** 32
+        assert top < 2 ** 32 and 1 << (max(L - 3, 1) + 2 * L - 5) < 2 ** 32  # the head bit and the tile count
+    assert 2 ** (3 * (h_max + 1) - 1) > 2 ** 32  # the limit is tight
