@@ -1,9 +1,15 @@
-"""The tile walks of two symmetric sweeps, restated from their kernels with
+"""The tile walks of the three symmetric sweeps, restated from their kernels with
 plain integer (and float32) arithmetic and checked against brute-force
 enumerations.  The GPU parity tests check the kernels' outputs; these check
 that the walks visit every live tile exactly once, for every size the
 kernels accept.
 
+* sigma = d = 2 (sweep_s2d2.cuh): tile k = (s, A, B) of 16 x 16 (a, beta)
+  pairs, thread index = Morton code of (a, beta) low bits, a thread live iff
+  a <= beta; the live threads own each orbit representative once, tiles
+  below the diagonal (skipped whole) hold none, the eight stored states of
+  the orbits partition the stored half, and a warp's 32 tails t = (a, b)
+  form one aligned run of 32 tail indices.
 * d = 2, sigma = 3, 4, 5 (sweep_d2s.cuh): tile (TA, TB) holds a pair (some
   A <= B) iff TB >= RHO TA, RHO = sigma^(KA - KB); live tile j maps back to
   its row through the root of P(TA) = TA nTB - RHO TA (TA - 1) / 2, estimated
@@ -21,6 +27,49 @@ import re
 
 import numpy as np
 import pytest
+
+
+def _spread2(x):
+    """bit i of each entry of x moved to bit 2i (x < 2^16)"""
+    y = np.zeros_like(x)
+    for i in range(16):
+        y |= ((x >> i) & 1) << (2 * i)
+    return y
+
+
+@pytest.mark.parametrize("h", [6, 7, 8, 9, 10, 11])
+def test_s2d2_orbit_walk(h):
+    L = h - 1
+    M = (1 << L) - 1
+    tn = (1 << (L - 1)) // 16
+    nt = 1 << (2 * L)
+    k = np.arange(2 * tn * tn, dtype=np.int64)[:, None]
+    tid = np.arange(256, dtype=np.int64)[None, :]
+    s, rem = k // (tn * tn), k % (tn * tn)
+    A, B = rem // tn, rem % tn
+    ia = sum(((tid >> (2 * i + 1)) & 1) << i for i in range(4))
+    ib = sum(((tid >> (2 * i)) & 1) << i for i in range(4))
+    a, beta = A * 16 + ia, B * 16 + ib
+    live = np.broadcast_to(a <= beta, (k.size, 256))
+    assert not live[(A > B)[:, 0]].any()  # the skipped tiles hold no representative
+    s, a, beta = (np.broadcast_to(x, live.shape)[live] for x in (s, a, beta))
+    K = 1 << (h - 2)
+    reps = set(zip(s.tolist(), a.tolist(), beta.tolist()))
+    assert len(reps) == s.size == K * (K + 1)
+    assert reps == {(ss, aa, bb) for ss in (0, 1) for bb in range(K) for aa in range(bb + 1)}
+    b = np.where(s == 1, M - beta, beta)
+    Ea, Eb = _spread2(a), _spread2(b)
+    t, sw = (Ea << 1) | Eb, (Eb << 1) | Ea
+    tails = np.stack([t, nt - 1 - t, nt - 1 - sw, sw])  # t, ~t, t', ~t'
+    states = [set(np.concatenate([tails[:, j], nt + tails[:, j]]).tolist()) for j in range(t.size)]
+    assert sum(len(x) for x in states) == 2 * nt  # orbits are disjoint ...
+    assert set().union(*states) == set(range(2 * nt))  # ... and cover the stored half
+    # every warp of every tile: its tails t, live or not, are one aligned run of 32
+    Ea_all, Eb_all = _spread2(A * 16 + ia), _spread2(np.where(k // (tn * tn) == 1, M - (B * 16 + ib), B * 16 + ib))
+    t_all = ((Ea_all << 1) | Eb_all).reshape(k.size, 8, 32)
+    assert (np.sort(t_all, axis=2) == (t_all.min(axis=2, keepdims=True) + np.arange(32))).all()
+    assert (t_all.min(axis=2) % 32 == 0).all()
+
 
 D2S_GEO = {3: (3, 2), 4: (2, 2), 5: (2, 1)}  # sigma: (KA, KB)
 
