@@ -95,3 +95,22 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.lcs_bound_export_orbit_fx(None, 0, None, 0) == binding.LCS_EINVAL
     assert L.lcs_bound_read(None, None, None, None, None, None) == binding.LCS_EINVAL
     L.lcs_bound_destroy(None)
+
+
+def test_missing_library_fails_loudly(monkeypatch):
+    """Without the CUDA library (not built and nvcc absent) every entry point
+    raises: the binding has no CPU path to fall back to."""
+    from paper_2407_10925_gb300 import binding
+
+    def no_nvcc():
+        raise RuntimeError("nvcc not found: the CUDA library cannot be built")
+
+    monkeypatch.setattr(binding, "_lib", None)
+    monkeypatch.setattr(binding._build, "up_to_date", lambda: False)
+    monkeypatch.setattr(binding._build, "_nvcc", no_nvcc)
+    with pytest.raises(RuntimeError, match="nvcc not found"):
+        binding.lib()
+    with pytest.raises(RuntimeError, match="nvcc not found"):
+        binding.LcsBound(2, 2, 8)
+    with pytest.raises(RuntimeError, match="nvcc not found"):
+        binding.lcs_bound_default_opts()
