@@ -1,0 +1,102 @@
+"""Host logic of bench.py that needs no GPU: the clock-sample summary, the
+measured-peak lookup, and the traffic figures keyed by the kernel sources.
+"""
+import hashlib
+import json
+import os
+import sys
+
+import pytest
+
+from conftest import ROOT
+
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_clock_summary_median_max_and_reasons(tmp_path):
+    cs = bench.ClockSampler(0)
+    cs.path = str(tmp_path / "clocks.csv")
+    cs.proc = object()  # as if nvidia-smi had run
+    rows = [
+        "0, 1965, 2070, 900.1, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "0, 1980, 2070, 1010.0, 0x4, Not Active, Not Active, Not Active, Active",
+        "0, 1950, 2070, 980.0, 0x0, Not Active, Not Active, Not Active, Not Active",
+        "garbage line",
+        "0, [N/A], 2070, 0, 0x0, Not Active, Not Active, Not Active, Not Active",
+    ]
+    (tmp_path / "clocks.csv").write_text("\n".join(rows) + "\n")
+    s = cs.summary()
+    assert s["sm_mhz"] == 1965 and s["sm_max_mhz"] == 2070 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+
+
+def test_clock_summary_flags_thermal_slowdown(tmp_path):
+    cs = bench.ClockSampler(0)
+    cs.path = str(tmp_path / "clocks.csv")
+    cs.proc = object()
+    (tmp_path / "clocks.csv").write_text("0, 1500, 2070, 1300, 0x20, Not Active, Active, Not Active, Not Active\n")
+    assert cs.summary()["reasons"] == ["hw_thermal_slowdown"]
+
+
+def test_clock_summary_without_nvidia_smi():
+    cs = bench.ClockSampler(0)
+    assert cs.summary() == {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+
+
+def test_measured_peak_and_fallback(tmp_path, monkeypatch):
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.measured_peaks() == (bench.FALLBACK_HBM_GBS, "fallback")
+    (tmp_path / "MEASURED_PEAKS.json").write_text(json.dumps({"hbm_gbs": 6782.1, "bf16_tflops": 1900.0}))
+    assert bench.measured_peaks() == (6782.1, "measured")
+
+
+def _hash(csrc, files):
+    """sha256 over each file's name and bytes, in the listed order, first 16 hex digits"""
+    h = hashlib.sha256()
+    for name in files:
+        h.update(name.encode())
+        h.update((csrc / name).read_bytes())
+    return h.hexdigest()[:16]
+
+
+def test_traffic_is_dropped_once_the_kernel_changes(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_2407_10925_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    (tmp_path / "profiles").mkdir()
+    (csrc / "k.cuh").write_text("// kernel\n")
+    (csrc / "k.cu").write_text("#include \"k.cuh\"\n")
+    files = ["k.cuh", "k.cu"]
+    entry = {"source_files": files, "source_hash": _hash(csrc, files), "dram_bytes_per_launch": 1234}
+    (tmp_path / "profiles" / "traffic.json").write_text(json.dumps({"sweep": {"h16": entry}}))
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    assert bench.profiled_traffic("h16", "sweep") == 1234
+    assert bench.profiled_traffic("h17", "sweep") is None  # no capture for that workload
+    (csrc / "k.cuh").write_text("// kernel, changed\n")
+    assert bench.profiled_traffic("h16", "sweep") is None
+
+
+def _stored_states(cfg_name):
+    c = bench.CONFIGS[cfg_name]
+    n = c["sigma"] ** (c["d"] * c["h"])
+    return n // 2 if c["sigma"] == 2 else n  # complement-half storage for sigma = 2
+
+
+def test_committed_traffic_entries_are_consistent():
+    """Each committed figure is its bytes per stored state times the stored
+    states of its workload (the capture's bytes per state do not depend on h)."""
+    with open(os.path.join(ROOT, "profiles", "traffic.json")) as f:
+        j = json.load(f)
+    n = 0
+    for kernel, per_cfg in j.items():
+        if kernel.startswith("_"):
+            continue
+        for cfg_name, e in per_cfg.items():
+            n += 1
+            assert cfg_name in bench.CONFIGS and e["captured_config"] in bench.CONFIGS
+            want = e["dram_bytes_per_stored_state"] * _stored_states(cfg_name)
+            assert e["dram_bytes_per_launch"] == pytest.approx(want, rel=1e-4), (kernel, cfg_name)
+            for name in e["source_files"]:
+                assert os.path.exists(os.path.join(ROOT, "paper_2407_10925_gb300", "csrc", name))
+            assert os.path.exists(os.path.join(ROOT, e["summary"]))
+    assert n >= 1
