@@ -362,7 +362,11 @@ int orc_F_fx(int sigma, int d, int h, int f_mode, int frac_bits, const int64_t* 
 
 static uint64_t splitmix64_at(uint64_t seed, uint64_t i) {
   uint64_t z = seed + (i + 1) * 0x9e3779b97f4a7c15ull;
+#if ORC_MUTANT == 11
+  z = (z ^ (z >> 29)) * 0xbf58476d1ce4e5b9ull;
+#else
   z = (z ^ (z >> 30)) * 0xbf58476d1ce4e5b9ull;
+#endif
   z = (z ^ (z >> 27)) * 0x94d049bb133111ebull;
   return z ^ (z >> 31);
 }
@@ -381,7 +385,9 @@ static uint64_t canonical_index(const shape_t* s, uint64_t y, int symmetric) {
     uint64_t w = ((y >> 1) & 0x5555555555555555ull) | ((y & 0x5555555555555555ull) << 1);
     uint64_t wc = s->n - 1 - w;
     if (w < best) best = w;
+#if ORC_MUTANT != 10
     if (wc < best) best = wc;
+#endif
   }
   if (symmetric == 3) {
     /* string j's letter at position p sits at bit 3 (h-1-p) + 2 - j */
@@ -393,7 +399,9 @@ static uint64_t canonical_index(const shape_t* s, uint64_t y, int symmetric) {
           w |= ((y >> (3 * i + 2 - order[q][j])) & 1ull) << (3 * i + 2 - j);
       uint64_t wc = s->n - 1 - w;
       if (w < best) best = w;
+#if ORC_MUTANT != 9
       if (wc < best) best = wc;
+#endif
     }
   }
   return best;

@@ -78,3 +78,14 @@ def test_generated_symmetric_modes_need_their_shapes(orc):
         orc.F_generated(2, 3, 2, SEEDS[:3], BASES[:3], SPREAD, xs, symmetric=2)
     with pytest.raises(Exception):
         orc.F_generated(3, 2, 2, SEEDS[:2], BASES[:2], SPREAD, xs, symmetric=1)
+
+
+def test_splitmix64_matches_its_published_outputs(orc):
+    """The generator both sides implement from its definition, against the
+    first outputs of the published SplitMix64 from state 0."""
+    from conftest import load_golden
+
+    rows = load_golden("splitmix64_seed0.txt")
+    assert len(rows) >= 4
+    for seed, i, out in rows:
+        assert orc.splitmix64_at(int(seed), int(i)) == int(out, 16)

@@ -71,3 +71,39 @@ def test_mutant_is_caught(orc, mutant):
     with orc.use_mutant(mutant):
         failures = _pins_hold(orc)
     assert failures, f"mutant {mutant} ({MUTANTS[mutant]}) passed every pin"
+
+
+# mistakes in the generated arguments of the full-size GPU parity tests
+GENERATED_MUTANTS = {
+    9: "the d = 3 canonical index misses the complements of the permuted states",
+    10: "the sigma = d = 2 canonical index misses the swapped complement",
+    11: "SplitMix64 with a wrong finaliser shift",
+}
+
+
+def _generated_pins_hold(orc):
+    import test_oracle_generated as gen
+
+    failures = []
+    for seed, i, out in load_golden("splitmix64_seed0.txt"):
+        if orc.splitmix64_at(int(seed), int(i)) != int(out, 16):
+            failures.append("SplitMix64 published outputs")
+            break
+    for s, d, h, sym in [(2, 2, 3, 2), (2, 3, 2, 3)]:
+        vs, _ = gen._explicit(orc, s, d, h, sym)
+        xs = np.arange(s ** (d * h), dtype=np.uint64)
+        got = orc.F_generated(s, d, h, gen.SEEDS[:d], gen.BASES[:d], gen.SPREAD, xs, symmetric=sym)
+        if not np.array_equal(got, orc.F(s, d, h, vs, arith="fx")):
+            failures.append(f"generated arguments {s, d, h, sym}")
+    return failures
+
+
+def test_unmutated_generator_passes(orc):
+    assert _generated_pins_hold(orc) == []
+
+
+@pytest.mark.parametrize("mutant", sorted(GENERATED_MUTANTS), ids=lambda m: GENERATED_MUTANTS[m])
+def test_generated_input_mutant_is_caught(orc, mutant):
+    with orc.use_mutant(mutant):
+        failures = _generated_pins_hold(orc)
+    assert failures, f"mutant {mutant} ({GENERATED_MUTANTS[mutant]}) passed every pin"
