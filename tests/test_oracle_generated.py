@@ -89,3 +89,23 @@ def test_splitmix64_matches_its_published_outputs(orc):
     assert len(rows) >= 4
     for seed, i, out in rows:
         assert orc.splitmix64_at(int(seed), int(i)) == int(out, 16)
+
+
+def test_gpu_side_generators_match_the_published_outputs():
+    """The torch restatements the full-size GPU tests fill their vectors with,
+    run on CPU tensors, give the published outputs' low 46 bits (the spread
+    those tests take)."""
+    import torch
+
+    from conftest import load_golden
+    import test_gpu_d3_fullsize as g3
+    import test_gpu_fullsize as g2
+
+    rows = [(int(s), int(i), int(o, 16)) for s, i, o in load_golden("splitmix64_seed0.txt")]
+    assert {s for s, _, _ in rows} == {0}
+    want = [o & ((1 << g2.SPREAD_BITS) - 1) for _, _, o in rows]
+    out = torch.empty(len(rows), dtype=torch.int64)
+    g2.splitmix_fill(torch, out, 0, 0, 0, 0)
+    assert out.tolist() == want
+    assert g3.SPREAD_BITS == g2.SPREAD_BITS
+    assert g3.splitmix(torch, torch.arange(len(rows), dtype=torch.int64), 0, 0).tolist() == want
