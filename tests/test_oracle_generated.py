@@ -109,3 +109,28 @@ def test_gpu_side_generators_match_the_published_outputs():
     assert out.tolist() == want
     assert g3.SPREAD_BITS == g2.SPREAD_BITS
     assert g3.splitmix(torch, torch.arange(len(rows), dtype=torch.int64), 0, 0).tolist() == want
+
+
+def test_gpu_side_canonical_maps_match_the_orbits(orc):
+    """The full-size GPU tests' canonical members, on CPU tensors at their own
+    sizes (sampled states), against the orbits enumerated with plain digit
+    arithmetic: sigma = 2, d = 3, h = 11 under the string orders and the
+    complement; sigma = d = 2, h = 16 under the swap and the complement
+    (through the generated values, which read the canonical member)."""
+    import torch
+
+    import test_gpu_d3_fullsize as g3
+    import test_gpu_fullsize as g2
+
+    rng = np.random.default_rng(2407)
+    ys = [0, 1, 2, 7, g3.N // 2 - 1, g3.N // 2, g3.N - 1] + [int(v) for v in rng.integers(0, g3.N, 300)]
+    got = g3.canonical(torch, torch.tensor(ys, dtype=torch.int64)).tolist()
+    assert got == [min(_images(2, 3, g3.H, y, 3)) for y in ys]
+
+    mask = (1 << g2.SPREAD_BITS) - 1
+    ys = [0, 5, g2.N // 2, g2.N - 1] + [int(v) for v in rng.integers(0, g2.N, 100)]
+    for y in ys:
+        out = torch.empty(1, dtype=torch.int64)
+        g2.splitmix_fill(torch, out, g2.SEEDS[0], 0, y, 2)
+        c = min(_images(2, 2, g2.H, y, 2))
+        assert out.item() == orc.splitmix64_at(g2.SEEDS[0], c) & mask, y
