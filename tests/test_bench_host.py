@@ -1,5 +1,6 @@
 """Host logic of bench.py that needs no GPU: the clock-sample summary, the
-measured-peak lookup, and the traffic figures keyed by the kernel sources.
+measured-peak lookup, the traffic figures keyed by the kernel sources, and the
+reference arm's JSON line.
 """
 import hashlib
 import json
@@ -100,3 +101,30 @@ def test_committed_traffic_entries_are_consistent():
                 assert os.path.exists(os.path.join(ROOT, "paper_2407_10925_gb300", "csrc", name))
             assert os.path.exists(os.path.join(ROOT, e["summary"]))
     assert n >= 1
+
+
+def test_reference_arm_prints_one_contract_line():
+    """`bench.py --impl reference` (the oracle on the host cores, no GPU): one
+    JSON line with the contract's keys, its value repeated in cpu_baseline and
+    e2e, and ms_per_step consistent with the value and the workload."""
+    import subprocess
+
+    env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                        "--warmup", "0"], capture_output=True, text=True, timeout=600, env=env)
+    assert r.returncode == 0, r.stderr
+    lines = [ln for ln in r.stdout.splitlines() if ln.strip()]
+    assert len(lines) == 1
+    j = json.loads(lines[0])
+    for key in ("impl", "metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better",
+                "scaling", "vs_baseline", "dtype", "data", "config", "cpu_baseline", "e2e"):
+        assert key in j, key
+    assert j["impl"] == "reference" and j["metric"] == bench.METRIC and j["unit"] == bench.METRIC
+    assert j["higher_is_better"] is True and j["n_gpus"] == 1 and j["steps"] == 1 and j["warmup"] == 0
+    assert j["value"] > 0 and j["cpu_baseline"]["value"] == j["value"] and j["e2e"]["value"] == j["value"]
+    assert j["cpu_baseline"]["kind"] == "oracle" and j["cpu_baseline"]["cores"] >= 1 and j["cpu_baseline"]["sample"]
+    assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["e2e"]["d2h_bytes_per_step"] == 0
+    cfg = j["config"]
+    assert cfg["states"] == 2 ** 32 and "workload" in cfg
+    want_ms = cfg["states"] * cfg["sweeps_per_step"] / j["value"] * 1e3
+    assert j["ms_per_step"] == pytest.approx(want_ms, rel=1e-6)
