@@ -13,7 +13,9 @@ kernels accept.
 * d = 2, sigma = 3, 4, 5 (sweep_d2s.cuh): tile (TA, TB) holds a pair (some
   A <= B) iff TB >= RHO TA, RHO = sigma^(KA - KB); live tile j maps back to
   its row through the root of P(TA) = TA nTB - RHO TA (TA - 1) / 2, estimated
-  in float32 and corrected exactly.
+  in float32 and corrected exactly.  Its threads own every pair A <= B once,
+  and the pairs' reads and writes, checked against the state index,
+  partition v_{t-1} and the output.
 * sigma = 2, d = 3 (sweep_d3s.cuh): the sheared box J0 < 2^max(L-3,1),
   J1 < 2^(L-2), J2 < 2^(L-3) with I0 = J0, I1 = J0 + J1, I2 = I1 / 2 +
   ((J2 + 37 row) mod 2^(L-3)) and the live test I1 < 2^(L-2), 4 I0 + 8 I2 <=
@@ -125,6 +127,89 @@ def test_d2s_live_tile_inverse_at_the_largest_sizes(s, L):
         TA, TB = d2s_live_tile(s, L, j)
         P = TA * nTB - rho * (TA * (TA - 1) // 2)
         assert 0 <= TA < nTA and rho * TA <= TB < nTB and P <= j < P + (nTB - rho * TA)
+
+
+
+def _d2s_pair(s, L, j, r):
+    """(A, B) of thread r of live tile j (d2s_pair): the thread index's base-s
+    digits are A0, B0, A1, B1, ... with A's surplus digits last."""
+    KA, KB = D2S_GEO[s]
+    TA, TB = d2s_live_tile(s, L, j)
+    ia = ib = 0
+    wa = wb = 1
+    for i in range(KA + KB):
+        dgt = r % s
+        r //= s
+        if i % 2 == 0 or i // 2 >= KB:
+            ia += dgt * wa
+            wa *= s
+        else:
+            ib += dgt * wb
+            wb *= s
+    return TA * s ** KA + ia, TB * s ** KB + ib
+
+
+def _spread_s2(x, s, L):
+    """base-s digits of x moved to base s^2 positions (d2s_spread)"""
+    return sum(((x // s ** i) % s) * s ** (2 * i) for i in range(L))
+
+
+def _d2_index(s, h, s0, s1):
+    """the header's state index of the strings s0, s1 (letter lists, head first)"""
+    return sum(s0[p] * s ** (2 * (h - 1 - p) + 1) + s1[p] * s ** (2 * (h - 1 - p)) for p in range(h))
+
+
+def _letters(x, s, L):
+    return [(x // s ** (L - 1 - p)) % s for p in range(L)]
+
+
+@pytest.mark.parametrize("s,L", [(3, 3), (3, 4), (4, 2), (4, 3), (5, 2), (5, 3)])
+def test_d2s_pairs_and_addresses(s, L):
+    """The d = 2 swap-aware sweep's pairs and addresses (sweep_d2s.cuh) against
+    the state index: every pair A <= B owned once; the reads of P(t, g) and
+    P(ts, g) partition v_{t-1} (each value read once), and each is the state
+    (g a, b c) of its definition; the block of v_{t-2} is the four-letter
+    advance of t; the outputs partition the states; inside a tile the P
+    addresses of consecutive threads are s apart (a warp reads one run)."""
+    KA, KB = D2S_GEO[s]
+    h = L + 1
+    nt = s ** (2 * L)
+    N = s ** (2 * h)
+    nTA, nTB, rho = s ** (L - KA), s ** (L - KB), s ** (KA - KB)
+    n_live = nTA * nTB - rho * (nTA * (nTA - 1) // 2)
+    T = s ** (KA + KB)
+    pairs, reads1, reads2, writes = [], [], [], []
+    for j in range(n_live):
+        bases = []
+        for r in range(T):
+            A, B = _d2s_pair(s, L, j, r)
+            eA, eB = _spread_s2(A, s, L), _spread_s2(B, s, L)
+            bases.append(eA * s + eB * s * s)
+            if A > B:
+                continue
+            pairs.append((A, B))
+            t, ts = eA * s + eB, eB * s + eA
+            a, b = _letters(A, s, L), _letters(B, s, L)
+            sides = [(eA, eB, a, b)] if t == ts else [(eA, eB, a, b), (eB, eA, b, a)]
+            for ex, ey, x, y in sides:
+                for g in range(s):
+                    for c in range(s):
+                        addr = g * nt * s + ex * s + ey * s * s + c
+                        assert addr == _d2_index(s, h, [g] + x, y + [c])
+                        reads1.append(addr)
+            for c in range(s * s):
+                addr = t * s * s + c
+                assert addr == _d2_index(s, h, a + [c // s], b + [c % s])
+                reads2.append(addr)
+            for H in range(s * s):
+                writes.append(H * nt + t)
+                if t != ts:
+                    writes.append(H * nt + ts)
+        assert all(bases[r] - bases[0] == s * r for r in range(T))
+    assert sorted(pairs) == [(A, B) for A in range(s ** L) for B in range(A, s ** L)]
+    assert sorted(reads1) == list(range(N))
+    assert len(set(reads2)) == len(reads2) == len(pairs) * s * s
+    assert sorted(writes) == list(range(N))
 
 
 def d3s_live_tiles_bruteforce(L):
