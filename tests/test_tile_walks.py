@@ -73,6 +73,68 @@ def test_s2d2_orbit_walk(h):
     assert (t_all.min(axis=2) % 32 == 0).all()
 
 
+
+@pytest.mark.parametrize("h", [6, 8, 10])
+def test_s2d2_reads(h):
+    """The sigma = d = 2 sweep's reads (s2d2_orbit, s2d2_sweep_orbit): pair
+    yb + c (c = 0, 1) of v_{t-1} is the state (0 x_a, x_b c) of its tail x =
+    t, ~t, t', ~t' (the heads-01 state with string 1 advanced); the pairs cover
+    the stored half (x < N/2), the diagonal orbits reading theirs twice.
+    The quad 4 t + c of v_{t-2} (both strings advanced from heads 00) is read
+    once per orbit, inside the stored half.  Counting all 32 threads (in a
+    diagonal tile some own no orbit and skip their reads), every stream of a
+    warp fills whole aligned runs of 32 values."""
+    L = h - 1
+    M = (1 << L) - 1
+    tn = (1 << (L - 1)) // 16
+    nt = 1 << (2 * L)
+    k = np.arange(2 * tn * tn, dtype=np.int64)[:, None]
+    tid = np.arange(256, dtype=np.int64)[None, :]
+    s_, rem = k // (tn * tn), k % (tn * tn)
+    A, B = rem // tn, rem % tn
+    ia = sum(((tid >> (2 * i + 1)) & 1) << i for i in range(4))
+    ib = sum(((tid >> (2 * i)) & 1) << i for i in range(4))
+    a = A * 16 + ia
+    beta = B * 16 + ib
+    b = np.where(s_ == 1, M - beta, beta)
+    a, b = np.broadcast_to(a, (k.size, 256)), np.broadcast_to(b, (k.size, 256))
+    live = np.broadcast_to(A * 16 + ia <= B * 16 + ib, (k.size, 256))
+    Ea, Eb = _spread2(a), _spread2(b)
+    maskE = _spread2(np.int64(M))
+    Eac, Ebc = maskE - Ea, maskE - Eb
+    yb = [(Ea << 1) | (Eb << 2), (Eac << 1) | (Ebc << 2), (Ebc << 1) | (Eac << 2), (Eb << 1) | (Ea << 2)]
+    t = (Ea << 1) | Eb
+
+    def index(s0, s1):  # two letter lists, head first
+        return sum(s0[p] * 2 ** (2 * (h - 1 - p) + 1) + s1[p] * 2 ** (2 * (h - 1 - p)) for p in range(h))
+
+    def bits(x):
+        return [(x >> (L - 1 - p)) & 1 for p in range(L)]
+
+    rng = np.random.default_rng(h)
+    rows, cols = np.nonzero(live)
+    for q in rng.choice(rows.size, 64, replace=False):
+        r, c_ = rows[q], cols[q]
+        ta, tb = int(a[r, c_]), int(b[r, c_])
+        for y, (x0, x1) in zip(yb, [(ta, tb), (M - ta, M - tb), (M - tb, M - ta), (tb, ta)]):
+            for c in (0, 1):
+                assert int(y[r, c_]) + c == index([0] + bits(x0), bits(x1) + [c])
+        for c in range(4):
+            assert 4 * int(t[r, c_]) + c == index(bits(ta) + [c >> 1], bits(tb) + [c & 1])
+
+    reads1 = np.concatenate([y[live] for y in yb])
+    reads1 = np.concatenate([reads1, reads1 + 1])
+    assert np.array_equal(np.unique(reads1), np.arange(2 * nt))
+    quads = t[live]
+    assert np.unique(quads).size == quads.size and (4 * quads + 3 < 2 * nt).all()
+    # warps: every aligned run of 32 values a stream touches is touched whole
+    for stream in [np.stack([y, y + 1], -1) for y in yb] + [4 * t[..., None] + np.arange(4)]:
+        w = stream.reshape(k.size, 8, -1)
+        for row in w.reshape(-1, w.shape[-1])[:: max(1, w.shape[0] * 8 // 512)]:
+            vals = np.unique(row)
+            assert vals.size % 32 == 0 and np.array_equal(np.unique(vals // 32).size * 32, vals.size)
+
+
 D2S_GEO = {3: (3, 2), 4: (2, 2), 5: (2, 1)}  # sigma: (KA, KB)
 
 
