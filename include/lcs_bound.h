@@ -72,8 +72,8 @@ typedef struct {
    * k > 0: check every k-th iteration (counted from creation) and at the last
    * iteration of each call.  1 is Algorithm 2 as printed. */
   int check_every;
-  /* 0: R = minimum increment (default).  1: R = maximum increment (the line of
-   * Algorithm 2 as printed).  E is evaluated for whichever R is taken. */
+  /* 0: R = minimum increment (default).  1: R = maximum increment (Algorithm
+   * 2 as printed).  E is evaluated for whichever R is taken. */
   int r_mode;
   /* 0: F as in the paper (max over z of F_z).  1: the max runs over every
    * non-empty set of advanced strings, and for equal heads the full set carries

@@ -33,10 +33,10 @@
  *   R2  F_z with N empty (all heads equal z) is not a candidate of the max.
  *       Letters z with the same N_z give the same F_z; each N is evaluated once.
  *   R3  b is added once, outside the max.
- *   R4  R is the minimum increment by default (the text's "maximum r with
- *       v_{n+1} - v_n >= r 1"); r_mode = 1 takes the maximum, as Algorithm 2's
- *       line for R is printed.  Both give feasible triplets because E is
- *       evaluated for whichever R is taken.
+ *   R4  R is the minimum increment by default: the text defines r as the
+ *       largest value that every entry of the increment reaches.  r_mode = 1
+ *       takes the maximum, the reading of Algorithm 2 as printed.  Both give
+ *       feasible triplets because E is evaluated for whichever R is taken.
  *   R5  Summation order (f64 arithmetic): one flat left-to-right accumulation
  *       over c in lexicographic order, c of the first advanced string most
  *       significant, exactly as the loop of Algorithm 1 is written; then one
@@ -471,9 +471,9 @@ int orc_decode(int sigma, int d, int h, uint64_t x, int* X) {
 }
 
 /* ------------------------------------------------------------------------ */
-/* Feasibility check (Algorithm 2, the lines computing W and E; Lemma 1's
- * third condition): W = u + dR - F(u + (d-1)R, .., u + 0R), E = max(0, max W).
- * work holds (d+1) * n values of scratch; W_out (n values) is optional. */
+/* Feasibility check (Algorithm 2's W and E; Lemma 1's third condition):
+ * W = u + dR - F(u + (d-1)R, .., u + 0R), E = max(0, max W).  work holds
+ * (d+1) * n values of scratch; W_out (n values) is optional. */
 
 int orc_check_f64(int sigma, int d, int h, int f_mode, const double* u, double R, double* work, double* W_out, double* E_out) {
   shape_t s;
