@@ -22,7 +22,8 @@ kernels accept.
   2^L - 1 visits each tile of the 4 x 4 x 8 grid that passes the corner test
   (I0 <= I1, I1 / 2 <= I2, 4 I0 + 8 I2 <= 2^L - 1) exactly once, and every
   orbit representative lies in one of those tiles.  Its 32-bit indices stay
-  inside the stored half for every h up to the kernel's limit.
+  inside the stored half for every h up to the kernel's limit; its outputs
+  partition the stored half, and its reads are the states they stand for.
 """
 import pathlib
 import re
@@ -371,3 +372,92 @@ def test_d3s_sweep_indices_stay_in_the_stored_half():
         assert 4 * nt == 2 ** (3 * h - 1) <= 2 ** 32
         assert top < 2 ** 32 and 1 << (max(L - 3, 1) + 2 * L - 5) < 2 ** 32  # the head bit and the tile count
     assert 2 ** (3 * (h_max + 1) - 1) > 2 ** 32  # the limit is tight
+
+
+
+def _d3s_rep(I0, I1, I2, M, L, r):
+    """d3s2_rep: the representative of thread pair r of tile (I0, I1, I2), or None"""
+    t1 = (r & 1) | (((r >> 3) & 1) << 1)
+    t0 = ((r >> 1) & 1) | (((r >> 4) & 1) << 1)
+    t2 = ((r >> 2) & 1) | (((r >> 5) & 1) << 1) | (((r >> 6) & 1) << 2)
+    T = (4 * I0 + t0, 4 * I1 + t1, 8 * I2 + t2)
+    if T[0] > T[1] or T[1] > T[2] or T[0] + T[2] > M:
+        return None
+    if T[0] + T[2] == M and T[1] >= 1 << (L - 1):
+        return None
+    return T
+
+
+PERMS3 = [(0, 1, 2), (0, 2, 1), (1, 0, 2), (1, 2, 0), (2, 0, 1), (2, 1, 0)]
+
+
+def _dup_mask(e01, e12):
+    return 0x3E if e01 and e12 else 0x2C if e01 else 0x32 if e12 else 0
+
+
+@pytest.mark.parametrize("L", [3, 4, 5, 6])
+def test_d3s_outputs_and_reads(L):
+    """The sigma = 2, d = 3 sweep (sweep_d3s.cuh), restated: over the walk's
+    live tiles and both sides (tau, ~tau) of every orbit pair, the outputs at
+    the four stored heads of every distinct permutation partition the stored
+    half (string 0's head 0).  On sampled pairs each read is the state it
+    stands for, by the header's index: A1[k] the pair (0 X_o, 0 X_o', X_k c)
+    of v_{t-1}, A2[k] the quad (0 X_k, X_o c, X_o' c') of v_{t-2}, the block
+    the eight (T0 c, T1 c', T2 c'') of v_{t-3}."""
+    h = L + 1
+    M = (1 << L) - 1
+    nt = 1 << (3 * L)
+
+    def tail(sa, sb, sc):
+        return (sa << 2) | (sb << 1) | sc
+
+    def index(s0, s1, s2):  # three letter lists, head first
+        return sum(s0[p] * 2 ** (3 * (h - 1 - p) + 2) + s1[p] * 2 ** (3 * (h - 1 - p) + 1) + s2[p] * 2 ** (3 * (h - 1 - p))
+                   for p in range(h))
+
+    def bits(x):
+        return [(x >> (L - 1 - p)) & 1 for p in range(L)]
+
+    writes, reps = [], []
+    for k in range(1 << (max(L - 3, 1) + 2 * L - 5)):
+        row = k >> (L - 3)
+        I0 = k >> (2 * L - 5)
+        I1 = I0 + (row & ((1 << (L - 2)) - 1))
+        I2 = (I1 >> 1) + ((k + 37 * row) & ((1 << (L - 3)) - 1))
+        if not (I1 < (1 << (L - 2)) and 4 * I0 + 8 * I2 <= M):
+            continue
+        for r in range(128):
+            T = _d3s_rep(I0, I1, I2, M, L, r)
+            if T is None:
+                continue
+            reps.append(T)
+            dup = _dup_mask(T[0] == T[1], T[1] == T[2])
+            for side in (0, 1):
+                S = [_spread3(x ^ (M if side else 0)) for x in T]
+                for q, (p0, p1, p2) in enumerate(PERMS3):
+                    if (dup >> q) & 1:
+                        continue
+                    x0 = tail(S[p0], S[p1], S[p2])
+                    writes.extend(m * nt + x0 for m in range(4))
+    assert sorted(writes) == list(range(4 * nt))
+    assert len(set(reps)) == len(reps)
+
+    rng = np.random.default_rng(L)
+    for i in rng.choice(len(reps), min(40, len(reps)), replace=False):
+        T = reps[i]
+        for side in (0, 1):
+            X = [x ^ (M if side else 0) for x in T]
+            S = [_spread3(x) for x in X]
+            for kk in range(3):
+                o, o2 = (1 if kk == 0 else 0), (1 if kk == 2 else 2)
+                for c in (0, 1):
+                    assert tail(S[o], S[o2], S[kk] << 3) + c == index([0] + bits(X[o]), [0] + bits(X[o2]), bits(X[kk]) + [c])
+                a2 = tail(S[kk], S[o] << 3, S[o2] << 3)
+                for c in range(4):
+                    assert a2 + c == index([0] + bits(X[kk]), bits(X[o]) + [c >> 1], bits(X[o2]) + [c & 1])
+        ST = [_spread3(x) for x in T]
+        for side in (0, 1):
+            b = (tail(ST[0], ST[1], ST[2]) << 3) + 4 * side
+            for c in range(4):
+                cc = 4 * side + c
+                assert b + c == index(bits(T[0]) + [cc >> 2], bits(T[1]) + [(cc >> 1) & 1], bits(T[2]) + [cc & 1])
