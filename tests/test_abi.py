@@ -114,3 +114,35 @@ def test_missing_library_fails_loudly(monkeypatch):
         binding.LcsBound(2, 2, 8)
     with pytest.raises(RuntimeError, match="nvcc not found"):
         binding.lcs_bound_default_opts()
+
+
+def _declarations():
+    """(return type, name, parameter count) of every function the header declares"""
+    text = open(HEADER).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    out = []
+    for m in re.finditer(r"^\s*((?:const\s+)?[\w]+\s*\*?)\s*(lcs_\w+)\s*\(([^;]*?)\)\s*;", text, flags=re.M | re.S):
+        ret, name, params = m.group(1).replace(" ", ""), m.group(2), m.group(3).strip()
+        depth, n = 0, (0 if params in ("", "void") else 1)
+        for ch in params:
+            depth += ch in "(["
+            depth -= ch in ")]"
+            n += ch == "," and depth == 0
+        out.append((ret, name, n))
+    return out
+
+
+def test_binding_signatures_match_the_header(L):
+    """Every declared function has ctypes argtypes of the header's arity and
+    the restype of its C return type, so a changed declaration cannot be
+    called with stale marshalling."""
+    import ctypes
+
+    want_res = {"lcs_status": ctypes.c_int, "void": None, "constchar*": ctypes.c_char_p, "int64_t": ctypes.c_int64}
+    decls = _declarations()
+    assert len(decls) == len(declared_functions())
+    for ret, name, n in decls:
+        fn = getattr(L, name)
+        assert fn.argtypes is not None and len(fn.argtypes) == n, (name, n, fn.argtypes)
+        assert ret in want_res, (name, ret)
+        assert fn.restype == want_res[ret], (name, ret, fn.restype)
