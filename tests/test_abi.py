@@ -116,19 +116,29 @@ def test_missing_library_fails_loudly(monkeypatch):
         binding.lcs_bound_default_opts()
 
 
+def _split_params(params):
+    if params in ("", "void"):
+        return []
+    out, depth, cur = [], 0, ""
+    for ch in params:
+        depth += ch in "(["
+        depth -= ch in ")]"
+        if ch == "," and depth == 0:
+            out.append(cur.strip())
+            cur = ""
+        else:
+            cur += ch
+    return out + [cur.strip()]
+
+
 def _declarations():
-    """(return type, name, parameter count) of every function the header declares"""
+    """(return type, name, parameter count, parameters) of every function the header declares"""
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
     out = []
     for m in re.finditer(r"^\s*((?:const\s+)?[\w]+\s*\*?)\s*(lcs_\w+)\s*\(([^;]*?)\)\s*;", text, flags=re.M | re.S):
-        ret, name, params = m.group(1).replace(" ", ""), m.group(2), m.group(3).strip()
-        depth, n = 0, (0 if params in ("", "void") else 1)
-        for ch in params:
-            depth += ch in "(["
-            depth -= ch in ")]"
-            n += ch == "," and depth == 0
-        out.append((ret, name, n))
+        ret, name, params = m.group(1).replace(" ", ""), m.group(2), _split_params(m.group(3).strip())
+        out.append((ret, name, len(params), params))
     return out
 
 
@@ -141,8 +151,16 @@ def test_binding_signatures_match_the_header(L):
     want_res = {"lcs_status": ctypes.c_int, "void": None, "constchar*": ctypes.c_char_p, "int64_t": ctypes.c_int64}
     decls = _declarations()
     assert len(decls) == len(declared_functions())
-    for ret, name, n in decls:
+    scalars = {"int": ctypes.c_int, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64, "double": ctypes.c_double,
+               "float": ctypes.c_float, "lcs_status": ctypes.c_int}
+    for ret, name, n, params in decls:
         fn = getattr(L, name)
         assert fn.argtypes is not None and len(fn.argtypes) == n, (name, n, fn.argtypes)
         assert ret in want_res, (name, ret)
         assert fn.restype == want_res[ret], (name, ret, fn.restype)
+        for param, ct in zip(params, fn.argtypes):
+            if "*" in param:  # any pointer: void*, char*, or a pointer to a struct or scalar
+                assert ct in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(ct, ctypes._Pointer), (name, param, ct)
+            else:
+                ctype = param.replace("const ", "").split()[0]
+                assert ct == scalars[ctype], (name, param, ct)
