@@ -1,7 +1,8 @@
 """include/lcs_bound.h is a C header: a C11 program (and the same file as C++)
 compiles against it with every warning an error, links with the library and
 runs the calls that need no device (defaults, status strings, argument errors
-raised before any CUDA call).
+raised before any CUDA call).  The structs the Python binding mirrors have the
+C compiler's sizes and field offsets.
 """
 import os
 import shutil
@@ -66,3 +67,36 @@ def test_header_compiles_links_and_runs(tmp_path, lib_dir, compiler, std):
     r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=120)
     assert r.returncode == 0, r.stderr
     assert r.stdout == WANT
+
+
+def test_struct_layouts_match_the_binding(tmp_path):
+    """Every struct the binding mirrors has the C compiler's size and field
+    offsets, so no field is read from the wrong place."""
+    import ctypes
+
+    from paper_2407_10925_gb300 import binding
+
+    cc = shutil.which("gcc")
+    if cc is None:
+        pytest.skip("gcc not installed")
+    structs = [binding.lcs_bound_opts, binding.lcs_bound_report, binding.lcs_bound_stats_t,
+               binding.lcs_bound_check_record, binding.lcs_bound_batch_info_t]
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "lcs_bound.h"', "int main(void) {"]
+    want = []
+    for st in structs:
+        name = st.__name__
+        lines.append(f'  printf("{name} %zu\\n", sizeof({name}));')
+        want.append(f"{name} {ctypes.sizeof(st)}")
+        for field, _ in st._fields_:
+            lines.append(f'  printf("{name}.{field} %zu\\n", offsetof({name}, {field}));')
+            want.append(f"{name}.{field} {getattr(st, field).offset}")
+    lines += ["  return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    r = subprocess.run([cc, "-std=c11", "-Wall", "-Werror", f"-I{os.path.join(ROOT, 'include')}", str(src), "-o",
+                        str(exe)], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([str(exe)], capture_output=True, text=True, timeout=60)
+    assert r.returncode == 0
+    assert r.stdout.split("\n")[:-1] == want
