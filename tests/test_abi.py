@@ -164,3 +164,37 @@ def test_binding_signatures_match_the_header(L):
             else:
                 ctype = param.replace("const ", "").split()[0]
                 assert ct == scalars[ctype], (name, param, ct)
+
+
+def test_product_never_reaches_the_oracle():
+    """The oracle is test infrastructure.  The package (Python, CUDA and the C
+    header) never names it.  bench.py imports it only in its CPU-sample
+    functions (the cpu_baseline leg and the reference arm), and the entry
+    module only in build() and smoke()."""
+    import ast
+
+    pkg = os.path.join(ROOT, "paper_2407_10925_gb300")
+    for base, _, files in os.walk(pkg):
+        if "_build" in base:
+            continue
+        for f in files:
+            if f.endswith((".py", ".cu", ".cuh", ".h", ".c", ".cpp")):
+                text = open(os.path.join(base, f)).read()
+                assert not re.search(r"^\s*(import|from)\s+oracle\b", text, flags=re.M), f
+                assert "lcs_oracle" not in text and "orc_" not in text, f
+    assert "oracle" not in open(HEADER).read().lower()
+
+    allowed = {"bench.py": {"_oracle_chunk", "oracle_sample"}, "__graft_entry__.py": {"build", "smoke"}}
+    for name, funcs in allowed.items():
+        tree = ast.parse(open(os.path.join(ROOT, name)).read())
+        found = set()
+        for fn in ast.walk(tree):
+            if isinstance(fn, ast.FunctionDef):
+                for node in ast.walk(fn):
+                    if isinstance(node, ast.Import) and any(a.name.split(".")[0] == "oracle" for a in node.names):
+                        found.add(fn.name)
+                    if isinstance(node, ast.ImportFrom) and (node.module or "").split(".")[0] == "oracle":
+                        found.add(fn.name)
+        top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
+        assert not any("oracle" in ast.dump(n) for n in top), name  # no module-level import
+        assert found <= funcs, (name, found)
