@@ -5,6 +5,7 @@ reference arm's JSON line.
 import hashlib
 import json
 import os
+import re
 import sys
 
 import pytest
@@ -128,3 +129,11 @@ def test_reference_arm_prints_one_contract_line():
     assert cfg["states"] == 2 ** 32 and "workload" in cfg
     want_ms = cfg["states"] * cfg["sweeps_per_step"] / j["value"] * 1e3
     assert j["ms_per_step"] == pytest.approx(want_ms, rel=1e-6)
+
+
+def test_readme_lists_every_bench_config():
+    """The README's bench line names exactly the workloads bench.py defines."""
+    text = open(os.path.join(ROOT, "README.md")).read()
+    m = re.search(r"--config ([\w|]+)", text)
+    assert m, "README names no --config list"
+    assert set(m.group(1).split("|")) == set(bench.CONFIGS)
