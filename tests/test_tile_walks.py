@@ -461,3 +461,26 @@ def test_d3s_outputs_and_reads(L):
             for c in range(4):
                 cc = 4 * side + c
                 assert b + c == index(bits(T[0]) + [cc >> 2], bits(T[1]) + [(cc >> 1) & 1], bits(T[2]) + [cc & 1])
+
+
+def _tri_decode(q):
+    """tri_decode (sweep_s2d2.cuh): the upper-triangle index q -> (A, B), A <= B,
+    q = B (B + 1) / 2 + A; a double-precision root corrected exactly"""
+    b = int((np.sqrt(8.0 * float(q) + 1.0) - 1.0) * 0.5)
+    while b * (b + 1) // 2 > q:
+        b -= 1
+    while (b + 1) * (b + 2) // 2 <= q:
+        b += 1
+    return q - b * (b + 1) // 2, b
+
+
+def test_tri_decode_of_the_batch_walk():
+    """The batch's sigma = d = 2 items number their upper-triangle tiles with q;
+    the decode is exact for every q of the sizes a batch takes and, sampled,
+    far beyond them."""
+    want = [(A, B) for B in range(700) for A in range(B + 1)]
+    assert [_tri_decode(q) for q in range(len(want))] == want
+    rng = np.random.default_rng(7)
+    for q in [int(v) for v in rng.integers(0, 1 << 52, 3000)] + [(1 << 52) - 1, (1 << 40) + 12345]:
+        A, B = _tri_decode(q)
+        assert 0 <= A <= B and B * (B + 1) // 2 + A == q
