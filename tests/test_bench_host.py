@@ -137,3 +137,22 @@ def test_readme_lists_every_bench_config():
     m = re.search(r"--config ((?:\w+\|)+\w+)", text)  # the list of all of them
     assert m, "README names no --config list"
     assert set(m.group(1).split("|")) == set(bench.CONFIGS)
+
+
+def test_profile_summaries_name_runnable_commands():
+    """Each ncu summary under profiles/ gives its command; every ncu there
+    leaves the clocks alone (--clock-control none), and every script it runs
+    is a committed file."""
+    pdir = os.path.join(ROOT, "profiles")
+    mds = [f for f in os.listdir(pdir) if f.endswith(".md")]
+    assert mds
+    for f in mds:
+        text = open(os.path.join(pdir, f)).read()
+        # join continued lines so each command reads as one
+        text = re.sub(r"\\\n\s*", " ", text)
+        ncu = [ln for ln in text.splitlines() if re.search(r"(^|\s)ncu\s+-", ln)]
+        assert ncu, f
+        for ln in ncu:
+            assert "--clock-control none" in ln, (f, ln)
+        for script in re.findall(r"python (\S+\.py)", text):
+            assert os.path.exists(os.path.join(ROOT, script)), (f, script)
