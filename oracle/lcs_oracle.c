@@ -52,8 +52,12 @@
  *   R9  f_mode = 1 (an extension the paper does not use): the max runs over
  *       every non-empty set of advanced strings; for equal heads the full set
  *       carries the +1 of the match.  The paper prints no value for it;
- *       it is pinned by brute force instead: every candidate drops heads,
- *       which can only lower the LCS, so F <= F_all <= W_n.
+ *       it is pinned by brute force instead (every candidate drops heads,
+ *       which can only lower the LCS, so F <= F_all <= W_n) and by values
+ *       worked out by hand at single states, one for each kind of winning
+ *       set: a singleton of a majority string, a pair with the minority
+ *       string, the full set without a match, a proper subset beating the
+ *       match on the exact W tables, the full set with its +1.
  */
 #include <math.h>
 #include <stdint.h>
@@ -172,7 +176,22 @@ static int candidate_sets(const shape_t* s, const int* X, int f_mode, int sets[]
       if (!dup) sizes[m++] = k;
     }
   } else {
+#if ORC_MUTANT == 13
+    for (uint64_t mask = 1; mask < ((uint64_t)1 << s->d) - 1; ++mask) {
+#else
     for (uint64_t mask = 1; mask < ((uint64_t)1 << s->d); ++mask) {
+#endif
+#if ORC_MUTANT == 12
+      /* only the sets N_z of f_mode 0 and the full set */
+      int is_nz = mask == ((uint64_t)1 << s->d) - 1;
+      for (int z = 0; z < s->sigma && !is_nz; ++z) {
+        uint64_t nz = 0;
+        for (int j = 0; j < s->d; ++j)
+          if (X[j] != z) nz |= (uint64_t)1 << j;
+        is_nz = nz == mask;
+      }
+      if (!is_nz) continue;
+#endif
       int k = 0;
       for (int j = 0; j < s->d; ++j)
         if (mask >> j & 1) sets[m][k++] = j;
@@ -256,7 +275,12 @@ static double F_state_f64(const shape_t* s, const double* const* v, uint64_t x, 
 #else
     double mean = div_dir(acc, (double)terms, mode);
 #endif
+#if ORC_MUTANT == 14
+#elif ORC_MUTANT == 15
+    if (f_mode == 1 && b) mean = add_dir(1.0, mean, mode);
+#else
     if (f_mode == 1 && b && k == s->d) mean = add_dir(1.0, mean, mode); /* R9 */
+#endif
 #if ORC_MUTANT == 4
     if (best == -INFINITY || mean < best) best = mean;
 #else
@@ -310,7 +334,12 @@ static int F_state_fx(const shape_t* s, const int64_t* const* v, uint64_t x, int
 #else
     __int128 mean = floor_div128(acc, (int64_t)terms);
 #endif
-    if (f_mode == 1 && b && k == s->d) mean += one;
+#if ORC_MUTANT == 14
+#elif ORC_MUTANT == 15
+    if (f_mode == 1 && b) mean += one;
+#else
+    if (f_mode == 1 && b && k == s->d) mean += one; /* R9 */
+#endif
 #if ORC_MUTANT == 4
     if (!have || mean < best) best = mean, have = 1;
 #else

@@ -107,3 +107,37 @@ def test_generated_input_mutant_is_caught(orc, mutant):
     with orc.use_mutant(mutant):
         failures = _generated_pins_hold(orc)
     assert failures, f"mutant {mutant} ({GENERATED_MUTANTS[mutant]}) passed every pin"
+
+
+# mistakes in the all-advance-sets F (f_mode 1), an extension the paper does
+# not print values for; its pins are the hand-worked single-state values
+F_MODE1_MUTANTS = {
+    12: "f_mode 1 keeps only the sets N_z and the full set",
+    13: "f_mode 1 never takes the full set",
+    14: "f_mode 1 drops the +1 of the full set for equal heads",
+    15: "f_mode 1 adds the +1 to every set when the heads are equal",
+}
+
+
+def _all_subsets_pins_hold(orc):
+    import test_oracle_pins as pins
+
+    return pins.all_subsets_hand_worked_failures(orc)
+
+
+def test_unmutated_all_subsets_passes(orc):
+    assert _all_subsets_pins_hold(orc) == []
+
+
+@pytest.mark.parametrize("mutant", sorted(F_MODE1_MUTANTS), ids=lambda m: F_MODE1_MUTANTS[m])
+def test_all_subsets_mutant_is_caught(orc, mutant):
+    with orc.use_mutant(mutant):
+        failures = _all_subsets_pins_hold(orc)
+    assert failures, f"mutant {mutant} ({F_MODE1_MUTANTS[mutant]}) passed every pin"
+
+
+@pytest.mark.parametrize("mutant", sorted(F_MODE1_MUTANTS), ids=lambda m: F_MODE1_MUTANTS[m])
+def test_all_subsets_mutant_leaves_the_paper_F_alone(orc, mutant):
+    """the f_mode 1 mutants change nothing of the paper's F: the f_mode 0 pins still hold"""
+    with orc.use_mutant(mutant):
+        assert _pins_hold(orc) == []

@@ -245,6 +245,105 @@ def test_all_subsets_iterates_below_W(orc, brute_tables, case):
             assert Fraction(int(v[x]), 1 << 44) <= W[n][x]
 
 
+# Values of the all-advance-sets F (f_mode 1) worked out by hand at single
+# states, one for each kind of set that can win the max.  f_mode 1 is the max,
+# over every non-empty set N of strings, of the mean over the appended letters
+# of v_|N| at the state whose strings in N lose their head and gain the letter
+# at their end; when every head is equal the full set carries the +1 of the
+# match (the extension of Algorithm 1 and Eq. ineq3 that reading R15 takes).
+# The paper's F (f_mode 0) only has the sets N_z = {j : head_j != z}.  With
+# h = 1 a state is one letter per string, and a string that advances becomes
+# the appended letter.  Values are in units; every one is exact in fixed point
+# and in binary floating point.
+def _unit_vector(n, where, value):
+    v = np.zeros(n)
+    for x in where:
+        v[x] = value
+    return v
+
+
+def all_subsets_hand_worked_cases():
+    """(name, (s, d, h), arguments v_1..v_d, state, F_all at the state, F at the state)."""
+    cases = []
+    # (2,3,1), state (a,b,c) = (0,0,1), index 0*4 + 0*2 + 1 = 1: heads 0,0,1.
+    # N_0 = {c} and N_1 = {a,b}; the other five sets are extra.
+    # A: v_1 = 8 at (1,0,1) (index 5), v_2 = v_3 = 0.  Advancing a alone
+    #    reads v_1 at (0,0,1) and (1,0,1): (0 + 8)/2 = 4.  Every other set reads
+    #    only zeros: {c} reads (0,0,0), (0,0,1); {b} reads (0,0,1), (0,1,1);
+    #    the pairs and the full set read v_2, v_3.  So F_all = 4, won by a
+    #    singleton of a majority string; F (unequal heads, no +1) = 0.
+    cases.append(("majority singleton", (2, 3, 1), [_unit_vector(8, [5], 8.0), np.zeros(8), np.zeros(8)], 1, 4.0, 0.0))
+    # B: v_2 = 8 at (1,0,0) (index 4), v_1 = v_3 = 0.  Advancing {a, c} reads
+    #    v_2 at (x,0,z) for x, z in {0,1}: indices 0, 1, 4, 5 -> (0+0+8+0)/4 = 2.
+    #    {a,b} reads (x,y,1): 1, 3, 5, 7 -> 0; {b,c} reads (0,y,z): 0..3 -> 0;
+    #    singletons read v_1 = 0, the full set v_3 = 0.  F_all = 2, won by a pair
+    #    holding the minority string; F = max({c}: 0, {a,b}: 0) = 0.
+    cases.append(("pair with the minority", (2, 3, 1), [np.zeros(8), _unit_vector(8, [4], 8.0), np.zeros(8)], 1, 2.0, 0.0))
+    # C: v_3 = 8 everywhere, v_1 = v_2 = 0.  The full set's mean is 8 and gets
+    #    no +1 (the heads differ); every other set reads zeros.  F_all = 8, F = 0.
+    cases.append(("full set, unequal heads", (2, 3, 1), [np.zeros(8), np.zeros(8), np.full(8, 8.0)], 1, 8.0, 0.0))
+    # E: (2,2,1), state (0,0), index 0: equal heads.  v_1 = 0, v_2 = 5
+    #    everywhere.  The full set gives 1 + 5 = 6 (the match), {a} and {b}
+    #    read v_1: 0.  F_all = 6 = F.
+    cases.append(("full set with the match", (2, 2, 1), [np.zeros(4), np.full(4, 5.0)], 0, 6.0, 6.0))
+    return cases
+
+
+# D, on the exact W tables: (2,2,2), strings a = 00, b = 01 (index 1: the
+# digits a_0 b_0 a_1 b_1 = 0 0 0 1), n = 2, so the arguments are v_1 = W_1 and
+# v_2 = W_0.  W_0 is the LCS of the two strings themselves; W_1 adds one
+# random letter to the string of our choice, after seeing the letters.
+#  * The match (full set, +1): 1 + the mean of W_0 over (0c, 1e): LCS(00, 10)
+#    = 1, LCS(00, 11) = 0, LCS(01, 10) = 1, LCS(01, 11) = 1 -> 1 + 3/4 = 7/4.
+#    That is the paper's F here (both heads are 0, so N_1 is the full set).
+#  * Advancing a alone: the mean of W_1 at (00, 01) and (01, 01).
+#    W_1(01, 01) = 2: the LCS is already 2 and cannot exceed the length 2 of
+#    the string left alone.  W_1(00, 01): the LCS is 1; a letter x for a and y
+#    for b are drawn, and appending x = 1 to a (001 vs 01) or y = 0 to b (00
+#    vs 010) reaches 2, which fails only when x = 0 and y = 1: 3/4 * 2 + 1/4 *
+#    1 = 7/4.  The mean is (7/4 + 2)/2 = 15/8.
+#  * Advancing b alone: the mean of W_1 at (00, 10) and (00, 11): at most
+#    (7/4 + 1)/2 < 15/8 (each LCS is at most 1, plus 1 with a drawn letter).
+# So F_all(W_1, W_0) = 15/8, won by a proper subset that skips the match, and
+# F(W_1, W_0) = 7/4.
+HAND_D = dict(shape=(2, 2, 2), state=1, W1={("00", "01"): Fraction(7, 4), ("01", "01"): Fraction(2)},
+              F_all=Fraction(15, 8), F=Fraction(7, 4))
+
+
+def _bits_state(a, b):
+    """index of (a, b) for sigma = d = 2, h = 2: digits a_0 b_0 a_1 b_1"""
+    return a[0] * 8 + b[0] * 4 + a[1] * 2 + b[1]
+
+
+def all_subsets_hand_worked_failures(orc, W222=None):
+    """the hand-worked f_mode 1 values that the oracle misses (empty: all agree)"""
+    failures = []
+    K = 44
+    for name, (s, d, h), vs, x, want_all, want_f in all_subsets_hand_worked_cases():
+        for arith in ("fx", "f64"):
+            args = [np.array([int(val * (1 << K)) for val in v], dtype=np.int64) for v in vs] if arith == "fx" else vs
+            scale = (1 << K) if arith == "fx" else 1
+            got_all = orc.F(s, d, h, args, arith=arith, f_mode=1)[x]
+            got_f = orc.F(s, d, h, args, arith=arith)[x]
+            if got_all != want_all * scale or got_f != want_f * scale:
+                failures.append(f"{name} ({arith})")
+    W = W222 if W222 is not None else bf.W_table(2, 2, 2, 2)
+    for (a, b), val in HAND_D["W1"].items():  # the hand-worked W_1 values are the brute force's
+        assert W[1][_bits_state([int(c) for c in a], [int(c) for c in b])] == val
+    vs = [np.array([int(W[1][y] * (1 << K)) for y in range(16)], dtype=np.int64),
+          np.array([int(W[0][y] * (1 << K)) for y in range(16)], dtype=np.int64)]
+    x = HAND_D["state"]
+    if (orc.F(2, 2, 2, vs, arith="fx", f_mode=1)[x] != HAND_D["F_all"] * (1 << K)
+            or orc.F(2, 2, 2, vs, arith="fx")[x] != HAND_D["F"] * (1 << K)):
+        failures.append("proper subset beats the match on W")
+    return failures
+
+
+def test_all_subsets_hand_worked(orc, brute_tables):
+    """f_mode 1 equals the values worked out by hand, one state per kind of winning set."""
+    assert all_subsets_hand_worked_failures(orc, brute_tables[(2, 2, 2, 4)]) == []
+
+
 def test_all_subsets_adds_candidates():
     """On random arguments the extra advance sets win somewhere (the test above is not vacuous)."""
     import oracle as orc_mod
