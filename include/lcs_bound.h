@@ -124,6 +124,12 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts,
  * device stores (half of it under complement symmetry). */
 lcs_status lcs_bound_size(const lcs_bound_t* hnd, uint64_t* n_states, uint64_t* n_stored);
 
+/* The shape (sigma, d, h) a single-instance handle was created with; any
+ * output pointer may be NULL.  LCS_EINVAL for a batch handle (its instances
+ * have their own shapes).  Lets a caller size the d vectors that
+ * set_start and export take without keeping the shape itself. */
+lcs_status lcs_bound_shape(const lcs_bound_t* hnd, int* sigma, int* d, int* h);
+
 /* Run n_iters >= 0 iterations of Algorithm 2: n_iters evaluations of F, the
  * increment of each iteration that is checked, and the checks selected by
  * check_every (always including the last of this call when n_iters > 0).
@@ -426,7 +432,8 @@ lcs_status lcs_fp32_experiment(int sigma, int d, int h, int64_t n_iters, double 
  * v_out = F(v_prev[0], .., v_prev[d-1]) where v_prev[k-1] is the iterate k
  * steps older than the one being computed (the k-th argument v_k of F).
  * All vectors are device pointers of sigma^(d h) fixed-point int64 values in
- * state-index order (no symmetry).  v_out must not alias any input.
+ * state-index order (no symmetry).  v_out must not share a byte with any
+ * input (LCS_EINVAL).
  * f_mode and frac_bits as in lcs_bound_opts.  Shapes as lcs_bound_create
  * (the general kernels serve those without a specialised one).  stream:
  * cudaStream_t or NULL (legacy default stream).  Asynchronous; no allocation. */
@@ -450,11 +457,17 @@ lcs_status lcs_sweep_fx(int sigma, int d, int h, int f_mode, int frac_bits, cons
  * The shapes with a specialised kernel only (see lcs_bound_create); others
  * return LCS_EUNSUPPORTED.
  *
+ * v_out must not share a byte with any v_prev[k]; R_out and argmin_out (8
+ * bytes each) must not share a byte with any vector or with each other
+ * (LCS_EINVAL).  The inputs may share bytes with each other.
+ *
  * Scratch: the per-CTA partials of the reduction live in a fixed 64 KiB
  * array inside the library (4096 partials), reserved on every device that
- * loads the library until the process exits.  The first call on each device
- * looks up that array's device address (cudaGetSymbolAddress) with the
- * device current; make that first call before any stream capture.  A call
+ * loads the library until the process exits.  Every call looks up that
+ * array's device address (cudaGetSymbolAddress, which allocates nothing) with
+ * the calling thread's current device, so the address stays right after the
+ * device is reset.  The first call on each device also loads the library's
+ * device code there: make that first call before any stream capture.  A call
  * whose launch would need more than 4096 partials returns LCS_EINVAL.  The
  * function calls no allocator (no cudaMalloc, cudaFree or allocating library
  * routine).  All calls share the one array and each call overwrites every

@@ -115,6 +115,7 @@ def lib():
                 "lcs_bound_default_opts": [P(lcs_bound_opts)],
                 "lcs_bound_create": [i32, i32, i32, P(lcs_bound_opts), P(vp)],
                 "lcs_bound_size": [vp, P(u64), P(u64)],
+                "lcs_bound_shape": [vp, P(i32), P(i32), P(i32)],
                 "lcs_bound_iterate": [vp, i64],
                 "lcs_bound_read": [vp, P(dbl), P(u64), P(dbl), P(dbl), P(i64)],
                 "lcs_bound_read_report": [vp, P(lcs_bound_report)],
@@ -209,6 +210,35 @@ def _ptr_and_kind(a, dtype):
     return a.ctypes.data, 0
 
 
+def _numel(a) -> int:
+    """number of values of a numpy array or torch tensor"""
+    try:
+        import torch
+    except ImportError:  # pragma: no cover
+        torch = None
+    if torch is not None and isinstance(a, torch.Tensor):
+        return int(a.numel())
+    if isinstance(a, np.ndarray):
+        return int(a.size)
+    raise TypeError("expected a numpy array or a torch tensor")
+
+
+def _require_vectors(vs, count: int, n: int, what: str):
+    """The C side reads `count` pointers and n values behind each: check both before the call."""
+    if len(vs) != count:
+        raise ValueError(f"{what}: {len(vs)} vectors given, {count} expected")
+    for k, v in enumerate(vs):
+        m = _numel(v)
+        if m != n:
+            raise ValueError(f"{what}: vector {k} holds {m} values, {n} expected")
+
+
+def _require_len(a, n: int, what: str, at_least: bool = False):
+    m = _numel(a)
+    if (m < n) if at_least else (m != n):
+        raise ValueError(f"{what} holds {m} values, {'at least ' if at_least else ''}{n} expected")
+
+
 class TorchAllocator:
     """Device memory for the library from PyTorch's caching allocator."""
 
@@ -258,6 +288,22 @@ def lcs_bound_size(hnd):
     return a.value, b.value
 
 
+def lcs_bound_shape(hnd):
+    """(sigma, d, h) of a single-instance handle."""
+    a, b, c = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+    _check(lib().lcs_bound_shape(hnd, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)), "lcs_bound_shape")
+    return a.value, b.value, c.value
+
+
+def _vectors_for(hnd, form: str):
+    """(d, values per vector) of the handle for a form: 'full', 'stored' or 'orbit'"""
+    _, d, _ = lcs_bound_shape(hnd)
+    if form == "orbit":
+        return d, lcs_bound_orbit_size(hnd)
+    n, n_stored = lcs_bound_size(hnd)
+    return d, n if form == "full" else n_stored
+
+
 def lcs_bound_iterate(hnd, n_iters: int):
     _check(lib().lcs_bound_iterate(hnd, int(n_iters)), "lcs_bound_iterate")
 
@@ -285,22 +331,26 @@ def _vec_array(vs, dtype):
 
 def lcs_bound_set_start(hnd, vs):
     """vs[k]: the iterate k steps older than the newest (float64, every state)."""
+    _require_vectors(vs, *_vectors_for(hnd, "full"), "lcs_bound_set_start")
     arr, on_dev = _vec_array(vs, np.float64)
     _check(lib().lcs_bound_set_start(hnd, arr, on_dev), "lcs_bound_set_start")
 
 
 def lcs_bound_set_start_fx(hnd, vs):
+    _require_vectors(vs, *_vectors_for(hnd, "full"), "lcs_bound_set_start_fx")
     arr, on_dev = _vec_array(vs, np.int64)
     _check(lib().lcs_bound_set_start_fx(hnd, arr, on_dev), "lcs_bound_set_start_fx")
 
 
 def lcs_bound_set_start_stored_fx(hnd, vs):
     """vs[k]: the stored form (lcs_bound_size's n_stored values) of the iterate k steps older than the newest."""
+    _require_vectors(vs, *_vectors_for(hnd, "stored"), "lcs_bound_set_start_stored_fx")
     arr, on_dev = _vec_array(vs, np.int64)
     _check(lib().lcs_bound_set_start_stored_fx(hnd, arr, on_dev), "lcs_bound_set_start_stored_fx")
 
 
 def lcs_bound_export_stored_fx(hnd, k: int, out):
+    _require_len(out, _vectors_for(hnd, "stored")[1], "lcs_bound_export_stored_fx: out")
     p, on_dev = _ptr_and_kind(out, np.int64)
     _check(lib().lcs_bound_export_stored_fx(hnd, k, p, on_dev), "lcs_bound_export_stored_fx")
     if on_dev:
@@ -317,11 +367,13 @@ def lcs_bound_orbit_size(hnd) -> int:
 
 def lcs_bound_set_start_orbit_fx(hnd, vs):
     """vs[k]: the orbit form (lcs_bound_orbit_size values) of the iterate k steps older than the newest."""
+    _require_vectors(vs, *_vectors_for(hnd, "orbit"), "lcs_bound_set_start_orbit_fx")
     arr, on_dev = _vec_array(vs, np.int64)
     _check(lib().lcs_bound_set_start_orbit_fx(hnd, arr, on_dev), "lcs_bound_set_start_orbit_fx")
 
 
 def lcs_bound_export_orbit_fx(hnd, k: int, out):
+    _require_len(out, _vectors_for(hnd, "orbit")[1], "lcs_bound_export_orbit_fx: out")
     p, on_dev = _ptr_and_kind(out, np.int64)
     _check(lib().lcs_bound_export_orbit_fx(hnd, k, p, on_dev), "lcs_bound_export_orbit_fx")
     if on_dev:
@@ -351,6 +403,7 @@ def lcs_bound_synchronize(hnd):
 
 
 def lcs_bound_export(hnd, k: int, out):
+    _require_len(out, _vectors_for(hnd, "full")[1], "lcs_bound_export: out")
     p, on_dev = _ptr_and_kind(out, np.float64)
     _check(lib().lcs_bound_export(hnd, k, p, on_dev), "lcs_bound_export")
     if on_dev:
@@ -359,6 +412,7 @@ def lcs_bound_export(hnd, k: int, out):
 
 
 def lcs_bound_export_fx(hnd, k: int, out):
+    _require_len(out, _vectors_for(hnd, "full")[1], "lcs_bound_export_fx: out")
     p, on_dev = _ptr_and_kind(out, np.int64)
     _check(lib().lcs_bound_export_fx(hnd, k, p, on_dev), "lcs_bound_export_fx")
     if on_dev:
@@ -367,6 +421,7 @@ def lcs_bound_export_fx(hnd, k: int, out):
 
 
 def lcs_bound_check_vector(hnd, u_dev, R: int) -> int:
+    _require_len(u_dev, _vectors_for(hnd, "stored")[1], "lcs_bound_check_vector: u", at_least=True)
     p, on_dev = _ptr_and_kind(u_dev, np.int64)
     if not on_dev:
         raise TypeError("u must be a CUDA tensor")
@@ -386,8 +441,19 @@ def lcs_bound_destroy(hnd):
         lib().lcs_bound_destroy(hnd)
 
 
+def _shape_states(sigma, d, h) -> int:
+    """sigma^(d h), or 0 for a shape the library rejects itself (LCS_EINVAL)"""
+    if sigma < 2 or d < 2 or h < 1 or d > 16 or sigma ** (d * h) >= 1 << 40:
+        return 0
+    return sigma ** (d * h)
+
+
 def lcs_sweep_fx(sigma, d, h, v_prev, v_out, f_mode=0, frac_bits=44, stream=None):
     """v_out = F(v_prev[0], .., v_prev[d-1]) on the device (CUDA int64 tensors)."""
+    n = _shape_states(sigma, d, h)
+    if n:  # a bad shape is the library's LCS_EINVAL
+        _require_vectors(v_prev, d, n, "lcs_sweep_fx: v_prev")
+        _require_len(v_out, n, "lcs_sweep_fx: v_out")
     arr, on_dev = _vec_array(v_prev, np.int64)
     po, od = _ptr_and_kind(v_out, np.int64)
     if not (on_dev and od):
@@ -402,6 +468,12 @@ def lcs_sweep_incr_fx_noalloc(sigma, d, h, v_prev, v_out, R_out, argmin_out, fra
     a fixed array inside the library.  R_out and argmin_out are one-element
     CUDA int64 tensors that receive R and its state index.
     """
+    n = _shape_states(sigma, d, h)
+    if n:  # a bad shape is the library's LCS_EINVAL
+        _require_vectors(v_prev, d, n, "lcs_sweep_incr_fx_noalloc: v_prev")
+        _require_len(v_out, n, "lcs_sweep_incr_fx_noalloc: v_out")
+    _require_len(R_out, 1, "lcs_sweep_incr_fx_noalloc: R_out", at_least=True)
+    _require_len(argmin_out, 1, "lcs_sweep_incr_fx_noalloc: argmin_out", at_least=True)
     arr, on_dev = _vec_array(v_prev, np.int64)
     po, od = _ptr_and_kind(v_out, np.int64)
     pr, rd = _ptr_and_kind(R_out, np.int64)
@@ -498,6 +570,7 @@ class LcsBatch:
         s, d, h = self.shapes[i]
         if out is None:
             out = np.empty(s ** (d * h), dtype=np.int64)
+        _require_len(out, s ** (d * h), "LcsBatch.export_fx: out")
         return lcs_bound_batch_export_fx(self.hnd, i, k, out)
 
     def info(self):
@@ -513,6 +586,7 @@ class LcsBatch:
 
 def lcs_fp32_experiment(sigma, d, h, n_iters, rho, newest_dev):
     """Float32-stored iteration from the zero start (an experiment, no bound); returns ms per sweep."""
+    _require_len(newest_dev, sigma ** (d * h), "lcs_fp32_experiment: newest")
     p, on = _ptr_and_kind(newest_dev, np.float64)
     if not on:
         raise TypeError("lcs_fp32_experiment writes a CUDA tensor")
@@ -523,6 +597,9 @@ def lcs_fp32_experiment(sigma, d, h, n_iters, rho, newest_dev):
 
 def lcs_lift_prefix(h_from, h_to, src_dev, r_hat, newest_dev, older_dev, frac_bits=44):
     """Prefix-truncation start: every tuple of length h_to takes the value of its first h_from letters."""
+    _require_len(src_dev, 4 ** h_from, "lcs_lift_prefix: src")
+    _require_len(newest_dev, 4 ** h_to, "lcs_lift_prefix: newest")
+    _require_len(older_dev, 4 ** h_to, "lcs_lift_prefix: older")
     ps, a = _ptr_and_kind(src_dev, np.int64)
     pn, b = _ptr_and_kind(newest_dev, np.float64)
     po, c = _ptr_and_kind(older_dev, np.float64)
@@ -590,6 +667,7 @@ class LcsMlp:
         return loss.value
 
     def predict(self, h, states_dev, out_dev):
+        _require_len(out_dev, _numel(states_dev), "LcsMlp.predict: out", at_least=True)
         ps, sd = _ptr_and_kind(states_dev, np.int64)
         if not sd or not out_dev.is_cuda:
             raise TypeError("predict takes CUDA tensors")
@@ -602,10 +680,12 @@ class LcsMlp:
     def predict_bf16(self, h, base, n, out_dev):
         if not out_dev.is_cuda:
             raise TypeError("predict_bf16 writes a CUDA tensor")
+        _require_len(out_dev, n, "LcsMlp.predict_bf16: out", at_least=True)
         _check(lib().lcs_mlp_predict_bf16(self.hnd, h, base, n, out_dev.data_ptr()), "lcs_mlp_predict_bf16")
         return out_dev
 
     def start_vectors(self, h, r_hat, newest_dev, older_dev):
+        _require_vectors([newest_dev, older_dev], 2, 4 ** h, "LcsMlp.start_vectors")
         pn, dn = _ptr_and_kind(newest_dev, np.float64)
         po, do = _ptr_and_kind(older_dev, np.float64)
         if not (dn and do):
@@ -614,6 +694,7 @@ class LcsMlp:
 
     def start_vectors_stored_fx(self, h, r_hat, newest_dev, older_dev, frac_bits=44):
         """The start in a complement-symmetric handle's stored form, fixed point (int64 CUDA tensors of 4^h / 2)."""
+        _require_vectors([newest_dev, older_dev], 2, 4 ** h // 2, "LcsMlp.start_vectors_stored_fx")
         pn, a = _ptr_and_kind(newest_dev, np.int64)
         po, b = _ptr_and_kind(older_dev, np.int64)
         if not (a and b):

@@ -533,6 +533,15 @@ lcs_status lcs_bound_size(const lcs_bound_t* H, uint64_t* n_states, uint64_t* n_
   return LCS_OK;
 }
 
+lcs_status lcs_bound_shape(const lcs_bound_t* H, int* sigma, int* d, int* h) {
+  if (!H) return fail(LCS_EINVAL, "handle is NULL");
+  if (H->batch) return fail(LCS_EINVAL, "a batch handle: its instances have their own shapes");
+  if (sigma) *sigma = H->sigma;
+  if (d) *d = H->d;
+  if (h) *h = H->h;
+  return LCS_OK;
+}
+
 static void fold_events(lcs_bound* H) {
   for (auto& e : H->sweep_ev) {
     float ms = 0;
@@ -1358,7 +1367,8 @@ lcs_status lcs_sweep_fx(int sigma, int d, int h, int f_mode, int frac_bits, cons
   SweepParams p{};
   for (int k = 0; k < d; ++k) {
     if (!v_prev[k]) return fail(LCS_EINVAL, "v_prev[%d] is NULL", k);
-    if ((const void*)v_prev[k] == (const void*)v_out) return fail(LCS_EINVAL, "v_out aliases an input");
+    const uintptr_t a = (uintptr_t)v_prev[k], b = (uintptr_t)v_out;
+    if (a < b + 8 * n && b < a + 8 * n) return fail(LCS_EINVAL, "v_out overlaps v_prev[%d]", k);
     p.prev[k] = (const long long*)v_prev[k];
   }
   p.out = (long long*)v_out;

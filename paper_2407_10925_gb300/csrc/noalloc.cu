@@ -18,7 +18,7 @@
 #include <climits>
 #include <cstdarg>
 #include <cstdio>
-#include <mutex>
+#include <cstdint>
 
 #include "../../include/lcs_bound.h"
 #include "lcs_common.h"
@@ -28,17 +28,12 @@ namespace lcs {
 // Capacity of the static scratch: one 16-byte partial per CTA of the sweep.
 // 4096 CTAs = 64 KiB; a GB300 (152 SMs) launches at most 152 x 8 = 1216.
 constexpr int kNoAllocMaxPartials = 4096;
-constexpr int kNoAllocMaxDevices = 64;
 
 // The scratch itself.  In host code this name is only a stand-in for the
 // device object, never a device address; host code obtains the address with
 // cudaGetSymbolAddress (see noalloc_setup) and passes it to the kernels.
 static __device__ __align__(256) RedPartial g_noalloc_partials[kNoAllocMaxPartials];
 
-static std::mutex g_noalloc_mutex;
-static bool g_noalloc_ready[kNoAllocMaxDevices];
-static RedPartial* g_noalloc_ptr[kNoAllocMaxDevices];
-static int g_noalloc_sms[kNoAllocMaxDevices];
 // defined in lcs_bound.cu: the message lcs_bound_last_error() returns
 void record_error(const char* msg);
 
@@ -52,25 +47,29 @@ static lcs_status noalloc_fail(lcs_status st, const char* fmt, ...) {
   return st;
 }
 
-// Once per device, with that device current: resolve the scratch's device
-// address.  Runs inside the first call of the entry point on each device.
+// With the calling thread's device current: the scratch's device address and
+// the device's SM count.  The address is looked up on every call
+// (cudaGetSymbolAddress allocates nothing): a cached one would go stale when
+// the device's context is re-created (cudaDeviceReset), which reloads the
+// library's device code and may move the array.  The first lookup on a device
+// loads that device code.
 static lcs_status noalloc_setup(int dev, RedPartial** ptr, int* sms) {
-  std::lock_guard<std::mutex> lock(g_noalloc_mutex);
-  if (!g_noalloc_ready[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
-    if (e != cudaSuccess)
-      return noalloc_fail(LCS_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
-    int n = 0;
-    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
-    if (e != cudaSuccess) return noalloc_fail(LCS_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
-    g_noalloc_ptr[dev] = static_cast<RedPartial*>(p);
-    g_noalloc_sms[dev] = n > 0 ? n : 1;
-    g_noalloc_ready[dev] = true;
-  }
-  *ptr = g_noalloc_ptr[dev];
-  *sms = g_noalloc_sms[dev];
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_partials);
+  if (e != cudaSuccess)
+    return noalloc_fail(LCS_ECUDA, "cudaGetSymbolAddress of the static scratch failed: %s", cudaGetErrorString(e));
+  int n = 0;
+  e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return noalloc_fail(LCS_ECUDA, "cudaDeviceGetAttribute: %s", cudaGetErrorString(e));
+  *ptr = static_cast<RedPartial*>(p);
+  *sms = n > 0 ? n : 1;
   return LCS_OK;
+}
+
+// [a, a + na) and [b, b + nb) share a byte
+static bool overlaps(const void* a, unsigned long long na, const void* b, unsigned long long nb) {
+  const uintptr_t x = (uintptr_t)a, y = (uintptr_t)b;
+  return x < y + nb && y < x + na;
 }
 
 // Reduce the sweep's per-CTA partials (min, or max with r_mode = 1, ties to
@@ -133,16 +132,24 @@ extern "C" lcs_status lcs_sweep_incr_fx_noalloc(int sigma, int d, int h, int fra
   for (int i = 0; i < d; ++i) sd *= (unsigned long long)sigma;
   const KernelSet* ks = find_kernels(sigma, d, 0);
   if (!ks) return noalloc_fail(LCS_EUNSUPPORTED, "no kernel for sigma=%d d=%d", sigma, d);
+  // the output vector and the two 8-byte results must not share a byte with
+  // any input or with each other (the inputs may share bytes: they are read only)
   SweepParams p{};
+  const unsigned long long bytes = 8ull * n;
   for (int k = 0; k < d; ++k) {
     if (!v_prev[k]) return noalloc_fail(LCS_EINVAL, "v_prev[%d] is NULL", k);
-    if ((const void*)v_prev[k] == (const void*)v_out) return noalloc_fail(LCS_EINVAL, "v_out aliases an input");
+    if (overlaps(v_prev[k], bytes, v_out, bytes)) return noalloc_fail(LCS_EINVAL, "v_out overlaps v_prev[%d]", k);
+    if (overlaps(v_prev[k], bytes, R_out, 8)) return noalloc_fail(LCS_EINVAL, "R_out lies inside v_prev[%d]", k);
+    if (overlaps(v_prev[k], bytes, argmin_out, 8))
+      return noalloc_fail(LCS_EINVAL, "argmin_out lies inside v_prev[%d]", k);
     p.prev[k] = (const long long*)v_prev[k];
   }
+  if (overlaps(v_out, bytes, R_out, 8)) return noalloc_fail(LCS_EINVAL, "R_out lies inside v_out");
+  if (overlaps(v_out, bytes, argmin_out, 8)) return noalloc_fail(LCS_EINVAL, "argmin_out lies inside v_out");
+  if (overlaps(R_out, 8, argmin_out, 8)) return noalloc_fail(LCS_EINVAL, "R_out and argmin_out overlap");
   int dev = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return noalloc_fail(LCS_ECUDA, "cudaGetDevice: %s", cudaGetErrorString(e));
-  if (dev < 0 || dev >= kNoAllocMaxDevices) return noalloc_fail(LCS_EINVAL, "device %d beyond %d", dev, kNoAllocMaxDevices);
   RedPartial* scratch = nullptr;
   int sms = 1;
   lcs_status st = noalloc_setup(dev, &scratch, &sms);

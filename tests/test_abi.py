@@ -198,3 +198,62 @@ def test_product_never_reaches_the_oracle():
         top = [n for n in tree.body if isinstance(n, (ast.Import, ast.ImportFrom))]
         assert not any("oracle" in ast.dump(n) for n in top), name  # no module-level import
         assert found <= funcs, (name, found)
+
+
+def test_overlapping_buffers_rejected_before_any_device_call(L):
+    """The stateless entry points refuse an output that shares a byte with an
+    input (or, for the one that allocates nothing, results inside a vector or
+    each other) before touching the device.  The addresses are never read."""
+    import ctypes
+
+    from paper_2407_10925_gb300 import binding
+
+    n = 2 ** 8  # (2, 2, 2): 256 states, 2048 bytes per vector
+    base = 1 << 40
+    v0, v1 = base, base + 4 * 8 * n
+
+    def noalloc(prev, out, R, arg):
+        arr = (ctypes.c_void_p * 2)(*prev)
+        return L.lcs_sweep_incr_fx_noalloc(2, 2, 4, 44, 0, arr, out, R, arg, None)
+
+    def sweep(prev, out):
+        arr = (ctypes.c_void_p * 2)(*prev)
+        return L.lcs_sweep_fx(2, 2, 4, 0, 44, arr, out, None)
+
+    ok_out, R, arg = base + 8 * 8 * n, base + 16 * 8 * n, base + 16 * 8 * n + 64
+    # an output vector that starts inside an input, or ends inside one (offset views)
+    for out in (v0 + 8, v1 - 8 * n + 8, v1 + 8 * (n - 1)):
+        assert noalloc([v0, v1], out, R, arg) == binding.LCS_EINVAL
+        assert sweep([v0, v1], out) == binding.LCS_EINVAL
+    # the 8-byte results inside a vector, or on top of each other
+    assert noalloc([v0, v1], ok_out, v0 + 8 * (n - 1), arg) == binding.LCS_EINVAL
+    assert noalloc([v0, v1], ok_out, R, ok_out + 8) == binding.LCS_EINVAL
+    assert noalloc([v0, v1], ok_out, R, R + 4) == binding.LCS_EINVAL
+    assert "overlap" in binding.lcs_bound_last_error() or "inside" in binding.lcs_bound_last_error()
+
+
+def test_binding_checks_vector_sizes_before_the_call(L):
+    """The C side receives bare pointers and cannot see a short buffer: the
+    binding checks the count and the length of every vector first."""
+    import numpy as np
+
+    from paper_2407_10925_gb300 import binding
+
+    n = 2 ** 8
+    good = [np.zeros(n, dtype=np.int64) for _ in range(2)]
+    short = np.zeros(n - 1, dtype=np.int64)
+    one = np.zeros(1, dtype=np.int64)
+    empty = np.zeros(0, dtype=np.int64)
+    cases = [
+        lambda: binding.lcs_sweep_incr_fx_noalloc(2, 2, 4, [good[0], short], good[1], one, one),
+        lambda: binding.lcs_sweep_incr_fx_noalloc(2, 2, 4, good[:1], good[1], one, one),
+        lambda: binding.lcs_sweep_incr_fx_noalloc(2, 2, 4, good, short, one, one),
+        lambda: binding.lcs_sweep_incr_fx_noalloc(2, 2, 4, good, good[1], empty, one),
+        lambda: binding.lcs_sweep_incr_fx_noalloc(2, 2, 4, good, good[1], one, empty),
+        lambda: binding.lcs_sweep_fx(2, 2, 4, [short, good[1]], good[0]),
+        lambda: binding.lcs_sweep_fx(2, 2, 4, good, short),
+        lambda: binding.lcs_sweep_fx(2, 2, 4, good + [good[0]], good[0]),
+    ]
+    for call in cases:
+        with pytest.raises(ValueError):
+            call()

@@ -224,7 +224,7 @@ def test_orbit_form_errors(lb):
         assert e.value.status == lb.LCS_EINVAL
         buf = torch.zeros(n + 2, dtype=torch.int64, device="cuda")
         with pytest.raises(lb.LcsError) as e:
-            hnd.set_start_orbit_fx([buf[1:], buf[1:]])  # 8-byte aligned only
+            hnd.set_start_orbit_fx([buf[1:n + 1], buf[1:n + 1]])  # 8-byte aligned only
         assert e.value.status == lb.LCS_EINVAL
 
 

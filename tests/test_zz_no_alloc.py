@@ -66,3 +66,40 @@ def test_noalloc_rejects_bad_arguments(env):
     with pytest.raises(lb.LcsError) as e:
         lb.lcs_sweep_incr_fx_noalloc(2, 2, 2, [v, v], v, R, R)
     assert e.value.status == 1  # output aliases an input
+    # an output that is an offset view of an input: shares all but one value
+    big = torch.zeros(17, dtype=torch.int64, device="cuda")
+    A = torch.zeros(1, dtype=torch.int64, device="cuda")
+    with pytest.raises(lb.LcsError) as e:
+        lb.lcs_sweep_incr_fx_noalloc(2, 2, 2, [big[:16], big[:16]], big[1:], R, A)
+    assert e.value.status == 1
+
+
+def test_noalloc_allocates_nothing_and_runs_on_a_caller_stream(env):
+    """The property the entry point exists for: after a first call (which may
+    load the library's device code), further calls change neither the
+    device's free memory nor PyTorch's allocations, here on a caller-owned
+    stream, and their results still equal the handle's."""
+    torch, lb = env
+    s, d, h = 2, 2, 6
+    hist = inputs.random_history(s, d, h, seed=21)
+    want_v, want_R, want_arg = _via_handle(lb, s, d, h, hist, 0)
+    dev = [torch.from_numpy(v).cuda() for v in hist]
+    out = torch.empty(s ** (d * h), dtype=torch.int64, device="cuda")
+    R = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    arg = torch.full((1,), -1, dtype=torch.int64, device="cuda")
+    stream = torch.cuda.Stream()
+    torch.cuda.synchronize()
+    lb.lcs_sweep_incr_fx_noalloc(s, d, h, dev, out, R, arg, stream=stream.cuda_stream)  # warm-up
+    stream.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0 = torch.cuda.memory_allocated()
+    for _ in range(3):
+        out.fill_(0)
+        R.fill_(-1)
+        torch.cuda.synchronize()
+        lb.lcs_sweep_incr_fx_noalloc(s, d, h, dev, out, R, arg, stream=stream.cuda_stream)
+        stream.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0
+        assert torch.cuda.memory_allocated() == alloc0
+        assert np.array_equal(out.cpu().numpy(), want_v)
+        assert (int(R.item()), int(arg.item())) == (want_R, want_arg)
