@@ -22,6 +22,7 @@ from __future__ import annotations
 import argparse
 import hashlib
 import json
+import math
 import multiprocessing as mp
 import os
 import statistics
@@ -46,6 +47,11 @@ CONFIGS = {
     "h14": dict(sigma=2, d=2, h=14),
     "h12": dict(sigma=2, d=2, h=12),
     "h8": dict(sigma=2, d=2, h=8),
+    # shapes of the general kernels (every shape without a specialised kernel)
+    # (sums of sigma^d values need fewer fractional bits than the default 44)
+    "s3d8h2": dict(sigma=3, d=8, h=2, frac_bits=36),  # 3^16 states
+    "s10d2h4": dict(sigma=10, d=2, h=4),  # 10^8 states
+    "s2d12h2": dict(sigma=2, d=12, h=2, frac_bits=36),  # 2^24 states, one warp per state
 }
 METRIC = "state-updates/s"
 FALLBACK_HBM_GBS = 6800.0
@@ -72,46 +78,121 @@ def parse():
 
 # ---------------------------------------------------------------------------
 # CPU side: the oracle on a bounded sample (spawned workers, before any CUDA use)
+#
+# The oracle's plain F (orc_F_fx) over a window of W = sigma^(d m) consecutive
+# states, aligned to W, with its arguments resident in host memory.  Such a
+# window varies only the last m letters of every string, so the states F reads
+# for one set of advanced strings lie in one aligned block of sigma^d W states
+# (the block of the window's first state advanced with the letters 0).  Each
+# argument is a full-length vector whose pages exist only where written (an
+# anonymous mapping without reservation); the blocks the window reads hold
+# seeded values like converged iterates (200 units, spread over 4).
 
 
-def _oracle_chunk(args):
-    sigma, d, h, x0, count = args
+def _sparse_vector(n):
+    """(numpy int64 view of n values, munmap callback): pages are allocated only where written"""
+    import ctypes
+
+    import numpy as np
+
+    libc = ctypes.CDLL(None, use_errno=True)
+    libc.mmap.restype = ctypes.c_void_p
+    libc.mmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_long]
+    libc.munmap.argtypes = [ctypes.c_void_p, ctypes.c_size_t]
+    prot_rw, map_private, map_anonymous, map_noreserve = 0x3, 0x02, 0x20, 0x4000
+    p = libc.mmap(None, n * 8, prot_rw, map_private | map_anonymous | map_noreserve, -1, 0)
+    if p is None or p == ctypes.c_void_p(-1).value:
+        raise OSError(ctypes.get_errno(), "mmap of the oracle's sparse argument vector failed")
+    arr = np.ctypeslib.as_array((ctypes.c_int64 * n).from_address(p))
+    return arr, (lambda: libc.munmap(p, n * 8))
+
+
+def window_arguments(sigma, d, h, x0, m, seed, vs):
+    """Fill, in the d argument vectors vs, the blocks that F reads for the window of sigma^(d m) states at x0."""
+    import itertools
+
     import numpy as np
 
     import oracle
 
-    seeds = [0x1234567 + k for k in range(d)]
+    B = sigma ** (d * (m + 1))
     one = 1 << oracle.DEFAULT_FRAC_BITS
-    bases = [(200 - k) * one for k in range(d)]
-    xs = np.arange(x0, x0 + count, dtype=np.uint64)
-    t = time.perf_counter()
-    oracle.F_generated(sigma, d, h, seeds, bases, 4 * one, xs)
-    return time.perf_counter() - t
+    rng = np.random.default_rng(seed)
+    X = oracle.decode(sigma, d, h, x0)
+    for adv in itertools.chain.from_iterable(itertools.combinations(range(d), k) for k in range(1, d + 1)):
+        Y = X.copy()
+        for j in adv:  # string j loses its head and gains the letter 0
+            Y[:-1, j] = X[1:, j]
+            Y[-1, j] = 0
+        base = oracle.encode(sigma, d, h, Y) // B * B
+        vs[len(adv) - 1][base:base + B] = (200 - len(adv)) * one + rng.integers(0, 4 * one, size=B)
 
 
-def oracle_sample(cfg, seconds_per_worker=1.5, workers=None, steps=1):
-    """Time the oracle's F on consecutive states of the workload; returns (states/s, cores, sample text)."""
+_BARRIER = None
+
+
+def _init_worker(barrier):
+    global _BARRIER
+    _BARRIER = barrier
+
+
+def _oracle_window(args):
+    """(start, end) wall-clock seconds of the oracle's F plus the increment minimum over one window.
+
+    The arguments are filled first; with `together`, every worker of the step
+    then meets at a barrier, so the timed parts of a step run side by side."""
+    sigma, d, h, x0, m, seed, together = args
+    import oracle
+
+    n = sigma ** (d * h)
+    W = sigma ** (d * m)
+    vs, frees = zip(*[_sparse_vector(n) for _ in range(d)])
+    window_arguments(sigma, d, h, x0, m, seed, vs)
+    if together:
+        _BARRIER.wait(timeout=600)
+    t0 = time.time()
+    out = oracle.F(sigma, d, h, list(vs), arith="fx", x0=x0, x1=x0 + W)
+    int((out - vs[0][x0:x0 + W]).min())
+    t1 = time.time()
+    del out
+    for f in frees:
+        f()
+    return t0, t1
+
+
+def oracle_sample(cfg, workers=None, steps=1, m=None):
+    """Time the oracle's plain F on windows of consecutive states of the workload.
+
+    Returns (per-step dicts of states and seconds on all workers, the 1-core rate, cores, sample text).
+    """
     import oracle
 
     oracle.build()
     sigma, d, h = cfg["sigma"], cfg["d"], cfg["h"]
     n = sigma ** (d * h)
     workers = workers or os.cpu_count() or 1
-    probe = min(1 << 14, n)
-    dt = _oracle_chunk((sigma, d, h, 0, probe))
-    per = max(1, min(n // workers, int(probe * seconds_per_worker / max(dt, 1e-6))))
+    if m is None:  # about a second of F per window (4^11 states for sigma = d = 2)
+        m = max(1, min(h - 1, round(22 / (d * math.log2(sigma)))))
+    W = sigma ** (d * m)
+    n_windows = n // W
     ctx = mp.get_context("spawn")
-    rates = []
-    with ctx.Pool(workers) as pool:
-        pool.map(_oracle_chunk, [(sigma, d, h, 0, 16)] * workers)  # import + build in every worker
+    barrier = ctx.Barrier(workers)
+    with ctx.Pool(workers, initializer=_init_worker, initargs=(barrier,)) as pool:
+        pool.map(_oracle_window, [(sigma, d, h, 0, 1, 0, True)] * workers, chunksize=1)  # import + build
+        a, b = pool.apply(_oracle_window, ((sigma, d, h, (n_windows // 3) * W, m, 1, False),))  # one core alone
+        t1 = b - a
+        steps_out = []
         for s in range(steps):
-            chunks = [(sigma, d, h, (i * per + s * 7919) % max(1, n - per), per) for i in range(workers)]
-            t = time.perf_counter()
-            pool.map(_oracle_chunk, chunks)
-            rates.append(workers * per / (time.perf_counter() - t))
-    sample = (f"oracle F (fixed point) at {workers} x {per} consecutive states of sigma={sigma} d={d} h={h}, "
-              f"arguments from SplitMix64 (the sweep part of one iteration; {workers} spawned processes)")
-    return rates, workers, sample
+            args = [(sigma, d, h, ((s * workers + i) * 7919 % n_windows) * W, m, 100 + s * workers + i, True)
+                    for i in range(workers)]
+            spans = pool.map(_oracle_window, args, chunksize=1)
+            steps_out.append({"states": workers * W,
+                              "seconds": max(e for _, e in spans) - min(st for st, _ in spans)})
+    sample = (f"the oracle's plain F (orc_F_fx, fixed point) and the increment minimum over {workers} windows of "
+              f"{W} consecutive states of sigma={sigma} d={d} h={h} per step, one window per spawned process, "
+              f"arguments resident in host memory (seeded values in the blocks each window reads), the "
+              f"processes starting together after filling them; 1-core figure: one window alone")
+    return steps_out, W / t1, workers, sample
 
 
 # ---------------------------------------------------------------------------
@@ -225,10 +306,11 @@ def reduce_max(x: float, dist=None, device=None) -> float:
 def run_reference(args, cfg, rank):
     if rank != 0:
         return
-    n = cfg["sigma"] ** (cfg["d"] * cfg["h"])
-    rates, cores, sample = oracle_sample(cfg, seconds_per_worker=1.0, steps=args.warmup + args.steps)
-    rates = rates[args.warmup:]
-    value = statistics.median(rates)
+    steps, rate_1core, cores, sample = oracle_sample(cfg, steps=args.warmup + args.steps)
+    timed = steps[args.warmup:]
+    states = sum(st["states"] for st in timed)
+    seconds = sum(st["seconds"] for st in timed)
+    value = states / seconds
     line = {
         "impl": "reference",
         "metric": METRIC,
@@ -237,15 +319,18 @@ def run_reference(args, cfg, rank):
         "n_gpus": args.gpus,
         "steps": args.steps,
         "warmup": args.warmup,
-        "ms_per_step": 1e3 * n * args.check_every / value,
+        "ms_per_step": 1e3 * seconds / len(timed),
         "higher_is_better": True,
         "scaling": "weak",
         "vs_baseline": None,
         "dtype": "int64",
         "data": "synthetic",
-        "config": {"workload": workload_name(cfg, args), "states": n, "sweeps_per_step": args.check_every},
+        "config": {"workload": workload_name(cfg, args), "states": cfg["sigma"] ** (cfg["d"] * cfg["h"]),
+                   "states_per_step": timed[0]["states"],
+                   "step": "one bounded sample: F and the increment minimum over one window of consecutive "
+                           "states on each host core (the GPU arm's step sweeps every state 10 times)"},
         "cpu_baseline": {"value": value, "unit": "state-updates/s", "cores": cores, "kind": "oracle",
-                         "sample": sample},
+                         "sample": sample, "value_1core": rate_1core, "value_all_cores": value},
         "e2e": {"value": value, "unit": "state-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
@@ -513,8 +598,10 @@ def main():
 
     cpu = None
     if rank == 0 and not args.no_cpu_baseline:
-        rates, cores, sample = oracle_sample(cfg, seconds_per_worker=1.5, steps=1)
-        cpu = {"value": rates[0], "unit": "state-updates/s", "cores": cores, "kind": "oracle", "sample": sample}
+        steps, rate_1core, cores, sample = oracle_sample(cfg, steps=2)
+        value = sum(st["states"] for st in steps) / sum(st["seconds"] for st in steps)
+        cpu = {"value": value, "unit": "state-updates/s", "cores": cores, "kind": "oracle", "sample": sample,
+               "value_1core": rate_1core, "value_all_cores": value}
 
     import torch
 
@@ -536,7 +623,9 @@ def main():
     # a dedicated stream: every kernel of the library and the timing events go here
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
-    hnd = lb.LcsBound(sigma, d, h, check_every=C, timing=1, symmetry=args.symmetry, stream=stream.cuda_stream)
+    K = cfg.get("frac_bits", 44)
+    hnd = lb.LcsBound(sigma, d, h, check_every=C, timing=1, symmetry=args.symmetry, frac_bits=K,
+                      stream=stream.cuda_stream)
     n = hnd.n_states
     for _ in range(args.warmup):
         hnd.iterate(C)
@@ -576,22 +665,32 @@ def main():
     e2e = None
     if not args.no_e2e and args.e2e_steps > 0:
         def e2e_run(set_start):
-            times = []
+            """the slowest step's time, and the phases of every step (host clock; each phase ends synchronised)"""
+            times, phases = [], []
             for i in range(args.e2e_steps + 1):
                 barrier()
                 torch.cuda.synchronize()
                 t0 = time.perf_counter()
-                set_start()
+                set_start()  # synchronous for host vectors
+                t1 = time.perf_counter()
                 hnd.iterate(C)
+                torch.cuda.synchronize()
+                t2 = time.perf_counter()
                 hnd.read()
                 torch.cuda.synchronize()
+                t3 = time.perf_counter()
                 if i > 0:
-                    times.append((time.perf_counter() - t0) * 1e3)
-            return reduce_max(max(times), dist, "cuda")
+                    times.append((t3 - t0) * 1e3)
+                    phases.append({"set_start_ms": (t1 - t0) * 1e3, "iterate_ms": (t2 - t1) * 1e3,
+                                   "read_ms": (t3 - t2) * 1e3})
+            return reduce_max(max(times), dist, "cuda"), phases
 
-        def entry(ms, h2d, what, host):
+        def entry(run, h2d, what, host):
+            ms, phases = run
+            rate = buffer_rate(host)
             return {"value": world * n * C / (ms / 1e3), "ms_per_step": ms, "h2d_bytes_per_step": h2d, "what": what,
-                    "host_buffer_h2d_gbs": buffer_rate(host)}
+                    "host_buffer_h2d_gbs": rate, "phases": phases,
+                    "link_ms_at_buffer_rate": h2d / (rate["median"] * 1e9) * 1e3}
 
         def buffer_rate(host):
             # the plain copy rate of this pinned buffer, 1 GiB segment by
@@ -648,7 +747,8 @@ def main():
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        with lb.LcsBound(sigma, d, h, check_every=100, symmetry=args.symmetry, stream=stream.cuda_stream) as hb:
+        with lb.LcsBound(sigma, d, h, check_every=100, symmetry=args.symmetry, frac_bits=K,
+                         stream=stream.cuda_stream) as hb:
             hb.iterate(bound_iters)
             b_rd = hb.read()[0]
         t_bound = reduce_max(time.perf_counter() - t0, dist, "cuda")

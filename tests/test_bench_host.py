@@ -107,7 +107,7 @@ def test_committed_traffic_entries_are_consistent():
 def test_reference_arm_prints_one_contract_line():
     """`bench.py --impl reference` (the oracle on the host cores, no GPU): one
     JSON line with the contract's keys, its value repeated in cpu_baseline and
-    e2e, and ms_per_step consistent with the value and the workload."""
+    e2e, and ms_per_step the measured time of the sample each step ran."""
     import subprocess
 
     env = {k: v for k, v in os.environ.items() if k not in ("RANK", "WORLD_SIZE", "LOCAL_RANK")}
@@ -127,8 +127,10 @@ def test_reference_arm_prints_one_contract_line():
     assert j["e2e"]["h2d_bytes_per_step"] == 0 and j["e2e"]["d2h_bytes_per_step"] == 0
     cfg = j["config"]
     assert cfg["states"] == 2 ** 32 and "workload" in cfg
-    want_ms = cfg["states"] * cfg["sweeps_per_step"] / j["value"] * 1e3
+    # the step is the sample it timed: ms_per_step is that time, not an extrapolation to the workload
+    want_ms = cfg["states_per_step"] / j["value"] * 1e3
     assert j["ms_per_step"] == pytest.approx(want_ms, rel=1e-6)
+    assert j["cpu_baseline"]["value_1core"] > 0 and j["cpu_baseline"]["value_all_cores"] == j["value"]
 
 
 def test_readme_lists_every_bench_config():
@@ -156,3 +158,28 @@ def test_profile_summaries_name_runnable_commands():
             assert "--clock-control none" in ln, (f, ln)
         for script in re.findall(r"python (\S+\.py)", text):
             assert os.path.exists(os.path.join(ROOT, script)), (f, script)
+
+
+@pytest.mark.parametrize("s,d,h,m", [(2, 2, 5, 2), (2, 2, 4, 1), (3, 2, 3, 1), (2, 3, 3, 1), (4, 2, 2, 1)])
+def test_cpu_baseline_window_reads_only_filled_blocks(s, d, h, m):
+    """The CPU baseline times the oracle's F over a window whose arguments exist
+    only in the blocks the window reads.  With every other value a sentinel far
+    below, F over each aligned window must not see a sentinel: its values stay
+    within the filled range (F of values near 200 units is within a unit of it)."""
+    import numpy as np
+
+    import oracle
+
+    one = 1 << oracle.DEFAULT_FRAC_BITS
+    n, W = s ** (d * h), s ** (d * m)
+    for x0 in range(0, n, W * max(1, n // W // 5)):
+        vs = [np.full(n, -(1 << 60), dtype=np.int64) for _ in range(d)]
+        bench.window_arguments(s, d, h, x0, m, 7, vs)
+        out = oracle.F(s, d, h, vs, arith="fx", x0=x0, x1=x0 + W)
+        assert out.min() >= 190 * one and out.max() <= 210 * one, x0
+
+
+def test_cpu_baseline_sample_runs():
+    steps, rate_1core, cores, sample = bench.oracle_sample({"sigma": 2, "d": 2, "h": 16}, workers=2, steps=1, m=5)
+    assert steps[0]["states"] == 2 * 4 ** 5 and steps[0]["seconds"] > 0
+    assert rate_1core > 0 and cores == 2 and "orc_F_fx" in sample
