@@ -500,3 +500,29 @@ def test_fx_to_double_rounds_down(orc):
     for a in [0, 1, -1, (1 << 53) + 1, -(1 << 53) - 1, (1 << 62) + 12345, -(1 << 62) - 3]:
         x = orc.fx_to_double_rd(a, 0)
         assert Fraction(x) <= a and Fraction(math.nextafter(x, math.inf)) > a
+
+
+def _run_arith(arith):
+    import oracle
+
+    res = oracle.run(2, 2, 8, 2000, arith=arith, check_every=0)
+    return res["iterates"][0], res["bound_rd"]
+
+
+def test_fx_tracks_f64_at_config_size():
+    """The GPU path computes in int64 fixed point (44 fractional bits, floor
+    means) and equals the oracle's fx mode bit for bit; the benchmark spec's
+    tolerance is stated against FP64.  At the config size (2,2,8) and its 2000
+    iterations, where the floor drift T 2^-44 is largest, the fx iterate stays
+    within 1e-12 relative of the f64 one (round to nearest, R5's order), the
+    two bounds agree to 1e-12, and both floor to Table 2's 0.776860."""
+    import multiprocessing as mp
+
+    with mp.get_context("spawn").Pool(2) as pool:  # the two arithmetics side by side
+        (v_fx, b_fx), (v_64, b_64) = pool.map(_run_arith, ["fx", "f64"])
+    v = v_fx.astype(np.float64) / (1 << 44)  # exact: |v| < 2^10, so fx values have < 53 significant bits
+    T = 2000
+    assert np.max(np.abs(v - v_64) / np.abs(v_64)) <= 1e-12
+    assert np.max(np.abs(v - v_64)) <= T * 2.0 ** -44 + T * 4 * np.finfo(np.float64).eps * np.max(np.abs(v_64))
+    assert abs(b_fx - b_64) <= 1e-12
+    assert floor6(b_fx) == floor6(b_64) == 0.776860
