@@ -47,6 +47,11 @@ CONFIGS = {
     "h14": dict(sigma=2, d=2, h=14),
     "h12": dict(sigma=2, d=2, h=12),
     "h8": dict(sigma=2, d=2, h=8),
+    # out of core: 32-bit offset-normalised rows, one of the three in pinned host memory
+    "h18": dict(sigma=2, d=2, h=18, frac_bits=26, outofcore=True, check=25, max_iters=800, target=0.790668),
+    "h16x": dict(sigma=2, d=2, h=16, frac_bits=26, outofcore=True, check=25, max_iters=400, target=0.789021),
+    # the same 32-bit rows, all three in device memory (h = 17: 3 x 32 GiB)
+    "h17n": dict(sigma=2, d=2, h=17, frac_bits=26, storage=1, bound_iters=400),
     # shapes of the general kernels (every shape without a specialised kernel)
     # (sums of sigma^d values need fewer fractional bits than the default 44)
     "s3d8h2": dict(sigma=3, d=8, h=2, frac_bits=36),  # 3^16 states
@@ -576,6 +581,85 @@ def run_fp32(args, cfg, world, rank, local_rank):
                           "results": results, "note": "no bound is derived from float32 iterates"}), flush=True)
 
 
+def link_rates(nbytes=1 << 32):
+    """host <-> device copy rates of a pinned buffer through PyTorch (GB/s)"""
+    import torch
+
+    host = torch.empty(nbytes // 8, dtype=torch.int64, pin_memory=True)
+    dev = torch.empty(nbytes // 8, dtype=torch.int64, device="cuda")
+    out = {}
+    for name, dst, src in (("h2d_gbs", dev, host), ("d2h_gbs", host, dev)):
+        best = 0.0
+        for _ in range(3):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            dst.copy_(src, non_blocking=True)
+            torch.cuda.synchronize()
+            best = max(best, nbytes / (time.perf_counter() - t0) / 1e9)
+        out[name] = best
+    del host, dev
+    torch.cuda.empty_cache()
+    return out
+
+
+def run_outofcore(args, cfg, world, rank, local_rank):
+    """Table 2 beyond device memory: sigma = d = 2 with 32-bit offset-normalised
+    rows, one of the three in pinned host memory, from the zero start until the
+    bound reaches the paper's printed value (checks every cfg['check'])."""
+    import torch
+
+    import paper_2407_10925_gb300 as lb
+
+    torch.cuda.set_device(local_rank)
+    H, K, C = cfg["h"], cfg["frac_bits"], cfg["check"]
+    rates = link_rates()
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    hnd = lb.LcsBound(2, 2, H, check_every=C, frac_bits=K, storage=1, host_slots=1, timing=1,
+                      stream=stream.cuda_stream)
+    t_create = time.perf_counter() - t0
+    n_stored = hnd.n_stored
+    it, bound, history, reached = 0, 0.0, [], None
+    with ClockSampler(local_rank) as clk:
+        while it < cfg["max_iters"]:
+            hnd.iterate(C)
+            it += C
+            bound = hnd.read()[0]
+            history.append((it, bound, time.perf_counter() - t0))
+            if reached is None and math.floor(bound * 1e6 + 1e-9) / 1e6 >= cfg["target"]:
+                reached = (it, time.perf_counter() - t0)
+                break
+    t_total = time.perf_counter() - t0
+    st = hnd.stats()
+    rep = hnd.report()
+    hnd.close()
+    sweep_ms = st["sweep_ms"] / max(1, st["sweep_launches"])
+    # over three sweeps the host row is written once, read whole once (as the
+    # newest input) and read in its distinct half once (as the older input)
+    link_bytes = (4 + 4 + 2) * n_stored / 3
+    line = {
+        "metric": "wall time to Table 2's printed bound out of core", "unit": "s", "value": t_total,
+        "higher_is_better": False, "n_gpus": world, "dtype": "int32 storage, int64 arithmetic",
+        "data": "the method's own iterates from the zero start",
+        "config": {"workload": f"sigma=2 d=2 h={H} ({4 ** H} states, {n_stored} stored): three 32-bit offset-normalised "
+                               f"rows of {n_stored * 4 / 2 ** 30:.0f} GiB, one in pinned host memory; {K} fractional "
+                               f"bits; a check every {C} iterations", "target": cfg["target"]},
+        "result": {"bound_rd": bound, "iterations": it, "reached_target": reached is not None,
+                   "iterations_to_target": reached[0] if reached else None,
+                   "seconds_to_target": reached[1] if reached else None, "r": rep["r"] / 2 ** K,
+                   "eps": rep["eps"] / 2 ** K, "kept_iter": rep["kept_iter"]},
+        "create_s": t_create,
+        "sweep_ms_mean": sweep_ms, "check_ms_mean": st["check_ms"] / max(1, st["check_launches"]),
+        "link": {"algorithmic_bytes_per_sweep": link_bytes, "achieved_gbs": link_bytes / (sweep_ms / 1e3) / 1e9,
+                 "copy_rates_gbs": rates},
+        "history": history, "clocks": clk.summary(),
+    }
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     cfg = CONFIGS[args.config]
@@ -594,6 +678,9 @@ def main():
         return
     if args.config == "fp32":
         run_fp32(args, cfg, world, rank, local_rank)
+        return
+    if cfg.get("outofcore"):
+        run_outofcore(args, cfg, world, rank, local_rank)
         return
 
     cpu = None
@@ -624,7 +711,8 @@ def main():
     stream = torch.cuda.Stream()
     torch.cuda.set_stream(stream)
     K = cfg.get("frac_bits", 44)
-    hnd = lb.LcsBound(sigma, d, h, check_every=C, timing=1, symmetry=args.symmetry, frac_bits=K,
+    storage = cfg.get("storage", 0)
+    hnd = lb.LcsBound(sigma, d, h, check_every=C, timing=1, symmetry=args.symmetry, frac_bits=K, storage=storage,
                       stream=stream.cuda_stream)
     n = hnd.n_states
     for _ in range(args.warmup):
@@ -670,6 +758,7 @@ def main():
             for i in range(args.e2e_steps + 1):
                 barrier()
                 torch.cuda.synchronize()
+                hnd.stats(reset=True)
                 t0 = time.perf_counter()
                 set_start()  # synchronous for host vectors
                 t1 = time.perf_counter()
@@ -681,8 +770,12 @@ def main():
                 t3 = time.perf_counter()
                 if i > 0:
                     times.append((t3 - t0) * 1e3)
+                    x = hnd.stats(reset=True)  # the library's events: copies and the kernels on their values
                     phases.append({"set_start_ms": (t1 - t0) * 1e3, "iterate_ms": (t2 - t1) * 1e3,
-                                   "read_ms": (t3 - t2) * 1e3})
+                                   "read_ms": (t3 - t2) * 1e3, "h2d_copy_ms": x["h2d_ms"],
+                                   "h2d_copy_gbs": x["h2d_bytes"] / max(x["h2d_ms"], 1e-9) / 1e6,
+                                   "transfer_kernel_ms": x["xfer_kernel_ms"], "sweep_ms": x["sweep_ms"],
+                                   "check_ms": x["check_ms"]})
             return reduce_max(max(times), dist, "cuda"), phases
 
         def entry(run, h2d, what, host):
@@ -747,7 +840,7 @@ def main():
         torch.cuda.synchronize()
         barrier()
         t0 = time.perf_counter()
-        with lb.LcsBound(sigma, d, h, check_every=100, symmetry=args.symmetry, frac_bits=K,
+        with lb.LcsBound(sigma, d, h, check_every=100, symmetry=args.symmetry, frac_bits=K, storage=storage,
                          stream=stream.cuda_stream) as hb:
             hb.iterate(bound_iters)
             b_rd = hb.read()[0]
@@ -791,6 +884,9 @@ def main():
                 "algorithmic_bytes_per_launch": per_launch_bytes,
                 "sweep_ms_per_launch": st["sweep_ms"] / max(1, st["sweep_launches"]),
                 "check_ms_per_launch": st["check_ms"] / max(1, st["check_launches"]),
+                "check": ("each check runs inside the next sweep (the first of the next step), which reads "
+                          "4 more bytes per stored state; those bytes count in the sweep's"
+                          if st["check_launches"] == 0 else "a kernel of its own per check"),
             },
             "cpu_baseline": cpu,
             "e2e": e2e,

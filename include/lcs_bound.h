@@ -102,6 +102,31 @@ typedef struct {
   void* alloc_ctx;
   /* cudaStream_t to enqueue on; NULL -> the library creates its own stream. */
   void* stream;
+  /* 0 (default): iterates stored as int64 fixed point.  1: offset-normalised
+   * 32-bit storage -- each vector holds w = v - c in int32 with one int64
+   * offset c per vector, kept on the device; half the bytes of every sweep.
+   * F is computed exactly as with int64 storage (Lemma 1's translation
+   * invariance: a mean of w + c is the mean of w plus c), so the iterates,
+   * R, E and the bound are bit for bit those of int64 storage at the same
+   * frac_bits, as long as every stored w fits in 32 bits; an output that does
+   * not sets LCS_EOVERFLOW (sticky, reported by the next read).  The offset of
+   * a new iterate is the previous iterate's value at state 0 plus the last
+   * reduced R, so every w stays within the spread of one iterate plus one
+   * step (2^(31 - frac_bits) units must hold it).  Needs sigma = d = 2,
+   * h >= 6, complement-symmetric storage, f_mode 0, keep_u 0 and
+   * frac_bits <= 30 (LCS_EUNSUPPORTED / LCS_EINVAL otherwise).  Starts and
+   * exports take and give int64 values: lcs_bound_set_start_stored_fx,
+   * lcs_bound_set_start_lift_fx, lcs_bound_export_fx, lcs_bound_export_stored_fx,
+   * lcs_bound_export; the other start forms, the orbit form, save/restore and
+   * check_vector return LCS_EUNSUPPORTED.  The start must be swap-symmetric. */
+  int storage;
+  /* 0 (default) or 1: the number of the d + 1 iterate vectors placed in
+   * pinned host memory (cudaHostAlloc, mapped) instead of device memory --
+   * the sweeps read and write that vector over the host link, so a shape
+   * whose vectors do not all fit in HBM runs out of core.  The host vector
+   * does not come from `alloc`.  Results are bit for bit those of an all-HBM
+   * handle. */
+  int host_slots;
 } lcs_bound_opts;
 
 /* Fill *opts with the defaults listed above. */
@@ -206,6 +231,18 @@ lcs_status lcs_bound_history(lcs_bound_t* hnd, lcs_bound_check_record* out, int6
  * synchronous for a host dst, asynchronous for a device dst.  The paper has
  * no counterpart of either call beyond the symmetry itself. */
 lcs_status lcs_bound_set_start_stored_fx(lcs_bound_t* hnd, const int64_t* const* v, int on_device);
+
+/* A start lifted from a shorter shape (sigma = d = 2, complement-symmetric
+ * storage; the paper's prefix truncation as a warm start): src is the stored
+ * form (4^h_from / 2 fixed-point values, states x < 4^h_from / 2) of an
+ * iterate of (2, 2, h_from), 2 <= h_from <= h, on the host (read through the
+ * staging pipeline) or the device.  The newest iterate of this handle becomes
+ * v[x] = src[x >> 2 (h - h_from)] -- each string cut to its first h_from
+ * letters -- and the older one v - r_hat (units of 2^-K).  The lift keeps the
+ * complement and swap symmetries of src.  Resets as lcs_bound_set_start_fx.
+ * Lemma 1 makes any start legitimate: the bound comes from the check.
+ * Synchronous.  No counterpart in the paper beyond the truncation itself. */
+lcs_status lcs_bound_set_start_lift_fx(lcs_bound_t* hnd, int h_from, const int64_t* src, int on_device, int64_t r_hat);
 lcs_status lcs_bound_export_stored_fx(lcs_bound_t* hnd, int k, int64_t* dst, int on_device);
 
 /* The ORBIT FORM (sigma = d = 2, complement-symmetric storage, h >= 6; other
@@ -270,9 +307,9 @@ lcs_status lcs_bound_export_fx(lcs_bound_t* hnd, int k, int64_t* dst, int on_dev
  * Synchronises the stream. */
 lcs_status lcs_bound_check_vector(lcs_bound_t* hnd, const int64_t* u_dev, int64_t R, int64_t* E_out);
 
-/* Timing of the enqueued sweep and check kernels (needs opts.timing = 1).
- * Synchronises the stream.  Counts and milliseconds since creation or the
- * last reset. */
+/* Timing of the enqueued sweep and check kernels and of the host transfers
+ * (needs opts.timing = 1).  Synchronises the stream.  Counts and milliseconds
+ * since creation or the last reset. */
 typedef struct {
   int64_t sweep_launches;
   double sweep_ms;
@@ -281,6 +318,14 @@ typedef struct {
   int64_t kernel_launches; /* every kernel this handle enqueued */
   uint64_t sweep_bytes;    /* algorithmic bytes of all sweeps: 8 (d+1) per stored state */
   uint64_t check_bytes;    /* algorithmic bytes of all checks: 8 per stored state */
+  /* host transfers of set_start / export: the copies' device time and bytes in
+   * each direction, and the time of the kernels that convert, unpack or pack
+   * the transferred values (summed per operation; copies and kernels overlap) */
+  double h2d_ms;
+  uint64_t h2d_bytes;
+  double d2h_ms;
+  uint64_t d2h_bytes;
+  double xfer_kernel_ms;
 } lcs_bound_stats_t;
 lcs_status lcs_bound_stats(lcs_bound_t* hnd, lcs_bound_stats_t* out, int reset);
 
@@ -338,6 +383,10 @@ typedef struct {
   int mode;               /* 0: one persistent launch; 1: concurrent single-instance kernels */
   double persistent_ms_per_iter;  /* the autotuner's timings of both modes */
   double concurrent_ms_per_iter;
+  int graph_captured;     /* 1 once a persistent launch was captured in a CUDA graph and instantiated */
+  int min_ctas_per_sm;    /* the persistent kernel's register budget the autotuner chose: 2 (128
+                           * registers a thread) or 4 (64, the heaviest bodies spill) CTAs per SM */
+  int64_t graph_replays;  /* iterate calls that replayed a captured graph */
 } lcs_bound_batch_info_t;
 lcs_status lcs_bound_batch_info(lcs_bound_t* hnd, lcs_bound_batch_info_t* out);
 /* Force the execution mode of a batch before its first iteration (LCS_EINVAL
@@ -369,6 +418,13 @@ typedef struct lcs_mlp lcs_mlp_t;
 int64_t lcs_mlp_param_count(void);
 /* random initialisation (uniform +-1/sqrt(fan-in), SplitMix64 stream `seed`) */
 lcs_status lcs_mlp_create(uint64_t seed, lcs_mlp_t** out);
+/* The same with a device allocator for every buffer of the network (as in
+ * lcs_bound_opts: alloc returns a device pointer aligned to 256 bytes or NULL;
+ * NULL alloc -> cudaMalloc / cudaFree).  A failed allocation gives LCS_ENOMEM:
+ * at creation with *out = NULL and everything already allocated freed; later
+ * (the training buffers, the inference table) with the handle still valid. */
+lcs_status lcs_mlp_create_with_allocator(uint64_t seed, void* (*alloc)(size_t bytes, void* ctx),
+                                         void (*free)(void* ptr, void* ctx), void* alloc_ctx, lcs_mlp_t** out);
 lcs_status lcs_mlp_get_params(lcs_mlp_t* m, float* host_out);
 lcs_status lcs_mlp_set_params(lcs_mlp_t* m, const float* host_in);
 /* mean squared error over n host rows (states, their h, targets) and its

@@ -36,6 +36,8 @@ class lcs_bound_opts(ctypes.Structure):
         ("free", _FREE),
         ("alloc_ctx", ctypes.c_void_p),
         ("stream", ctypes.c_void_p),
+        ("storage", ctypes.c_int),
+        ("host_slots", ctypes.c_int),
     ]
 
 
@@ -63,6 +65,11 @@ class lcs_bound_stats_t(ctypes.Structure):
         ("kernel_launches", ctypes.c_int64),
         ("sweep_bytes", ctypes.c_uint64),
         ("check_bytes", ctypes.c_uint64),
+        ("h2d_ms", ctypes.c_double),
+        ("h2d_bytes", ctypes.c_uint64),
+        ("d2h_ms", ctypes.c_double),
+        ("d2h_bytes", ctypes.c_uint64),
+        ("xfer_kernel_ms", ctypes.c_double),
     ]
 
 
@@ -90,6 +97,9 @@ class lcs_bound_batch_info_t(ctypes.Structure):
         ("mode", ctypes.c_int),
         ("persistent_ms_per_iter", ctypes.c_double),
         ("concurrent_ms_per_iter", ctypes.c_double),
+        ("graph_captured", ctypes.c_int),
+        ("min_ctas_per_sm", ctypes.c_int),
+        ("graph_replays", ctypes.c_int64),
     ]
 
 
@@ -122,6 +132,7 @@ def lib():
                 "lcs_bound_set_start": [vp, vp, i32],
                 "lcs_bound_set_start_fx": [vp, vp, i32],
                 "lcs_bound_set_start_stored_fx": [vp, vp, i32],
+                "lcs_bound_set_start_lift_fx": [vp, i32, vp, i32, i64],
                 "lcs_bound_export_stored_fx": [vp, i32, vp, i32],
                 "lcs_bound_orbit_size": [vp, P(u64)],
                 "lcs_bound_set_start_orbit_fx": [vp, vp, i32],
@@ -142,6 +153,7 @@ def lib():
                 "lcs_bound_batch_set_mode": [vp, i32],
                 "lcs_bound_batch_set_spin_budget": [vp, i64],
                 "lcs_mlp_create": [u64, P(vp)],
+                "lcs_mlp_create_with_allocator": [u64, _ALLOC, _FREE, vp, P(vp)],
                 "lcs_mlp_get_params": [vp, vp],
                 "lcs_mlp_set_params": [vp, vp],
                 "lcs_mlp_gradient": [vp, i32, vp, vp, vp, P(ctypes.c_float), vp],
@@ -347,6 +359,13 @@ def lcs_bound_set_start_stored_fx(hnd, vs):
     _require_vectors(vs, *_vectors_for(hnd, "stored"), "lcs_bound_set_start_stored_fx")
     arr, on_dev = _vec_array(vs, np.int64)
     _check(lib().lcs_bound_set_start_stored_fx(hnd, arr, on_dev), "lcs_bound_set_start_stored_fx")
+
+
+def lcs_bound_set_start_lift_fx(hnd, h_from: int, src, r_hat: int):
+    """Start from the stored form of a shorter shape's iterate (sigma = d = 2): v[x] = src[x >> 2 (h - h_from)]."""
+    _require_len(src, 4 ** h_from // 2, "lcs_bound_set_start_lift_fx: src")
+    p, on_dev = _ptr_and_kind(src, np.int64)
+    _check(lib().lcs_bound_set_start_lift_fx(hnd, h_from, p, on_dev, int(r_hat)), "lcs_bound_set_start_lift_fx")
 
 
 def lcs_bound_export_stored_fx(hnd, k: int, out):
@@ -615,9 +634,15 @@ def lcs_mlp_param_count() -> int:
 class LcsMlp:
     """The warm-start network (lcs_mlp_*); every computation runs in the library's kernels."""
 
-    def __init__(self, seed=1):
+    def __init__(self, seed=1, allocator=None):
+        """allocator: an object with ctypes callbacks .alloc and .free (e.g. TorchAllocator), or None"""
         self.hnd = ctypes.c_void_p()
-        _check(lib().lcs_mlp_create(seed, ctypes.byref(self.hnd)), "lcs_mlp_create")
+        self._allocator = allocator  # the callbacks must outlive the handle
+        if allocator is None:
+            _check(lib().lcs_mlp_create(seed, ctypes.byref(self.hnd)), "lcs_mlp_create")
+        else:
+            _check(lib().lcs_mlp_create_with_allocator(seed, allocator.alloc, allocator.free, None,
+                                                       ctypes.byref(self.hnd)), "lcs_mlp_create_with_allocator")
         self.n_params = lcs_mlp_param_count()
 
     def close(self):
@@ -711,11 +736,12 @@ class LcsBound:
     """Owns one handle; see ``include/lcs_bound.h`` for the semantics."""
 
     def __init__(self, sigma, d, h, *, check_every=0, r_mode=0, f_mode=0, frac_bits=44, keep_u=0, symmetry=1,
-                 timing=0, stream=None, torch_alloc=False):
+                 timing=0, stream=None, torch_alloc=False, storage=0, host_slots=0):
         self.sigma, self.d, self.h = sigma, d, h
         o = lcs_bound_default_opts()
         o.check_every, o.r_mode, o.f_mode, o.frac_bits = check_every, r_mode, f_mode, frac_bits
         o.keep_u, o.symmetry, o.timing = keep_u, symmetry, timing
+        o.storage, o.host_slots = storage, host_slots
         self._alloc = None
         if torch_alloc:
             self._alloc = TorchAllocator()
@@ -773,6 +799,9 @@ class LcsBound:
 
     def set_start_stored_fx(self, vs):
         lcs_bound_set_start_stored_fx(self.hnd, vs)
+
+    def set_start_lift_fx(self, h_from, src, r_hat):
+        lcs_bound_set_start_lift_fx(self.hnd, h_from, src, r_hat)
 
     def export_stored_fx(self, k=0, out=None):
         if out is None:

@@ -301,7 +301,11 @@ __device__ __forceinline__ void run_phase(BatchCtl* ctl, unsigned long long phas
   __syncthreads();
 }
 
-__global__ void __launch_bounds__(kBlock, 2)
+// MINB = CTAs per SM the compiler must fit: 2 lets every kind's body keep its
+// registers (128); 4 caps them at 64 (the heaviest bodies spill) for twice the
+// warps in flight.  The autotuner times both.
+template <int MINB>
+__global__ void __launch_bounds__(kBlock, MINB)
     batch_kernel(const BatchInst* __restrict__ insts, int n_inst, unsigned long long total_items, long long n_iters,
                  int check_every, int r_mode, long long one, BatchCtl* ctl) {
   __shared__ BatchInst si[kMaxBatch];
@@ -399,6 +403,9 @@ struct BatchState {
   std::vector<void*> owned;
   std::map<long long, cudaGraphExec_t> graphs;
   bool use_graph;
+  long long graph_replays;  // launches that replayed a captured graph
+  int variant;              // persistent kernel: 0 = batch_kernel<2>, 1 = batch_kernel<4>
+  int max_grid[2];          // resident CTAs of each variant
   long long spin_budget;
   int tune_grid_choice, tune_units_choice;
   double tuned_ms;
@@ -608,7 +615,8 @@ static lcs_status launch_block(BatchState* B, cudaStream_t s, long long n_iters)
   attr[0].val.cooperative = 1;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  B_CUDA(cudaLaunchKernelExC(&cfg, (const void*)batch_kernel, args));
+  const void* fn = B->variant ? (const void*)batch_kernel<4> : (const void*)batch_kernel<2>;
+  B_CUDA(cudaLaunchKernelExC(&cfg, fn, args));
   B->launches++;
   return LCS_OK;
 }
@@ -648,6 +656,7 @@ lcs_status batch_iterate(BatchState* B, cudaStream_t s, long long n_iters) {
     if (B->use_graph) {
       B_CUDA(cudaGraphLaunch(it->second, s));
       B->launches++;
+      B->graph_replays++;
       B->iter_done_host += n_iters;
       return LCS_OK;
     }
@@ -660,11 +669,11 @@ lcs_status batch_iterate(BatchState* B, cudaStream_t s, long long n_iters) {
 
 // autotuner: time a few iterations of each launch shape from the zero start,
 // keep the fastest, then return every vector to the zero start
-static lcs_status autotune(BatchState* B, cudaStream_t s, int max_grid, int sms) {
-  const int grid_choices[] = {sms, 2 * sms};
+static lcs_status autotune(BatchState* B, cudaStream_t s, int sms) {
+  const int grid_choices[] = {sms, 2 * sms, 4 * sms};
   const int unit_choices[] = {2, 4};
   double best = 1e30;
-  int bg = max_grid, bu = 1;
+  int bg = B->max_grid[0], bu = 1, bv = 0;
   cudaEvent_t e0, e1;
   B_CUDA(cudaEventCreate(&e0));
   B_CUDA(cudaEventCreate(&e1));
@@ -672,11 +681,14 @@ static lcs_status autotune(BatchState* B, cudaStream_t s, int max_grid, int sms)
   B->use_graph = false;
   // short probes: the candidates differ by far more than the noise of 4 iterations
   const long long probe_iters = 4;
+  for (int var = 0; var < 2; ++var)
   for (int gc : grid_choices) {
-    const int grid = std::min(gc, max_grid);
+    if (gc > B->max_grid[var] && gc != sms) continue;  // not resident: the cooperative launch would fail
+    const int grid = std::min(gc, B->max_grid[var]);
     for (int uc : unit_choices) {
       layout_items(B, uc);
       B->grid = grid;
+      B->variant = var;
       B_CUDA(cudaMemcpyAsync(B->d_inst, B->inst.data(), sizeof(BatchInst) * B->n, cudaMemcpyHostToDevice, s));
       lcs_status st = reset_zero(B, s);
       if (st) return st;
@@ -689,11 +701,12 @@ static lcs_status autotune(BatchState* B, cudaStream_t s, int max_grid, int sms)
       B_CUDA(cudaEventSynchronize(e1));
       float ms = 0;
       B_CUDA(cudaEventElapsedTime(&ms, e0, e1));
-      if (ms < best) best = ms, bg = grid, bu = uc;
+      if (ms < best) best = ms, bg = grid, bu = uc, bv = var;
     }
   }
   B->use_graph = saved_graph;
   B->grid = bg;
+  B->variant = bv;
   B->tune_grid_choice = bg;
   B->tune_units_choice = bu;
   B->ms_persistent = best / (double)probe_iters;
@@ -822,21 +835,25 @@ lcs_status batch_create(int n, const int (*shapes)[3], const lcs_bound_opts& o, 
     batch_destroy(B);
     return bfail(LCS_ENOMEM, "batch control");
   }
-  int per_sm = 0;
-  B_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, (const void*)batch_kernel, kBlock, 0));
-  if (per_sm < 1) {
-    batch_destroy(B);
-    return bfail(LCS_ECUDA, "the batch kernel cannot be resident");
+  for (int var = 0; var < 2; ++var) {
+    int per_sm = 0;
+    const void* fn = var ? (const void*)batch_kernel<4> : (const void*)batch_kernel<2>;
+    B_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, fn, kBlock, 0));
+    if (per_sm < 1) {
+      batch_destroy(B);
+      return bfail(LCS_ECUDA, "the batch kernel cannot be resident");
+    }
+    B->max_grid[var] = per_sm * sms;
   }
-  const int max_grid = per_sm * sms;
   layout_items(B, 1);
-  B->grid = max_grid;
+  B->variant = 0;
+  B->grid = B->max_grid[0];
   lcs_status st = conc_setup(B, sms);
   if (st) {
     batch_destroy(B);
     return st;
   }
-  st = autotune(B, s, max_grid, sms);
+  st = autotune(B, s, sms);
   if (st) {
     batch_destroy(B);
     return st;
@@ -901,12 +918,16 @@ int batch_size(const BatchState* B) { return B->n; }
 int batch_d(const BatchState* B, int i) { return B->d[i]; }
 
 void batch_tuning(const BatchState* B, int* grid, int* units, double* ms, long long* launches, int* graph, int* mode,
-                  double* ms_persistent, double* ms_concurrent) {
+                  double* ms_persistent, double* ms_concurrent, int* graph_captured, long long* graph_replays,
+                  int* min_ctas_per_sm) {
   *grid = B->tune_grid_choice;
   *units = B->tune_units_choice;
   *ms = B->tuned_ms;
   *launches = B->launches;
   *graph = (B->mode == 0 && B->use_graph) ? 1 : 0;
+  *graph_captured = B->graphs.empty() ? 0 : 1;
+  *graph_replays = B->graph_replays;
+  *min_ctas_per_sm = B->variant ? 4 : 2;
   *mode = B->mode;
   *ms_persistent = B->ms_persistent;
   *ms_concurrent = B->ms_concurrent;

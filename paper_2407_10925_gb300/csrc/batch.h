@@ -21,7 +21,8 @@ const long long* batch_vector(BatchState* B, cudaStream_t s, int i, int k, unsig
 lcs_status batch_set_spin_budget(BatchState* B, cudaStream_t s, long long cycles);
 lcs_status batch_clear_status(BatchState* B, cudaStream_t s);
 void batch_tuning(const BatchState* B, int* grid, int* units, double* ms, long long* launches, int* graph, int* mode,
-                  double* ms_persistent, double* ms_concurrent);
+                  double* ms_persistent, double* ms_concurrent, int* graph_captured, long long* graph_replays,
+                  int* min_ctas_per_sm);
 lcs_status batch_set_mode(BatchState* B, cudaStream_t s, int mode);
 int batch_size(const BatchState* B);
 int batch_d(const BatchState* B, int i);
@@ -40,6 +41,9 @@ void launch_swap_check_d2s(int sigma, const long long* v, unsigned long long n, 
 
 // provided by kernels_rt.cu: the general kernels (any d, full storage, f_mode 0)
 const KernelSet* kernels_rt(int sigma);
+// provided by kernels_s2d2.cu: the sigma = d = 2 swap-aware sweep over
+// offset-normalised 32-bit storage
+const KernelSet* kernels_s2d2_narrow();
 unsigned long long rt_work_items(int sigma, int d, unsigned long long n_states, unsigned long long n_tail);
 
 // provided by kernels_orbit.cu (sigma = d = 2 orbit form)

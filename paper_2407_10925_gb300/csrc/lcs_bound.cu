@@ -179,15 +179,18 @@ __global__ void ingest_kernel(const void* __restrict__ src, unsigned long long o
   }
 }
 
-// out[i] = value of state off+i (mirrored from the stored half when needed)
-template <bool TO_DOUBLE>
-__global__ void export_kernel(const long long* __restrict__ src, unsigned long long off, unsigned long long len,
+// out[i] = value of state off+i (mirrored from the stored half when needed).
+// With offset-normalised 32-bit storage (T = int) the vector's offset, read
+// from the device, is added back.
+template <bool TO_DOUBLE, class T = long long>
+__global__ void export_kernel(const T* __restrict__ src, unsigned long long off, unsigned long long len,
                               unsigned long long n_stored, unsigned long long n_total, double scale,
-                              void* __restrict__ out) {
+                              void* __restrict__ out, const long long* offs = nullptr, int slot = 0) {
+  const long long c = sizeof(T) == 4 ? offs[slot] : 0;
   for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < len;
        i += (unsigned long long)gridDim.x * blockDim.x) {
     const unsigned long long g = off + i;
-    const long long q = src[g < n_stored ? g : n_total - 1 - g];
+    const long long q = (long long)src[g < n_stored ? g : n_total - 1 - g] + c;
     if constexpr (TO_DOUBLE)
       static_cast<double*>(out)[i] = __ll2double_rn(q) * scale;
     else
@@ -211,21 +214,81 @@ __global__ void maxabs_kernel(const long long* __restrict__ v, unsigned long lon
 // exchanges the two bits of every position in the interleaved index; a swapped
 // index in the upper half is read through the complement symmetry.  A warp's
 // swapped indices fall in one 32-value block, so both reads are coalesced.
-__global__ void maxabs_swap_check_kernel(const long long* __restrict__ v, unsigned long long n_stored,
-                                         unsigned long long n_total, DevState* st) {
+template <class T = long long>
+__global__ void maxabs_swap_check_kernel(const T* __restrict__ v, unsigned long long n_stored,
+                                         unsigned long long n_total, DevState* st, const long long* offs = nullptr,
+                                         int slot = 0) {
+  const long long c = sizeof(T) == 4 ? offs[slot] : 0;  // 32-bit storage: the swap test needs no offset
   long long m = 0;
   bool bad = false;
   for (unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; x < n_stored;
        x += (unsigned long long)gridDim.x * blockDim.x) {
-    const long long a = v[x];
+    const long long a = (long long)v[x] + c;
     m = max(m, a == LLONG_MIN ? LLONG_MAX : (a < 0 ? -a : a));
     unsigned long long y = ((x >> 1) & 0x5555555555555555ull) | ((x & 0x5555555555555555ull) << 1);
     if (y >= n_stored) y = n_total - 1 - y;
-    bad |= v[y] != a;
+    bad |= (long long)v[y] + c != a;
   }
   for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&st->maxabs, m);
   if (bad) atomicExch((unsigned long long*)&st->swap_bad, 1ull);
+}
+
+// dst[i] = src[i] - c as 32-bit values (offset-normalised storage); a value
+// outside 32 bits sets the overflow status; max |src| goes to st->maxabs
+__global__ void narrow_kernel(const long long* __restrict__ src, int* __restrict__ dst, unsigned long long n,
+                              long long c, DevState* st) {
+  long long m = 0;
+  bool bad = false;
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x) {
+    const long long a = src[i], w = a - c;
+    bad |= w < INT_MIN || w > INT_MAX;
+    dst[i] = (int)w;
+    m = max(m, a == LLONG_MIN ? LLONG_MAX : (a < 0 ? -a : a));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&st->maxabs, m);
+  if (bad) atomicExch((unsigned long long*)&st->status, (unsigned long long)LCS_EOVERFLOW);
+}
+
+// dst[i] = src[i] + offs[slot] (32-bit storage back to fixed-point values)
+__global__ void widen_kernel(const int* __restrict__ src, long long* __restrict__ dst, unsigned long long n,
+                             const long long* offs, int slot) {
+  const long long c = offs[slot];
+  for (unsigned long long i = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; i < n;
+       i += (unsigned long long)gridDim.x * blockDim.x)
+    dst[i] = (long long)src[i] + c;
+}
+
+__global__ void set_offset_kernel(long long* offs, int slot, long long c) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) offs[slot] = c;
+}
+
+// The prefix lift of a start: states [lo, hi) of the two newest rows from the
+// source values src[0, len) holding states from src_off on of the shorter
+// shape (sigma = d = 2): state x takes the value of state x >> 2s, its strings
+// cut to their first h - s letters.  newest = value - sub_newest, older =
+// value - sub_older; 32-bit rows flag a value outside 32 bits.  max |value|
+// goes to st->maxabs.
+template <class T>
+__global__ void lift_kernel(const long long* __restrict__ src, unsigned long long src_off, int s2,
+                            unsigned long long lo, unsigned long long hi, T* __restrict__ newest, T* __restrict__ older,
+                            long long sub_newest, long long sub_older, DevState* st) {
+  long long m = 0;
+  bool bad = false;
+  for (unsigned long long x = lo + (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x; x < hi;
+       x += (unsigned long long)gridDim.x * blockDim.x) {
+    const long long a = src[(x >> s2) - src_off];
+    const long long wn = a - sub_newest, wo = a - sub_older;
+    if (sizeof(T) == 4) bad |= wn < INT_MIN || wn > INT_MAX || wo < INT_MIN || wo > INT_MAX;
+    newest[x] = (T)wn;
+    older[x] = (T)wo;
+    m = max(m, a == LLONG_MIN ? LLONG_MAX : (a < 0 ? -a : a));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0 && m > 0) atomicMax(&st->maxabs, m);
+  if (bad) atomicExch((unsigned long long*)&st->status, (unsigned long long)LCS_EOVERFLOW);
 }
 
 __global__ void init_state_kernel(DevState* st) {
@@ -254,16 +317,35 @@ struct lcs_bound {
   const KernelSet* ks;       // kernels for the storage scheme (complement-symmetric or full)
   const KernelSet* ks_swap;  // kernels that also use the string swap / permutations (d = 2, 3)
   bool swap_ok;              // the live iterates are swap-symmetric: ks_swap may run
-  long long* ring[kMaxD + 1];
+  long long* ring[kMaxD + 1];  // element type: long long, or int with narrow storage
   int newest;  // ring slot of the newest iterate
+  // opts.storage = 1: 32-bit offset-normalised rows, offs[slot] their offsets
+  // (device); elem = bytes per stored value
+  int narrow;
+  size_t elem;
+  long long* offs;
+  // opts.host_slots: the ring rows placed in pinned host memory (read and
+  // written by the kernels over the host link); host_base = their allocations
+  void* host_base[kMaxD + 1];
   long long* ubuf;
   DevState* dstate;
   RedPartial* partials;
   CheckRecord* hist;               // the check history (kHistCap records)
   unsigned long long* hist_count;  // checks recorded since creation or the last start
   int grid_sweep, grid_check, grid_sweep_swap, grid_check_swap, n_partials;
-  void* staging;  // device staging for host transfers
-  size_t staging_bytes;
+  // the check of a checked iteration may wait for the next sweep, which then
+  // evaluates it in the same pass (KernelSet::sweep_check): pending_check marks
+  // an iteration whose R is on the device but whose check has not run
+  int grid_fused;
+  RedPartial* check_partials;
+  bool pending_check;
+  long long pending_iter;
+  // host transfers: a stream for the copies and two staging buffers, so the
+  // copy of one piece overlaps the kernel that converts the previous one
+  cudaStream_t xstream;
+  void* stage[2];
+  cudaEvent_t stage_ready[2], stage_free[2], xsync;
+  bool stage_recorded[2];  // stage_free[i] marks the end of the last use of stage[i]
   long long iters_done;
   double vbound;  // upper bound of max |v| over the live iterates, in units of 2^-K
   long long one;
@@ -271,6 +353,10 @@ struct lcs_bound {
   // timing
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> sweep_ev, check_ev;
   double sweep_ms, check_ms;
+  // transfer timing: kXferH2D, kXferD2H (copies), kXferKernel (kernels moving transferred values)
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> xfer_ev[3];
+  double xfer_ms[3];
+  unsigned long long h2d_bytes, d2h_bytes;
   long long sweep_n, check_n, launches;
   unsigned long long sweep_bytes, check_bytes;
   int last_check_grid;
@@ -341,6 +427,8 @@ lcs_status lcs_bound_default_opts(lcs_bound_opts* o) {
   o->keep_u = 0;
   o->symmetry = 1;
   o->timing = 0;
+  o->storage = 0;
+  o->host_slots = 0;
   return LCS_OK;
 }
 
@@ -372,14 +460,30 @@ void lcs_bound_destroy(lcs_bound_t* H) {
   if (H->stream) cudaStreamSynchronize(H->stream);
   for (auto& e : H->sweep_ev) cudaEventDestroy(e.first), cudaEventDestroy(e.second);
   for (auto& e : H->check_ev) cudaEventDestroy(e.first), cudaEventDestroy(e.second);
+  for (auto& v : H->xfer_ev)
+    for (auto& e : v) cudaEventDestroy(e.first), cudaEventDestroy(e.second);
+  if (H->xstream) {
+    cudaStreamSynchronize(H->xstream);
+    cudaStreamDestroy(H->xstream);
+    for (int i = 0; i < 2; ++i) cudaEventDestroy(H->stage_ready[i]), cudaEventDestroy(H->stage_free[i]);
+    cudaEventDestroy(H->xsync);
+  }
   if (H->batch) batch_destroy(H->batch);
-  for (int k = 0; k <= H->d; ++k) dev_free(H, H->ring[k]);
+  for (int k = 0; k <= H->d; ++k) {
+    if (H->host_base[k])
+      cudaFreeHost(H->host_base[k]);
+    else
+      dev_free(H, H->ring[k]);
+  }
+  dev_free(H, H->offs);
+  dev_free(H, H->check_partials);
   dev_free(H, H->ubuf);
   dev_free(H, H->dstate);
   dev_free(H, H->partials);
   dev_free(H, H->hist);
   dev_free(H, H->hist_count);
-  dev_free(H, H->staging);
+  dev_free(H, H->stage[0]);
+  dev_free(H, H->stage[1]);
   if (H->own_stream && H->stream) cudaStreamDestroy(H->stream);
   delete H;
 }
@@ -399,6 +503,15 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   if (opts.check_every < 0) return fail(LCS_EINVAL, "check_every %d", opts.check_every);
   if (opts.f_mode != 0 && opts.f_mode != 1) return fail(LCS_EINVAL, "f_mode %d", opts.f_mode);
   if (opts.alloc && !opts.free) return fail(LCS_EINVAL, "alloc given without free");
+  if (opts.storage != 0 && opts.storage != 1) return fail(LCS_EINVAL, "storage %d", opts.storage);
+  if (opts.host_slots < 0 || opts.host_slots > 1) return fail(LCS_EINVAL, "host_slots %d outside 0..1", opts.host_slots);
+  if (opts.storage == 1) {
+    if (sigma != 2 || d != 2 || h < 6 || !opts.symmetry || opts.f_mode != 0)
+      return fail(LCS_EUNSUPPORTED,
+                  "32-bit storage needs sigma = d = 2, h >= 6, complement-symmetric storage and f_mode 0");
+    if (opts.keep_u) return fail(LCS_EUNSUPPORTED, "32-bit storage does not retain u (keep_u)");
+    if (opts.frac_bits > 30) return fail(LCS_EINVAL, "32-bit storage needs frac_bits <= 30 (got %d)", opts.frac_bits);
+  }
   // state count below 2^40
   unsigned long long n = 1;
   for (int i = 0; i < d * h; ++i) {
@@ -422,6 +535,7 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
       ks_swap = find_kernels(sigma, d, 3);
   }
   if (d == 3 && sigma == 2 && sym && h >= d3s_min_h() && h <= d3s_max_h()) ks_swap = find_kernels(sigma, d, 4, opts.f_mode);
+  if (opts.storage == 1) ks = ks_swap = kernels_s2d2_narrow();  // the swap-aware sweep only
 
   lcs_bound* H = new (std::nothrow) lcs_bound();
   if (!H) return fail(LCS_ENOMEM, "host allocation");
@@ -440,6 +554,8 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   H->swap_ok = ks_swap != nullptr;  // the zero start is swap-symmetric
   H->one = 1ll << opts.frac_bits;
   H->newest = d - 1;
+  H->narrow = opts.storage == 1;
+  H->elem = H->narrow ? sizeof(int) : sizeof(long long);
 
   cudaError_t e = cudaGetDevice(&H->device);
   if (e != cudaSuccess) {
@@ -475,10 +591,30 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
     H->grid_sweep_swap = grid_for(ks_swap->sweep_fn, sms, tiles * kBlock);
     H->grid_check_swap = grid_for(ks_swap->check_fn, sms, tiles * kBlock);
     H->n_partials = std::max(H->n_partials, std::max(H->grid_sweep_swap, H->grid_check_swap));
+    if (ks_swap->sweep_check) {
+      H->grid_fused = grid_for(ks_swap->sweep_check_fn, sms, tiles * kBlock);
+      H->n_partials = std::max(H->n_partials, H->grid_fused);
+    }
   }
 
-  const size_t vbytes = (size_t)H->n_stored * sizeof(long long);
+  const size_t vbytes = (size_t)H->n_stored * H->elem;
   for (int k = 0; k <= d; ++k) {
+    if (k >= d + 1 - opts.host_slots) {
+      // a row in pinned host memory, mapped into the device's address space
+      void* hp = nullptr;
+      void* dp = nullptr;
+      e = cudaHostAlloc(&hp, vbytes, cudaHostAllocPortable | cudaHostAllocMapped);
+      if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dp, hp, 0);
+      if (e != cudaSuccess) {
+        cudaGetLastError();
+        if (hp) cudaFreeHost(hp);
+        lcs_bound_destroy(H);
+        return fail(LCS_ENOMEM, "iterate vector %d in pinned host memory (%zu bytes)", k, vbytes);
+      }
+      H->host_base[k] = hp;
+      H->ring[k] = (long long*)dp;
+      continue;
+    }
     H->ring[k] = (long long*)dev_alloc(H, vbytes);
     if (!H->ring[k]) {
       lcs_bound_destroy(H);
@@ -499,6 +635,25 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   if (!H->dstate || !H->partials || !H->hist || !H->hist_count) {
     lcs_bound_destroy(H);
     return fail(LCS_ENOMEM, "state and reduction scratch");
+  }
+  if (ks_swap && ks_swap->sweep_check) {
+    H->check_partials = (RedPartial*)dev_alloc(H, sizeof(RedPartial) * (size_t)H->n_partials);
+    if (!H->check_partials) {
+      lcs_bound_destroy(H);
+      return fail(LCS_ENOMEM, "partials of the fused check");
+    }
+  }
+  if (H->narrow) {
+    H->offs = (long long*)dev_alloc(H, sizeof(long long) * (size_t)(kMaxD + 1));
+    if (!H->offs) {
+      lcs_bound_destroy(H);
+      return fail(LCS_ENOMEM, "offsets of the 32-bit rows");
+    }
+    e = cudaMemsetAsync(H->offs, 0, sizeof(long long) * (size_t)(kMaxD + 1), H->stream);
+    if (e != cudaSuccess) {
+      lcs_bound_destroy(H);
+      return fail(LCS_ECUDA, "cudaMemsetAsync: %s", cudaGetErrorString(e));
+    }
   }
   e = cudaMemsetAsync(H->hist_count, 0, sizeof(unsigned long long), H->stream);
   if (e != cudaSuccess) {
@@ -561,6 +716,17 @@ static void fold_events(lcs_bound* H) {
   }
   H->sweep_ev.clear();
   H->check_ev.clear();
+  for (int c = 0; c < 3; ++c) {
+    for (auto& e : H->xfer_ev[c]) {
+      float ms = 0;
+      cudaEventSynchronize(e.second);
+      cudaEventElapsedTime(&ms, e.first, e.second);
+      H->xfer_ms[c] += ms;
+      cudaEventDestroy(e.first);
+      cudaEventDestroy(e.second);
+    }
+    H->xfer_ev[c].clear();
+  }
 }
 
 static lcs_status timed_begin(lcs_bound* H, cudaEvent_t* a) {
@@ -577,6 +743,27 @@ static lcs_status timed_end(lcs_bound* H, cudaEvent_t a, bool sweep) {
   LCS_CUDA(cudaEventRecord(b, H->stream));
   (sweep ? H->sweep_ev : H->check_ev).emplace_back(a, b);
   if (H->sweep_ev.size() + H->check_ev.size() > 8192) fold_events(H);
+  return LCS_OK;
+}
+
+enum { kXferH2D = 0, kXferD2H = 1, kXferKernel = 2 };
+
+// events around one transfer operation on stream s (opts.timing only)
+static lcs_status xfer_begin(lcs_bound* H, cudaStream_t s, cudaEvent_t* a) {
+  *a = nullptr;
+  if (!H->opts.timing) return LCS_OK;
+  LCS_CUDA(cudaEventCreate(a));
+  LCS_CUDA(cudaEventRecord(*a, s));
+  return LCS_OK;
+}
+
+static lcs_status xfer_end(lcs_bound* H, cudaStream_t s, cudaEvent_t a, int cat) {
+  if (!H->opts.timing) return LCS_OK;
+  cudaEvent_t b;
+  LCS_CUDA(cudaEventCreate(&b));
+  LCS_CUDA(cudaEventRecord(b, s));
+  H->xfer_ev[cat].emplace_back(a, b);
+  if (H->xfer_ev[cat].size() > 4096) fold_events(H);
   return LCS_OK;
 }
 
@@ -615,6 +802,30 @@ static lcs_status run_check(lcs_bound* H, const long long* u, bool R_from_state,
   return LCS_OK;
 }
 
+// the part of a check that follows its partials: E, the keep test (and the
+// history record), then the copy of a kept u
+static lcs_status finish_check(lcs_bound* H, const RedPartial* parts, int n_parts, const long long* u, long long iter) {
+  finalize_check_kernel<<<1, kFinalBlock, 0, H->stream>>>(parts, n_parts, H->dstate, iter, H->hist, H->hist_count);
+  LCS_CUDA(cudaGetLastError());
+  H->launches++;
+  if (H->ubuf) {
+    copy_if_kept_kernel<<<H->grid_sweep, kBlock, 0, H->stream>>>(u, H->ubuf, H->n_stored, H->dstate);
+    LCS_CUDA(cudaGetLastError());
+    H->launches++;
+  }
+  return LCS_OK;
+}
+
+// run a check that waits for the next sweep on its own (before anything that
+// reads the results of Algorithm 2)
+static lcs_status flush_pending(lcs_bound* H) {
+  if (!H->pending_check) return LCS_OK;
+  H->pending_check = false;
+  const long long* u = H->ring[H->newest];
+  if (lcs_status st = run_check(H, u, true, 0, H->pending_iter, false, true)) return st;
+  return finish_check(H, H->partials, H->last_check_grid, u, H->pending_iter);
+}
+
 lcs_status lcs_bound_iterate(lcs_bound_t* H, int64_t n_iters) {
   if (!H) return fail(LCS_EINVAL, "handle is NULL");
   if (n_iters < 0) return fail(LCS_EINVAL, "n_iters < 0");
@@ -632,6 +843,8 @@ lcs_status lcs_bound_iterate(lcs_bound_t* H, int64_t n_iters) {
   if (!headroom_ok(H, vb_after))
     return fail(LCS_EOVERFLOW, "iterates could exceed the fixed-point range (max |v| up to %.3g)",
                 vb_after / (double)H->one);
+  if (H->narrow && !H->swap_ok)
+    return fail(LCS_EINVAL, "32-bit storage runs only the swap-aware sweep, and the start lacks the swap symmetry");
   const int rows = H->d + 1;
   for (int64_t i = 0; i < n_iters; ++i) {
     const long long it = H->iters_done + 1;
@@ -647,31 +860,55 @@ lcs_status lcs_bound_iterate(lcs_bound_t* H, int64_t n_iters) {
     p.r_mode = H->opts.r_mode;
     p.one = H->one;
     p.partials = H->partials;
+    p.state = H->dstate;
+    if (H->narrow) {
+      p.offs = H->offs;
+      p.slot_in0 = H->newest;
+      p.slot_in1 = (H->newest - 1 + rows) % rows;
+      p.slot_out = out_slot;
+      p.step = 0;  // before the first increment the offsets stay put
+    }
     const bool use_swap = H->swap_ok && H->ks_swap;
     const KernelSet* K = use_swap ? H->ks_swap : H->ks;
-    const int grid = use_swap ? H->grid_sweep_swap : H->grid_sweep;
+    // a check left by the previous iteration runs inside this sweep if the
+    // kernels can fuse it, else on its own first
+    const bool fuse = H->pending_check && K->sweep_check;
+    if (H->pending_check && !fuse)
+      if (lcs_status st = flush_pending(H)) return st;
+    const int grid = fuse ? H->grid_fused : use_swap ? H->grid_sweep_swap : H->grid_sweep;
     cudaEvent_t a = nullptr;
     lcs_status st = timed_begin(H, &a);
     if (st) return st;
-    K->sweep(p, grid, H->stream);
+    if (fuse) {
+      p.check_partials = H->check_partials;
+      K->sweep_check(p, grid, H->stream);
+    } else {
+      K->sweep(p, grid, H->stream);
+    }
     LCS_CUDA(cudaGetLastError());
     st = timed_end(H, a, true);
     if (st) return st;
     H->sweep_n++;
     // the general kernels: every output written once, each of the d inputs read once
     const int algo = K->tails_per_thread == 0 ? 8 * (H->d + 1) : K->sweep_algo_bytes;
-    H->sweep_bytes += (unsigned long long)algo * H->n_stored;
+    // a fused check adds one more read of the newest input's blocks: half of a check's bytes
+    H->sweep_bytes += (unsigned long long)(algo + (fuse ? K->check_algo_bytes / 2 : 0)) * H->n_stored;
     H->launches++;
+    if (fuse) {  // the pending check's E and keep test, before this iteration's increment replaces R
+      H->pending_check = false;
+      if (lcs_status st2 = finish_check(H, H->check_partials, grid, p.prev[0], H->pending_iter)) return st2;
+    }
     if (check) {
       finalize_incr_kernel<<<1, kFinalBlock, 0, H->stream>>>(H->partials, grid, H->opts.r_mode, H->dstate, it);
       LCS_CUDA(cudaGetLastError());
       H->launches++;
-      st = run_check(H, p.out, true, 0, it, true, true);
-      if (st) return st;
-      if (H->ubuf) {
-        copy_if_kept_kernel<<<H->grid_sweep, kBlock, 0, H->stream>>>(p.out, H->ubuf, H->n_stored, H->dstate);
-        LCS_CUDA(cudaGetLastError());
-        H->launches++;
+      if (use_swap && K->sweep_check) {
+        H->pending_check = true;  // the next sweep, or the next call that reads results, runs it
+        H->pending_iter = it;
+      } else {
+        st = run_check(H, p.out, true, 0, it, false, true);
+        if (st) return st;
+        if (lcs_status st2 = finish_check(H, H->partials, H->last_check_grid, p.out, it)) return st2;
       }
     }
     H->newest = out_slot;
@@ -684,6 +921,7 @@ lcs_status lcs_bound_iterate(lcs_bound_t* H, int64_t n_iters) {
 lcs_status lcs_bound_read_report(lcs_bound_t* H, lcs_bound_report* out) {
   if (!H || !out) return fail(LCS_EINVAL, "NULL argument");
   if (H->batch) return fail(LCS_EINVAL, "a batch handle: use the lcs_bound_batch_* calls");
+  if (lcs_status st = flush_pending(H)) return st;
   DevState s;
   LCS_CUDA(cudaMemcpyAsync(&s, H->dstate, sizeof s, cudaMemcpyDeviceToHost, H->stream));
   LCS_CUDA(cudaStreamSynchronize(H->stream));
@@ -727,16 +965,95 @@ lcs_status lcs_bound_read(lcs_bound_t* H, double* bound_rd, uint64_t* argmin_sta
   return LCS_OK;
 }
 
-static lcs_status ensure_staging(lcs_bound* H, size_t bytes) {
-  if (H->staging_bytes >= bytes) return LCS_OK;
-  dev_free(H, H->staging);
-  H->staging = dev_alloc(H, bytes);
-  H->staging_bytes = H->staging ? bytes : 0;
-  if (!H->staging) return fail(LCS_ENOMEM, "staging buffer (%zu bytes)", bytes);
+static const size_t kChunk = (size_t)32 << 20;    // values per staged piece (256 MiB)
+
+// The copy stream, its events and the two staging buffers, made on the first
+// host transfer of a handle.
+static lcs_status ensure_xfer(lcs_bound* H, bool staging) {
+  if (!H->xstream) {
+    LCS_CUDA(cudaStreamCreateWithFlags(&H->xstream, cudaStreamNonBlocking));
+    for (int i = 0; i < 2; ++i) {
+      LCS_CUDA(cudaEventCreateWithFlags(&H->stage_ready[i], cudaEventDisableTiming));
+      LCS_CUDA(cudaEventCreateWithFlags(&H->stage_free[i], cudaEventDisableTiming));
+    }
+    LCS_CUDA(cudaEventCreateWithFlags(&H->xsync, cudaEventDisableTiming));
+  }
+  for (int i = 0; staging && i < 2; ++i) {
+    if (H->stage[i]) continue;
+    H->stage[i] = dev_alloc(H, kChunk * 8);
+    if (!H->stage[i]) return fail(LCS_ENOMEM, "staging buffer (%zu bytes)", kChunk * 8);
+  }
   return LCS_OK;
 }
 
-static const size_t kChunk = (size_t)32 << 20;  // elements per host transfer chunk (256 MiB)
+// make stream `to` wait for everything enqueued on stream `from` so far
+static lcs_status stream_after(lcs_bound* H, cudaStream_t to, cudaStream_t from) {
+  LCS_CUDA(cudaEventRecord(H->xsync, from));
+  LCS_CUDA(cudaStreamWaitEvent(to, H->xsync, 0));
+  return LCS_OK;
+}
+
+// One copy between host and device on the copy stream, timed.
+static lcs_status xfer_copy(lcs_bound* H, void* dst, const void* src, size_t bytes, bool h2d) {
+  cudaEvent_t a;
+  if (lcs_status st = xfer_begin(H, H->xstream, &a)) return st;
+  LCS_CUDA(cudaMemcpyAsync(dst, src, bytes, h2d ? cudaMemcpyHostToDevice : cudaMemcpyDeviceToHost, H->xstream));
+  (h2d ? H->h2d_bytes : H->d2h_bytes) += bytes;
+  return xfer_end(H, H->xstream, a, h2d ? kXferH2D : kXferD2H);
+}
+
+// (templates: C++ linkage inside the extern "C" block)
+extern "C++" {
+// Host -> device through the two staging buffers: piece i is copied into
+// stage[i % 2] on the copy stream while `consume` (kernels on the handle's
+// stream) converts piece i - 1 out of the other buffer.  A staging buffer is
+// refilled only after the last kernel that read it (stage_free), also across
+// calls, so the copies of one call may run ahead while the handle's stream
+// still works on an earlier one.
+template <class Consume>
+static lcs_status h2d_pipelined(lcs_bound* H, const void* src_host, unsigned long long n, Consume consume) {
+  if (lcs_status st = ensure_xfer(H, true)) return st;
+  int i = 0;
+  for (unsigned long long off = 0; off < n; off += kChunk, ++i) {
+    const int b = i & 1;
+    const unsigned long long len = std::min<unsigned long long>(kChunk, n - off);
+    if (H->stage_recorded[b]) LCS_CUDA(cudaStreamWaitEvent(H->xstream, H->stage_free[b], 0));
+    if (lcs_status st = xfer_copy(H, H->stage[b], (const char*)src_host + off * 8, len * 8, true)) return st;
+    LCS_CUDA(cudaEventRecord(H->stage_ready[b], H->xstream));
+    LCS_CUDA(cudaStreamWaitEvent(H->stream, H->stage_ready[b], 0));
+    cudaEvent_t a;
+    if (lcs_status st = xfer_begin(H, H->stream, &a)) return st;
+    if (lcs_status st = consume((const long long*)H->stage[b], off, len)) return st;
+    if (lcs_status st = xfer_end(H, H->stream, a, kXferKernel)) return st;
+    LCS_CUDA(cudaEventRecord(H->stage_free[b], H->stream));
+    H->stage_recorded[b] = true;
+  }
+  return LCS_OK;
+}
+
+// Device -> host through the two staging buffers: `produce` (kernels on the
+// handle's stream) fills stage[i % 2] with piece i while the copy stream
+// moves piece i - 1 out.  The handle's stream waits for the last copy.
+template <class Produce>
+static lcs_status d2h_pipelined(lcs_bound* H, void* dst_host, unsigned long long n, Produce produce) {
+  if (lcs_status st = ensure_xfer(H, true)) return st;
+  int i = 0;
+  for (unsigned long long off = 0; off < n; off += kChunk, ++i) {
+    const int b = i & 1;
+    const unsigned long long len = std::min<unsigned long long>(kChunk, n - off);
+    if (H->stage_recorded[b]) LCS_CUDA(cudaStreamWaitEvent(H->stream, H->stage_free[b], 0));
+    cudaEvent_t a;
+    if (lcs_status st = xfer_begin(H, H->stream, &a)) return st;
+    if (lcs_status st = produce((long long*)H->stage[b], off, len)) return st;
+    if (lcs_status st = xfer_end(H, H->stream, a, kXferKernel)) return st;
+    LCS_CUDA(cudaEventRecord(H->stage_ready[b], H->stream));
+    LCS_CUDA(cudaStreamWaitEvent(H->xstream, H->stage_ready[b], 0));
+    if (lcs_status st = xfer_copy(H, (char*)dst_host + off * 8, H->stage[b], len * 8, false)) return st;
+    LCS_CUDA(cudaEventRecord(H->stage_free[b], H->xstream));
+    H->stage_recorded[b] = true;
+  }
+  return stream_after(H, H->stream, H->xstream);
+}
 
 // dst[i] = src[i], 16 B at a time (both 16-byte aligned, n even) plus a tail
 __global__ void copy_values_kernel(const long long* __restrict__ src, long long* __restrict__ dst,
@@ -750,11 +1067,6 @@ __global__ void copy_values_kernel(const long long* __restrict__ src, long long*
   if (blockIdx.x == 0 && threadIdx.x == 0 && (n & 1)) dst[n - 1] = src[n - 1];
 }
 
-// Host <-> device copies of n values through the staging buffer, in kChunk
-// pieces, with a kernel moving each piece between staging and dst / src, the
-// way the full-vector start does.  Copy-engine copies straight into (or out
-// of) a buffer of tens of GiB were seen to run at a fifth of the link's rate
-// while this path kept its rate on the same device; elsewhere the two match.
 static lcs_status copy_values(lcs_bound* H, const long long* src, long long* dst, unsigned long long n) {
   const int grid = (int)std::min<unsigned long long>(1024, (n / 2 + kBlock - 1) / kBlock + 1);
   copy_values_kernel<<<grid, kBlock, 0, H->stream>>>(src, dst, n);
@@ -763,24 +1075,25 @@ static lcs_status copy_values(lcs_bound* H, const long long* src, long long* dst
   return LCS_OK;
 }
 
-static lcs_status h2d_staged(lcs_bound* H, long long* dst_dev, const void* src_host, unsigned long long n) {
-  if (lcs_status st = ensure_staging(H, kChunk * 8)) return st;
-  for (unsigned long long off = 0; off < n; off += kChunk) {
-    const unsigned long long len = std::min<unsigned long long>(kChunk, n - off);
-    LCS_CUDA(cudaMemcpyAsync(H->staging, (const char*)src_host + off * 8, len * 8, cudaMemcpyHostToDevice, H->stream));
-    if (lcs_status st = copy_values(H, (const long long*)H->staging, dst_dev + off, len)) return st;
-  }
-  return LCS_OK;
+}  // extern "C++"
+
+// n values between host memory and a device buffer with no conversion.  Even
+// these go through the staging pipeline: on this GB300's link, copy-engine
+// copies straight into (or out of) a buffer of many GiB were measured at a
+// tenth to a half of the link's rate in some processes (after heavy earlier
+// use of the machine), while copies through a 256 MiB buffer kept 210 GB/s in
+// the same processes; the copy kernel on the device side costs a pass over
+// the values at HBM speed, hidden behind the link.
+static lcs_status h2d_copy(lcs_bound* H, long long* dst_dev, const void* src_host, unsigned long long n) {
+  return h2d_pipelined(H, src_host, n, [&](const long long* stage, unsigned long long off, unsigned long long len) {
+    return copy_values(H, stage, dst_dev + off, len);
+  });
 }
 
-static lcs_status d2h_staged(lcs_bound* H, void* dst_host, const long long* src_dev, unsigned long long n) {
-  if (lcs_status st = ensure_staging(H, kChunk * 8)) return st;
-  for (unsigned long long off = 0; off < n; off += kChunk) {
-    const unsigned long long len = std::min<unsigned long long>(kChunk, n - off);
-    if (lcs_status st = copy_values(H, src_dev + off, (long long*)H->staging, len)) return st;
-    LCS_CUDA(cudaMemcpyAsync((char*)dst_host + off * 8, H->staging, len * 8, cudaMemcpyDeviceToHost, H->stream));
-  }
-  return LCS_OK;
+static lcs_status d2h_copy(lcs_bound* H, void* dst_host, const long long* src_dev, unsigned long long n) {
+  return d2h_pipelined(H, dst_host, n, [&](long long* stage, unsigned long long off, unsigned long long len) {
+    return copy_values(H, src_dev + off, stage, len);
+  });
 }
 
 // Ingest [off, off+len) of an input vector.  Under complement-symmetric
@@ -818,6 +1131,7 @@ static lcs_status finish_start(lcs_bound* H) {
   LCS_CUDA(cudaStreamSynchronize(H->stream));
   H->newest = H->d - 1;
   H->iters_done = 0;
+  H->pending_check = false;
   if (s.status == LCS_EINVAL)
     return fail(LCS_EINVAL, "start vectors are not complement-symmetric (v[N-1-x] != v[x])");
   if (s.status == LCS_EOVERFLOW) return fail(LCS_EOVERFLOW, "start values outside the fixed-point range");
@@ -827,12 +1141,77 @@ static lcs_status finish_start(lcs_bound* H) {
   return LCS_OK;
 }
 
+// calls that 32-bit storage does not offer
+static lcs_status wide_only(const lcs_bound* H, const char* what) {
+  if (H && H->narrow) return fail(LCS_EUNSUPPORTED, "%s is not available with 32-bit storage", what);
+  return LCS_OK;
+}
+
+// the checks of one start row: max |v|, and the symmetries the fast kernels use
+static lcs_status start_row_checks(lcs_bound* H, int slot) {
+  long long* dst = H->ring[slot];
+  const int grid = (int)std::min<unsigned long long>(4096, (H->n_stored + kBlock - 1) / kBlock);
+  if (H->narrow) {  // max |v| came with the narrowing
+    maxabs_swap_check_kernel<int><<<grid, kBlock, 0, H->stream>>>((const int*)dst, H->n_stored, H->n_total,
+                                                                  H->dstate, H->offs, slot);
+    LCS_CUDA(cudaGetLastError());
+    H->launches++;
+    return LCS_OK;
+  }
+  if (H->ks_swap && H->ks_swap->sym == 2) {
+    maxabs_swap_check_kernel<<<grid, kBlock, 0, H->stream>>>(dst, H->n_stored, H->n_total, H->dstate);
+    LCS_CUDA(cudaGetLastError());
+    H->launches++;
+    return LCS_OK;
+  }
+  maxabs_kernel<<<grid, kBlock, 0, H->stream>>>(dst, H->n_stored, H->dstate);
+  LCS_CUDA(cudaGetLastError());
+  H->launches++;
+  if (H->ks_swap) {
+    if (H->ks_swap->sym == 3)
+      launch_swap_check_d2s(H->sigma, dst, H->n_stored, H->h, H->dstate, grid, H->stream);
+    else
+      launch_perm_check_d3s(dst, H->n_stored, H->n_total, H->dstate, grid, H->stream);
+    LCS_CUDA(cudaGetLastError());
+    H->launches++;
+  }
+  return LCS_OK;
+}
+
+// a stored-form row into 32-bit storage: offset c = the row's first value
+static lcs_status narrow_row(lcs_bound* H, const void* src, int on_device, int slot) {
+  long long c = 0;
+  if (on_device)
+    LCS_CUDA(cudaMemcpy(&c, src, sizeof c, cudaMemcpyDeviceToHost));
+  else
+    c = *static_cast<const long long*>(src);
+  int* dst = reinterpret_cast<int*>(H->ring[slot]);
+  auto conv = [&](const long long* from, unsigned long long off, unsigned long long len) {
+    const int grid = (int)std::min<unsigned long long>(4096, (len + kBlock - 1) / kBlock);
+    narrow_kernel<<<grid, kBlock, 0, H->stream>>>(from, dst + off, len, c, H->dstate);
+    LCS_CUDA(cudaGetLastError());
+    H->launches++;
+    return LCS_OK;
+  };
+  if (on_device) {
+    if (lcs_status st = conv(static_cast<const long long*>(src), 0, H->n_stored)) return st;
+  } else if (lcs_status st = h2d_pipelined(H, src, H->n_stored, conv)) {
+    return st;
+  }
+  set_offset_kernel<<<1, 32, 0, H->stream>>>(H->offs, slot, c);
+  LCS_CUDA(cudaGetLastError());
+  H->launches++;
+  return LCS_OK;
+}
+
 // stored = true: v[k] holds the n_stored stored values (the storage form), copied as they are
 static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_device, bool from_double,
                                     bool stored = false) {
   if (!H) return fail(LCS_EINVAL, "handle is NULL");
   if (H->batch) return fail(LCS_EINVAL, "a batch handle: use the lcs_bound_batch_* calls");
   if (!v) return fail(LCS_EINVAL, "NULL argument");
+  if (!stored)
+    if (lcs_status st = wide_only(H, "a start of full vectors (use the stored form)")) return st;
   const double scale = std::ldexp(1.0, H->opts.frac_bits);
   LCS_CUDA(cudaMemsetAsync(H->dstate, 0, sizeof(DevState), H->stream));
   LCS_CUDA(cudaMemsetAsync(H->hist_count, 0, sizeof(unsigned long long), H->stream));
@@ -840,45 +1219,27 @@ static lcs_status set_start_checked(lcs_bound* H, const void* const* v, int on_d
     if (!v[k]) return fail(LCS_EINVAL, "start vector %d is NULL", k);
   for (int k = 0; k < H->d; ++k) {
     long long* dst = H->ring[H->d - 1 - k];
-    if (stored) {
-      if (on_device) {
-        LCS_CUDA(cudaMemcpyAsync(dst, v[k], H->n_stored * 8, cudaMemcpyDeviceToDevice, H->stream));
-      } else if (lcs_status st = h2d_staged(H, dst, v[k], H->n_stored)) {
-        return st;
-      }
+    if (H->narrow) {
+      if (lcs_status st = narrow_row(H, v[k], on_device, H->d - 1 - k)) return st;
+    } else if (stored && !on_device) {
+      if (lcs_status st = h2d_copy(H, dst, v[k], H->n_stored)) return st;
+    } else if (stored) {
+      LCS_CUDA(cudaMemcpyAsync(dst, v[k], H->n_stored * 8, cudaMemcpyDeviceToDevice, H->stream));
     } else if (on_device) {
       lcs_status st = ingest_range(H, v[k], 0, H->n_total, dst, from_double, scale);
       if (st) return st;
     } else {
-      lcs_status st = ensure_staging(H, kChunk * 8);
+      lcs_status st = h2d_pipelined(H, v[k], H->n_total,
+                                    [&](const long long* stage, unsigned long long off, unsigned long long len) {
+                                      return ingest_range(H, stage, off, len, dst, from_double, scale);
+                                    });
       if (st) return st;
-      for (unsigned long long off = 0; off < H->n_total; off += kChunk) {
-        const unsigned long long len = std::min<unsigned long long>(kChunk, H->n_total - off);
-        LCS_CUDA(cudaMemcpyAsync(H->staging, (const char*)v[k] + off * 8, len * 8, cudaMemcpyHostToDevice, H->stream));
-        st = ingest_range(H, H->staging, off, len, dst, from_double, scale);
-        if (st) return st;
-      }
     }
-    const int grid = (int)std::min<unsigned long long>(4096, (H->n_stored + kBlock - 1) / kBlock);
-    if (H->ks_swap && H->ks_swap->sym == 2) {
-      maxabs_swap_check_kernel<<<grid, kBlock, 0, H->stream>>>(dst, H->n_stored, H->n_total, H->dstate);
-      LCS_CUDA(cudaGetLastError());
-      H->launches++;
-      continue;
-    }
-    maxabs_kernel<<<grid, kBlock, 0, H->stream>>>(dst, H->n_stored, H->dstate);
-    LCS_CUDA(cudaGetLastError());
-    H->launches++;
-    if (H->ks_swap) {
-      if (H->ks_swap->sym == 3)
-        launch_swap_check_d2s(H->sigma, dst, H->n_stored, H->h, H->dstate, grid, H->stream);
-      else
-        launch_perm_check_d3s(dst, H->n_stored, H->n_total, H->dstate, grid, H->stream);
-      LCS_CUDA(cudaGetLastError());
-      H->launches++;
-    }
+    if (lcs_status st = start_row_checks(H, H->d - 1 - k)) return st;
   }
-  return finish_start(H);
+  if (lcs_status st = finish_start(H)) return st;
+  if (H->narrow && !H->swap_ok) return fail(LCS_EINVAL, "32-bit storage needs swap-symmetric start vectors");
+  return LCS_OK;
 }
 
 lcs_status lcs_bound_set_start(lcs_bound_t* H, const double* const* v, int on_device) {
@@ -893,21 +1254,88 @@ lcs_status lcs_bound_set_start_stored_fx(lcs_bound_t* H, const int64_t* const* v
   return set_start_checked(H, (const void* const*)v, on_device, false, true);
 }
 
+lcs_status lcs_bound_set_start_lift_fx(lcs_bound_t* H, int h_from, const int64_t* src, int on_device, int64_t r_hat) {
+  if (!H || !src) return fail(LCS_EINVAL, "NULL argument");
+  if (H->batch) return fail(LCS_EINVAL, "a batch handle: use the lcs_bound_batch_* calls");
+  if (H->sigma != 2 || H->d != 2 || !H->sym)
+    return fail(LCS_EUNSUPPORTED, "the prefix lift needs sigma = d = 2 with complement-symmetric storage");
+  if (h_from < 2 || h_from > H->h) return fail(LCS_EINVAL, "h_from %d outside 2..%d", h_from, H->h);
+  const int s2 = 2 * (H->h - h_from);
+  const unsigned long long n_src = H->n_stored >> s2;  // the stored half of the shorter shape
+  long long first = 0;
+  if (on_device)
+    LCS_CUDA(cudaMemcpy(&first, src, sizeof first, cudaMemcpyDeviceToHost));
+  else
+    first = src[0];
+  // 64-bit rows hold the values; 32-bit rows hold value - first (newest) and
+  // value - r_hat - (first - r_hat) (older): the same numbers, two offsets
+  const long long sub_new = H->narrow ? first : 0, sub_old = H->narrow ? first : (long long)r_hat;
+  LCS_CUDA(cudaMemsetAsync(H->dstate, 0, sizeof(DevState), H->stream));
+  LCS_CUDA(cudaMemsetAsync(H->hist_count, 0, sizeof(unsigned long long), H->stream));
+  const int s_new = H->d - 1, s_old = H->d - 2;  // ring rows of v[0] (newest) and v[1]
+  auto lift = [&](const long long* from, unsigned long long off, unsigned long long len) {
+    const unsigned long long lo = off << s2, hi = (off + len) << s2;
+    const int grid = (int)std::min<unsigned long long>(4096, (hi - lo + kBlock - 1) / kBlock);
+    if (H->narrow)
+      lift_kernel<int><<<grid, kBlock, 0, H->stream>>>(from, off, s2, lo, hi, (int*)H->ring[s_new],
+                                                       (int*)H->ring[s_old], sub_new, sub_old, H->dstate);
+    else
+      lift_kernel<long long><<<grid, kBlock, 0, H->stream>>>(from, off, s2, lo, hi, H->ring[s_new], H->ring[s_old],
+                                                             sub_new, sub_old, H->dstate);
+    LCS_CUDA(cudaGetLastError());
+    H->launches++;
+    return LCS_OK;
+  };
+  if (on_device) {
+    if (lcs_status st = lift(reinterpret_cast<const long long*>(src), 0, n_src)) return st;
+  } else if (lcs_status st = h2d_pipelined(H, src, n_src, lift)) {
+    return st;
+  }
+  if (H->narrow) {
+    set_offset_kernel<<<1, 32, 0, H->stream>>>(H->offs, s_new, first);
+    set_offset_kernel<<<1, 32, 0, H->stream>>>(H->offs, s_old, first - (long long)r_hat);
+    LCS_CUDA(cudaGetLastError());
+    H->launches += 2;
+  }
+  for (int slot : {s_new, s_old})
+    if (lcs_status st = start_row_checks(H, slot)) return st;
+  if (lcs_status st = finish_start(H)) return st;
+  if (H->narrow && !H->swap_ok) return fail(LCS_EINVAL, "32-bit storage needs swap-symmetric start vectors");
+  return LCS_OK;
+}
+
 lcs_status lcs_bound_export_stored_fx(lcs_bound_t* H, int k, int64_t* dst, int on_device) {
   if (!H || !dst) return fail(LCS_EINVAL, "NULL argument");
   if (H->batch) return fail(LCS_EINVAL, "a batch handle: use the lcs_bound_batch_* calls");
   if (k < -1 || k >= H->d) return fail(LCS_EINVAL, "k=%d outside -1..d-1", k);
+  if (k == -1)
+    if (lcs_status st = flush_pending(H)) return st;  // u is the kept iterate: its check must have run
   const long long* src;
+  int slot = -1;
   if (k == -1) {
     if (!H->ubuf) return fail(LCS_EINVAL, "u is not retained (opts.keep_u = 0)");
     src = H->ubuf;
   } else {
     const int rows = H->d + 1;
-    src = H->ring[(H->newest - k + rows) % rows];
+    slot = (H->newest - k + rows) % rows;
+    src = H->ring[slot];
   }
-  if (on_device) {
+  if (H->narrow) {  // widen: value = stored + the row's offset (no u is kept with 32-bit storage)
+    auto widen = [&](long long* to, unsigned long long off, unsigned long long len) {
+      const int grid = (int)std::min<unsigned long long>(4096, (len + kBlock - 1) / kBlock);
+      widen_kernel<<<grid, kBlock, 0, H->stream>>>(reinterpret_cast<const int*>(src) + off, to, len, H->offs, slot);
+      LCS_CUDA(cudaGetLastError());
+      H->launches++;
+      return LCS_OK;
+    };
+    if (on_device) {
+      if (lcs_status st = widen(reinterpret_cast<long long*>(dst), 0, H->n_stored)) return st;
+    } else if (lcs_status st = d2h_pipelined(H, dst, H->n_stored, widen)) {
+      return st;
+    }
+  } else if (on_device) {
     LCS_CUDA(cudaMemcpyAsync(dst, src, H->n_stored * 8, cudaMemcpyDeviceToDevice, H->stream));
-  } else if (lcs_status st = d2h_staged(H, dst, src, H->n_stored)) {
+  } else if (lcs_status st = d2h_copy(H, dst, src, H->n_stored)) {
     return st;
   }
   if (!on_device) LCS_CUDA(cudaStreamSynchronize(H->stream));
@@ -921,6 +1349,7 @@ static lcs_status orbit_supported(const lcs_bound* H) {
   if (H->batch) return fail(LCS_EINVAL, "a batch handle: use the lcs_bound_batch_* calls");
   if (!H->ks_swap || H->ks_swap->sym != 2)
     return fail(LCS_EUNSUPPORTED, "the orbit form needs sigma = d = 2, complement-symmetric storage and h >= 6");
+  if (lcs_status st = wide_only(H, "the orbit form")) return st;
   return LCS_OK;
 }
 
@@ -941,18 +1370,29 @@ lcs_status lcs_bound_set_start_orbit_fx(lcs_bound_t* H, const int64_t* const* v,
   const unsigned long long n_orb = orbit_len(H->h);
   LCS_CUDA(cudaMemsetAsync(H->dstate, 0, sizeof(DevState), H->stream));
   LCS_CUDA(cudaMemsetAsync(H->hist_count, 0, sizeof(unsigned long long), H->stream));
-  // host vectors pass through the ring row the start does not fill
-  // (n_orb = 4^(h-1) + 2^h <= n_stored = 2 4^(h-1))
-  long long* scratch = H->ring[H->d];
-  for (int k = 0; k < H->d; ++k) {
-    const long long* src = reinterpret_cast<const long long*>(v[k]);
-    if (!on_device) {
-      if (lcs_status st = h2d_staged(H, scratch, v[k], n_orb)) return st;
-      src = scratch;
+  if (on_device) {
+    for (int k = 0; k < H->d; ++k) {
+      launch_orbit_unpack(reinterpret_cast<const long long*>(v[k]), H->ring[H->d - 1 - k], H->h, H->n_tail,
+                          H->dstate, H->stream);
+      LCS_CUDA(cudaGetLastError());
+      H->launches++;
     }
-    launch_orbit_unpack(src, H->ring[H->d - 1 - k], H->h, H->n_tail, H->dstate, H->stream);
-    LCS_CUDA(cudaGetLastError());
-    H->launches++;
+  } else {
+    // Host vectors land in rows the unpacking does not write yet (n_orb =
+    // 4^(h-1) + 2^h <= n_stored = 2 4^(h-1)): v[0] in row 0, which v[1] fills
+    // later, and v[1] in row 2, which the start leaves free.  While v[0] is
+    // unpacked into row 1, the copy stream already moves the first pieces of
+    // v[1]; unpacking v[1] into row 0 follows on the stream.
+    long long* scratch[2] = {H->ring[0], H->ring[2]};
+    for (int k = 0; k < 2; ++k) {
+      if (lcs_status st = h2d_copy(H, scratch[k], v[k], n_orb)) return st;
+      cudaEvent_t a;
+      if (lcs_status st = xfer_begin(H, H->stream, &a)) return st;
+      launch_orbit_unpack(scratch[k], H->ring[1 - k], H->h, H->n_tail, H->dstate, H->stream);
+      LCS_CUDA(cudaGetLastError());
+      if (lcs_status st = xfer_end(H, H->stream, a, kXferKernel)) return st;
+      H->launches++;
+    }
   }
   return finish_start(H);  // symmetric by construction: swap_bad stays 0
 }
@@ -961,6 +1401,8 @@ lcs_status lcs_bound_export_orbit_fx(lcs_bound_t* H, int k, int64_t* dst, int on
   if (lcs_status st = orbit_supported(H)) return st;
   if (!dst) return fail(LCS_EINVAL, "NULL argument");
   if (k < -1 || k >= H->d) return fail(LCS_EINVAL, "k=%d outside -1..d-1", k);
+  if (k == -1)
+    if (lcs_status st = flush_pending(H)) return st;  // u is the kept iterate: its check must have run
   if (!H->swap_ok) return fail(LCS_EINVAL, "the iterates are not swap-symmetric (the start lacked the symmetry)");
   if (on_device && ((uintptr_t)dst & 15)) return fail(LCS_EINVAL, "device destination is not 16-byte aligned");
   const int rows = H->d + 1;
@@ -984,7 +1426,7 @@ lcs_status lcs_bound_export_orbit_fx(lcs_bound_t* H, int k, int64_t* dst, int on
   launch_orbit_pack(src, scratch, H->h, H->n_tail, H->stream);
   LCS_CUDA(cudaGetLastError());
   H->launches++;
-  if (lcs_status st = d2h_staged(H, dst, scratch, n_orb)) return st;
+  if (lcs_status st = d2h_copy(H, dst, scratch, n_orb)) return st;
   LCS_CUDA(cudaStreamSynchronize(H->stream));
   return LCS_OK;
 }
@@ -992,6 +1434,7 @@ lcs_status lcs_bound_export_orbit_fx(lcs_bound_t* H, int k, int64_t* dst, int on
 lcs_status lcs_bound_history(lcs_bound_t* H, lcs_bound_check_record* out, int64_t max_records, int64_t* n_checks) {
   if (!H) return fail(LCS_EINVAL, "handle is NULL");
   if (H->batch) return fail(LCS_EINVAL, "batch handles keep no history");
+  if (lcs_status st = flush_pending(H)) return st;
   if (max_records < 0 || (max_records > 0 && !out)) return fail(LCS_EINVAL, "bad output buffer");
   static_assert(sizeof(CheckRecord) == sizeof(lcs_bound_check_record), "record layouts differ");
   unsigned long long count = 0;
@@ -1061,6 +1504,9 @@ static lcs_status read_vector(lcs_bound* H, FILE* f, long long* dst, std::vector
 }
 
 lcs_status lcs_bound_save(lcs_bound_t* H, const char* path) {
+  if (lcs_status st = wide_only(H, "lcs_bound_save")) return st;
+  if (H && !H->batch)
+    if (lcs_status st = flush_pending(H)) return st;
   if (!H || !path) return fail(LCS_EINVAL, "NULL argument");
   if (H->batch) return fail(LCS_EINVAL, "batch handles have no checkpoint");
   CkptHeader hd{};
@@ -1103,6 +1549,7 @@ lcs_status lcs_bound_save(lcs_bound_t* H, const char* path) {
 }
 
 lcs_status lcs_bound_restore(lcs_bound_t* H, const char* path) {
+  if (lcs_status st = wide_only(H, "lcs_bound_restore")) return st;
   if (!H || !path) return fail(LCS_EINVAL, "NULL argument");
   if (H->batch) return fail(LCS_EINVAL, "batch handles have no checkpoint");
   FileCloser fc{fopen(path, "rb")};
@@ -1136,6 +1583,7 @@ lcs_status lcs_bound_restore(lcs_bound_t* H, const char* path) {
   LCS_CUDA(cudaStreamSynchronize(H->stream));
   H->newest = H->d - 1;
   H->iters_done = hd.iters_done;
+  H->pending_check = false;  // a saved handle has run all its checks
   H->vbound = hd.vbound;
   H->swap_ok = H->ks_swap != nullptr && hd.swap_ok;
   return LCS_OK;
@@ -1145,38 +1593,45 @@ static lcs_status export_impl(lcs_bound* H, int k, void* dst, int on_device, boo
   if (!H || !dst) return fail(LCS_EINVAL, "NULL argument");
   if (H->batch) return fail(LCS_EINVAL, "a batch handle: use the lcs_bound_batch_* calls");
   if (k < -1 || k >= H->d) return fail(LCS_EINVAL, "k=%d outside -1..d-1", k);
+  if (k == -1)
+    if (lcs_status st = flush_pending(H)) return st;  // u is the kept iterate: its check must have run
   const long long* src;
+  int slot = 0;
   if (k == -1) {
     if (!H->ubuf) return fail(LCS_EINVAL, "u is not retained (opts.keep_u = 0)");
     src = H->ubuf;
   } else {
     const int rows = H->d + 1;
-    src = H->ring[(H->newest - k + rows) % rows];
+    slot = (H->newest - k + rows) % rows;
+    src = H->ring[slot];
   }
   const double scale = std::ldexp(1.0, -H->opts.frac_bits);
-  if (on_device) {
-    const int grid = (int)std::min<unsigned long long>(4096, (H->n_total + kBlock - 1) / kBlock);
-    if (to_double)
-      export_kernel<true><<<grid, kBlock, 0, H->stream>>>(src, 0, H->n_total, H->n_stored, H->n_total, scale, dst);
-    else
-      export_kernel<false><<<grid, kBlock, 0, H->stream>>>(src, 0, H->n_total, H->n_stored, H->n_total, scale, dst);
+  // one launch of the conversion for [off, off + len) of the states into `to`
+  auto conv = [&](void* to, unsigned long long off, unsigned long long len) {
+    const int grid = (int)std::min<unsigned long long>(4096, (len + kBlock - 1) / kBlock);
+    if (H->narrow) {
+      const int* w = reinterpret_cast<const int*>(src);
+      if (to_double)
+        export_kernel<true, int><<<grid, kBlock, 0, H->stream>>>(w, off, len, H->n_stored, H->n_total, scale, to,
+                                                                 H->offs, slot);
+      else
+        export_kernel<false, int><<<grid, kBlock, 0, H->stream>>>(w, off, len, H->n_stored, H->n_total, scale, to,
+                                                                  H->offs, slot);
+    } else if (to_double) {
+      export_kernel<true><<<grid, kBlock, 0, H->stream>>>(src, off, len, H->n_stored, H->n_total, scale, to);
+    } else {
+      export_kernel<false><<<grid, kBlock, 0, H->stream>>>(src, off, len, H->n_stored, H->n_total, scale, to);
+    }
     LCS_CUDA(cudaGetLastError());
     H->launches++;
     return LCS_OK;
-  }
-  lcs_status st = ensure_staging(H, kChunk * 8);
+  };
+  if (on_device) return conv(dst, 0, H->n_total);
+  lcs_status st = d2h_pipelined(H, dst, H->n_total,
+                                [&](long long* stage, unsigned long long off, unsigned long long len) {
+                                  return conv(stage, off, len);
+                                });
   if (st) return st;
-  for (unsigned long long off = 0; off < H->n_total; off += kChunk) {
-    const unsigned long long len = std::min<unsigned long long>(kChunk, H->n_total - off);
-    const int grid = (int)std::min<unsigned long long>(4096, (len + kBlock - 1) / kBlock);
-    if (to_double)
-      export_kernel<true><<<grid, kBlock, 0, H->stream>>>(src, off, len, H->n_stored, H->n_total, scale, H->staging);
-    else
-      export_kernel<false><<<grid, kBlock, 0, H->stream>>>(src, off, len, H->n_stored, H->n_total, scale, H->staging);
-    LCS_CUDA(cudaGetLastError());
-    H->launches++;
-    LCS_CUDA(cudaMemcpyAsync((char*)dst + off * 8, H->staging, len * 8, cudaMemcpyDeviceToHost, H->stream));
-  }
   LCS_CUDA(cudaStreamSynchronize(H->stream));
   return LCS_OK;
 }
@@ -1190,6 +1645,7 @@ lcs_status lcs_bound_export_fx(lcs_bound_t* H, int k, int64_t* dst, int on_devic
 }
 
 lcs_status lcs_bound_check_vector(lcs_bound_t* H, const int64_t* u_dev, int64_t R, int64_t* E_out) {
+  if (lcs_status st = wide_only(H, "lcs_bound_check_vector")) return st;
   if (!H || !u_dev || !E_out) return fail(LCS_EINVAL, "NULL argument");
   if (H->batch) return fail(LCS_EINVAL, "a batch handle: use the lcs_bound_batch_* calls");
   lcs_status st = run_check(H, (const long long*)u_dev, false, R, 0, false, false);
@@ -1215,10 +1671,17 @@ lcs_status lcs_bound_stats(lcs_bound_t* H, lcs_bound_stats_t* out, int reset) {
   out->kernel_launches = H->launches;
   out->sweep_bytes = H->sweep_bytes;
   out->check_bytes = H->check_bytes;
+  out->h2d_ms = H->xfer_ms[kXferH2D];
+  out->h2d_bytes = H->h2d_bytes;
+  out->d2h_ms = H->xfer_ms[kXferD2H];
+  out->d2h_bytes = H->d2h_bytes;
+  out->xfer_kernel_ms = H->xfer_ms[kXferKernel];
   if (reset) {
     H->sweep_n = H->check_n = H->launches = 0;
     H->sweep_ms = H->check_ms = 0;
     H->sweep_bytes = H->check_bytes = 0;
+    H->xfer_ms[0] = H->xfer_ms[1] = H->xfer_ms[2] = 0;
+    H->h2d_bytes = H->d2h_bytes = 0;
   }
   return LCS_OK;
 }
@@ -1309,15 +1772,13 @@ lcs_status lcs_bound_batch_export_fx(lcs_bound_t* H, int i, int k, int64_t* dst,
     LCS_CUDA(cudaGetLastError());
     return LCS_OK;
   }
-  st = ensure_staging(H, kChunk * 8);
-  if (st) return st;
-  for (unsigned long long off = 0; off < n_total; off += kChunk) {
-    const unsigned long long len = std::min<unsigned long long>(kChunk, n_total - off);
+  st = d2h_pipelined(H, dst, n_total, [&](long long* stage, unsigned long long off, unsigned long long len) {
     const int grid = (int)std::min<unsigned long long>(4096, (len + kBlock - 1) / kBlock);
-    export_kernel<false><<<grid, kBlock, 0, H->stream>>>(src, off, len, n_stored, n_total, 1.0, H->staging);
+    export_kernel<false><<<grid, kBlock, 0, H->stream>>>(src, off, len, n_stored, n_total, 1.0, stage);
     LCS_CUDA(cudaGetLastError());
-    LCS_CUDA(cudaMemcpyAsync((char*)dst + off * 8, H->staging, len * 8, cudaMemcpyDeviceToHost, H->stream));
-  }
+    return LCS_OK;
+  });
+  if (st) return st;
   LCS_CUDA(cudaStreamSynchronize(H->stream));
   return LCS_OK;
 }
@@ -1325,10 +1786,12 @@ lcs_status lcs_bound_batch_export_fx(lcs_bound_t* H, int i, int k, int64_t* dst,
 lcs_status lcs_bound_batch_info(lcs_bound_t* H, lcs_bound_batch_info_t* out) {
   if (!H || !out) return fail(LCS_EINVAL, "NULL argument");
   if (!H->batch) return fail(LCS_EINVAL, "not a batch handle");
-  long long launches = 0;
+  long long launches = 0, replays = 0;
   batch_tuning(H->batch, &out->grid, &out->units_per_item, &out->tuned_ms_per_iter, &launches, &out->graph,
-               &out->mode, &out->persistent_ms_per_iter, &out->concurrent_ms_per_iter);
+               &out->mode, &out->persistent_ms_per_iter, &out->concurrent_ms_per_iter, &out->graph_captured, &replays,
+               &out->min_ctas_per_sm);
   out->launches = launches;
+  out->graph_replays = replays;
   out->n_instances = batch_size(H->batch);
   return LCS_OK;
 }

@@ -48,6 +48,18 @@ struct SweepParams {
   int r_mode;                    // 0: min, 1: max
   long long one;                 // 2^K
   RedPartial* partials;          // one per CTA when incr
+  // Offset-normalised 32-bit storage (sigma = d = 2 only): a stored w stands
+  // for v = w + offs[slot] of its vector.  The output's offset is the first
+  // input's value at state 0 plus the last increment R (state->R once one
+  // has been reduced, else step); the sweep records it and flags an output
+  // outside 32 bits in state->status.  Unused (null) with 64-bit storage.
+  long long* offs;
+  int slot_in0, slot_in1, slot_out;
+  long long step;
+  DevState* state;
+  // a sweep fused with the check of its newest input (KernelSet::sweep_check):
+  // one max-W partial per CTA; R is read from state
+  RedPartial* check_partials;
 };
 
 // Arguments of one check launch: W = u + dR - F(u + (d-1)R, .., u).
@@ -80,6 +92,9 @@ struct KernelSet {
   // distinct input value the kernel's storage scheme needs read once
   int sweep_algo_bytes;
   int check_algo_bytes;
+  // optional: the sweep fused with the check of its newest input (null if none)
+  void (*sweep_check)(const SweepParams&, int grid, cudaStream_t);
+  const void* sweep_check_fn;
 };
 
 // Registry filled by the per-alphabet translation units.

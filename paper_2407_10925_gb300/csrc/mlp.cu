@@ -24,6 +24,7 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <new>
 #include <vector>
 
 #include <cuda_bf16.h>
@@ -337,7 +338,35 @@ struct lcs_mlp {
   void* W2c;
   float* table;
   int* err;
+  // device allocator (NULL alloc: cudaMalloc / cudaFree)
+  void* (*alloc)(size_t, void*);
+  void (*free)(void*, void*);
+  void* alloc_ctx;
 };
+
+// every device buffer of the network goes through these two
+template <class T>
+static lcs_status mlp_alloc(lcs_mlp* M, T** p, size_t bytes) {
+  void* q = nullptr;
+  if (M->alloc) {
+    q = M->alloc(bytes, M->alloc_ctx);
+  } else if (cudaMalloc(&q, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    q = nullptr;
+  }
+  *p = static_cast<T*>(q);
+  if (!q) return mfail(LCS_ENOMEM, "mlp: device allocation of %zu bytes failed", bytes);
+  return LCS_OK;
+}
+
+static void mlp_free(lcs_mlp* M, void* p) {
+  if (!p) return;
+  if (M->alloc) {
+    if (M->free) M->free(p, M->alloc_ctx);
+  } else {
+    cudaFree(p);
+  }
+}
 
 static unsigned long long host_splitmix(unsigned long long seed, unsigned long long i) {
   unsigned long long z = seed + (i + 1) * 0x9e3779b97f4a7c15ull;
@@ -348,24 +377,28 @@ static unsigned long long host_splitmix(unsigned long long seed, unsigned long l
 
 static lcs_status ensure_cap(lcs_mlp* M, int rows) {
   if (rows <= M->cap) return LCS_OK;
+  M_CUDA(cudaStreamSynchronize(M->stream));  // the old buffers may still be in use
+  M->cap = 0;
   float** bufs[] = {&M->Z1, &M->A1, &M->Z2, &M->A2, &M->dZ2, &M->dA1};
   for (float** b : bufs) {
-    cudaFree(*b);
+    mlp_free(M, *b);
     *b = nullptr;
-    M_CUDA(cudaMalloc(b, sizeof(float) * (size_t)rows * kHid));
+    if (lcs_status st = mlp_alloc(M, b, sizeof(float) * (size_t)rows * kHid)) return st;
   }
   float** small[] = {&M->y, &M->t, &M->dy};
   for (float** b : small) {
-    cudaFree(*b);
+    mlp_free(M, *b);
     *b = nullptr;
-    M_CUDA(cudaMalloc(b, sizeof(float) * (size_t)rows));
+    if (lcs_status st = mlp_alloc(M, b, sizeof(float) * (size_t)rows)) return st;
   }
-  cudaFree(M->states);
-  cudaFree(M->mask);
-  cudaFree(M->hs);
-  M_CUDA(cudaMalloc(&M->states, sizeof(unsigned long long) * (size_t)rows));
-  M_CUDA(cudaMalloc(&M->mask, sizeof(unsigned long long) * (size_t)rows));
-  M_CUDA(cudaMalloc(&M->hs, sizeof(int) * (size_t)rows));
+  mlp_free(M, M->states);
+  mlp_free(M, M->mask);
+  mlp_free(M, M->hs);
+  M->states = M->mask = nullptr;
+  M->hs = nullptr;
+  if (lcs_status st = mlp_alloc(M, &M->states, sizeof(unsigned long long) * (size_t)rows)) return st;
+  if (lcs_status st = mlp_alloc(M, &M->mask, sizeof(unsigned long long) * (size_t)rows)) return st;
+  if (lcs_status st = mlp_alloc(M, &M->hs, sizeof(int) * (size_t)rows)) return st;
   M->cap = rows;
   return LCS_OK;
 }
@@ -414,25 +447,39 @@ void lcs_mlp_destroy(lcs_mlp_t* M) {
   if (M->stream) cudaStreamSynchronize(M->stream);
   void* ptrs[] = {M->P, M->G, M->Mm, M->V, M->Z1, M->A1, M->Z2, M->A2, M->y, M->t, M->dy, M->dZ2, M->dA1,
                   M->states, M->mask, M->hs, M->sets, M->W2c, M->table, M->err};
-  for (void* p : ptrs) cudaFree(p);
+  for (void* p : ptrs) mlp_free(M, p);
   if (M->stream) cudaStreamDestroy(M->stream);
   delete M;
 }
 
 lcs_status lcs_mlp_create(uint64_t seed, lcs_mlp_t** out) {
+  return lcs_mlp_create_with_allocator(seed, nullptr, nullptr, nullptr, out);
+}
+
+lcs_status lcs_mlp_create_with_allocator(uint64_t seed, void* (*alloc)(size_t, void*), void (*free_fn)(void*, void*),
+                                         void* alloc_ctx, lcs_mlp_t** out) {
   if (!out) return mfail(LCS_EINVAL, "out is NULL");
   *out = nullptr;
-  lcs_mlp* M = new lcs_mlp();
+  if (alloc && !free_fn) return mfail(LCS_EINVAL, "alloc given without free");
+  lcs_mlp* M = new (std::nothrow) lcs_mlp();
+  if (!M) return mfail(LCS_ENOMEM, "host allocation");
   std::memset(M, 0, sizeof *M);
+  M->alloc = alloc;
+  M->free = free_fn;
+  M->alloc_ctx = alloc_ctx;
   cudaError_t e = cudaStreamCreateWithFlags(&M->stream, cudaStreamNonBlocking);
-  if (e == cudaSuccess) e = cudaMalloc(&M->P, sizeof(float) * kNParams);
-  if (e == cudaSuccess) e = cudaMalloc(&M->G, sizeof(float) * kNParams);
-  if (e == cudaSuccess) e = cudaMalloc(&M->Mm, sizeof(float) * kNParams);
-  if (e == cudaSuccess) e = cudaMalloc(&M->V, sizeof(float) * kNParams);
-  if (e == cudaSuccess) e = cudaMalloc(&M->sets, sizeof(TrainSet) * 8);
   if (e != cudaSuccess) {
     lcs_mlp_destroy(M);
-    return mfail(LCS_ENOMEM, "mlp: %s", cudaGetErrorString(e));
+    return mfail(LCS_ECUDA, "mlp stream: %s", cudaGetErrorString(e));
+  }
+  lcs_status st = mlp_alloc(M, &M->P, sizeof(float) * kNParams);
+  if (!st) st = mlp_alloc(M, &M->G, sizeof(float) * kNParams);
+  if (!st) st = mlp_alloc(M, &M->Mm, sizeof(float) * kNParams);
+  if (!st) st = mlp_alloc(M, &M->V, sizeof(float) * kNParams);
+  if (!st) st = mlp_alloc(M, &M->sets, sizeof(TrainSet) * 8);
+  if (st) {
+    lcs_mlp_destroy(M);
+    return st;
   }
   // uniform(-1/sqrt(fan_in), 1/sqrt(fan_in)) from SplitMix64; biases zero
   std::vector<float> h(kNParams, 0.f);
@@ -567,11 +614,13 @@ lcs_status lcs_mlp_train(lcs_mlp_t* M, int n_sets, const int64_t* const* vectors
 
 // the BF16 prediction table of shape h (mlp_tc.cu) into M->table
 static lcs_status build_table(lcs_mlp* M, int h) {
-  if (!M->W2c) {
-    M_CUDA(cudaMalloc(&M->W2c, mlp_w2c_bytes()));
-    M_CUDA(cudaMalloc(&M->table, sizeof(float) * (size_t)mlp_table_rows(kHin)));
-    M_CUDA(cudaMalloc(&M->err, sizeof(int)));
-  }
+  // made on first use; after a failed allocation the next call retries the missing ones
+  if (!M->W2c)
+    if (lcs_status st = mlp_alloc(M, &M->W2c, mlp_w2c_bytes())) return st;
+  if (!M->table)
+    if (lcs_status st = mlp_alloc(M, &M->table, sizeof(float) * (size_t)mlp_table_rows(kHin))) return st;
+  if (!M->err)
+    if (lcs_status st = mlp_alloc(M, &M->err, sizeof(int))) return st;
   M_CUDA(mlp_table_tc(M->P, h, M->table, M->W2c, M->err, M->stream));
   int err = 0;
   M_CUDA(cudaMemcpyAsync(&err, M->err, sizeof(int), cudaMemcpyDeviceToHost, M->stream));

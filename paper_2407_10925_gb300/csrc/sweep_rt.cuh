@@ -89,7 +89,9 @@ __device__ __forceinline__ void rt_tail_parts(const RtGeo<SIG>& g, int h, unsign
 // the terms m0 .. m1-1 of M(z, S) from vector v: strings in S keep head z and
 // their tail, the others advance and take every letter c; term m is the c
 // whose base-sigma digits, least significant first, are the letters of the
-// advanced strings from the last one back
+// advanced strings from the last one back.  The addresses do not depend on
+// the loaded values, so the walk forms four of them before it loads: four
+// loads in flight per thread instead of one.
 template <int SIG>
 __device__ __forceinline__ long long rt_sum_range(const RtGeo<SIG>& g, const unsigned long long (&tp)[kMaxD], int z,
                                                   unsigned S, const long long* __restrict__ v, unsigned long long m0,
@@ -113,19 +115,78 @@ __device__ __forceinline__ long long rt_sum_range(const RtGeo<SIG>& g, const uns
     m /= SIG;
     off += (unsigned long long)c[i] * w[i];
   }
-  long long s = 0;
-  for (unsigned long long t = m0; t < m1; ++t) {
-    s += ld_vec<false>(v + base + off);
+  const long long* vb = v + base;
+  if (n >= 2 && SIG <= 8 && m0 % SIG == 0 && m1 % SIG == 0) {
+    // whole runs of the lowest digit: SIG loads at off + c0 w[0] per step of
+    // the higher digits, two steps at a time -- 2 SIG loads in flight
+    auto step_hi = [&]() {
+      for (int i = 1; i < n; ++i) {
+        if (++c[i] < SIG) {
+          off += w[i];
+          return;
+        }
+        c[i] = 0;
+        off -= (unsigned long long)(SIG - 1) * w[i];
+      }
+    };
+    const unsigned long long w0 = w[0];
+    long long acc[SIG];
+#pragma unroll
+    for (int j = 0; j < SIG; ++j) acc[j] = 0;
+    unsigned long long t = m0;
+    for (; t + 2 * SIG <= m1; t += 2 * SIG) {
+      const unsigned long long oa = off;
+      step_hi();
+      const unsigned long long ob = off;
+      step_hi();
+      long long la[SIG], lb[SIG];
+#pragma unroll
+      for (int j = 0; j < SIG; ++j) la[j] = ld_vec<false>(vb + oa + j * w0);
+#pragma unroll
+      for (int j = 0; j < SIG; ++j) lb[j] = ld_vec<false>(vb + ob + j * w0);
+#pragma unroll
+      for (int j = 0; j < SIG; ++j) acc[j] += la[j] + lb[j];
+    }
+    if (t < m1) {
+#pragma unroll
+      for (int j = 0; j < SIG; ++j) acc[j] += ld_vec<false>(vb + off + j * w0);
+    }
+    long long sum = 0;
+#pragma unroll
+    for (int j = 0; j < SIG; ++j) sum += acc[j];
+    return sum;
+  }
+  auto step = [&]() {
     for (int i = 0; i < n; ++i) {
       if (++c[i] < SIG) {
         off += w[i];
-        break;
+        return;
       }
       c[i] = 0;
       off -= (unsigned long long)(SIG - 1) * w[i];
     }
+  };
+  long long s0 = 0, s1 = 0, s2 = 0, s3 = 0;
+  unsigned long long t = m0;
+  for (; t + 4 <= m1; t += 4) {
+    const unsigned long long o0 = off;
+    step();
+    const unsigned long long o1 = off;
+    step();
+    const unsigned long long o2 = off;
+    step();
+    const unsigned long long o3 = off;
+    step();
+    s0 += ld_vec<false>(vb + o0);
+    s1 += ld_vec<false>(vb + o1);
+    s2 += ld_vec<false>(vb + o2);
+    s3 += ld_vec<false>(vb + o3);
   }
-  return s;
+  for (; t < m1; ++t) {
+    s0 += ld_vec<false>(vb + off);
+    step();
+  }
+  return (s0 + s1) + (s2 + s3);
 }
 
 // every term of M(z, S)
@@ -138,35 +199,73 @@ __device__ __forceinline__ long long rt_sum(const RtGeo<SIG>& g, const unsigned 
 // the table entry of (z, S): S = {} is shared by every z
 __device__ __forceinline__ int rt_entry(int z, unsigned S, int d) { return S ? (z << d) | (int)S : 0; }
 
+// the terms one of `parts` threads or lanes sums: a whole number of runs of
+// the lowest digit (terms = sigma^k is a multiple of sigma)
+template <int SIG>
+__device__ __forceinline__ unsigned long long rt_chunk(unsigned long long terms, unsigned parts) {
+  const unsigned long long per = (terms + parts - 1) / parts;
+  return (per + SIG - 1) / SIG * SIG;
+}
+
+constexpr unsigned long long kRtWarpTerms = 32;  // entries with this many terms or more: one warp each
+constexpr unsigned long long kRtCtaTerms = 512;  // entries with this many terms or more: the whole CTA
+
 // The table of one tail tuple.  An entry's terms are loads that mostly miss
-// the caches, and the largest entry (every string advances) has sigma^d of
-// them: entries of 32 terms or more go to a whole warp, each lane summing a
-// contiguous block, the rest to single threads.
+// the caches; the entry where every string advances has sigma^d of them.  So
+// the work is split by size: entries of fewer than 32 terms go to single
+// threads, those up to 512 to one warp each (lanes sum contiguous blocks),
+// and the largest to the whole CTA (every thread a contiguous block, the sums
+// meeting in the table through shared-memory atomics).  The caller
+// synchronises before and after.
 template <int SIG>
 __device__ __forceinline__ void rt_fill_table(const RtGeo<SIG>& g, const unsigned long long (&tp)[kMaxD],
                                               const long long* const* vs, long long* table) {
   const int entries = SIG << g.d;
+  auto used = [&](int e) {
+    const unsigned S = (unsigned)e & g.full;
+    return !(S == g.full || (S == 0 && (e >> g.d) > 0));  // no candidate / shared entry
+  };
+  const bool cta_entries = g.sd >= kRtCtaTerms;  // uniform: the largest entry has sigma^d terms
+  if (cta_entries) {  // the CTA-wide entries start at zero
+    for (int e = threadIdx.x; e < entries; e += blockDim.x)
+      if (used(e) && g.pw[g.d - __popc((unsigned)e & g.full)] >= kRtCtaTerms) table[e] = 0;
+    __syncthreads();
+  }
   for (int e = threadIdx.x; e < entries; e += blockDim.x) {
+    if (!used(e)) continue;
     const int z = e >> g.d;
     const unsigned S = (unsigned)e & g.full;
-    if (S == g.full || (S == 0 && z > 0)) continue;  // no candidate / shared entry
     const int k = g.d - __popc(S);
-    if (g.pw[k] < 32) table[e] = rt_sum<SIG>(g, tp, z, S, vs[k - 1]);
+    if (g.pw[k] < kRtWarpTerms) table[e] = rt_sum<SIG>(g, tp, z, S, vs[k - 1]);
   }
   const int lane = threadIdx.x & 31;
   for (int e = threadIdx.x >> 5; e < entries; e += blockDim.x >> 5) {  // uniform over the warp
+    if (!used(e)) continue;
     const int z = e >> g.d;
     const unsigned S = (unsigned)e & g.full;
-    if (S == g.full || (S == 0 && z > 0)) continue;
     const int k = g.d - __popc(S);
     const unsigned long long terms = g.pw[k];
-    if (terms < 32) continue;
-    const unsigned long long per = (terms + 31) / 32;
+    if (terms < kRtWarpTerms || terms >= kRtCtaTerms) continue;
+    const unsigned long long per = rt_chunk<SIG>(terms, 32);
     const unsigned long long m0 = min(terms, (unsigned long long)lane * per), m1 = min(terms, m0 + per);
     long long sum = rt_sum_range<SIG>(g, tp, z, S, vs[k - 1], m0, m1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0) table[e] = sum;
+  }
+  for (int e = 0; cta_entries && e < entries; ++e) {  // uniform over the CTA
+    if (!used(e)) continue;
+    const int z = e >> g.d;
+    const unsigned S = (unsigned)e & g.full;
+    const int k = g.d - __popc(S);
+    const unsigned long long terms = g.pw[k];
+    if (terms < kRtCtaTerms) continue;
+    const unsigned long long per = rt_chunk<SIG>(terms, blockDim.x);
+    const unsigned long long m0 = min(terms, (unsigned long long)threadIdx.x * per), m1 = min(terms, m0 + per);
+    long long sum = rt_sum_range<SIG>(g, tp, z, S, vs[k - 1], m0, m1);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(table + e), (unsigned long long)sum);
   }
 }
 

@@ -159,7 +159,9 @@ def test_binding_signatures_match_the_header(L):
         assert ret in want_res, (name, ret)
         assert fn.restype == want_res[ret], (name, ret, fn.restype)
         for param, ct in zip(params, fn.argtypes):
-            if "*" in param:  # any pointer: void*, char*, or a pointer to a struct or scalar
+            if re.search(r"\(\s*\*\s*\w+\s*\)\s*\(", param):  # a function pointer: a ctypes callback type
+                assert issubclass(ct, ctypes._CFuncPtr), (name, param, ct)
+            elif "*" in param:  # any other pointer: void*, char*, or a pointer to a struct or scalar
                 assert ct in (ctypes.c_void_p, ctypes.c_char_p) or issubclass(ct, ctypes._Pointer), (name, param, ct)
             else:
                 ctype = param.replace("const ", "").split()[0]

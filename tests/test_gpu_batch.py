@@ -91,9 +91,16 @@ def test_batch_config3_shapes_match_single_handles(lb, mode):
         assert info["persistent_ms_per_iter"] > 0 and info["concurrent_ms_per_iter"] > 0
         if mode is None:
             assert info["mode"] == (1 if info["concurrent_ms_per_iter"] < info["persistent_ms_per_iter"] else 0)
+        assert info["min_ctas_per_sm"] in (2, 4)
+        total = iters
+        if mode == 0:  # the persistent launch was captured in a CUDA graph
+            assert info["graph_captured"] == 1 and info["graph"] == 1
+            b.iterate(iters)  # a call of the same length replays the captured graph
+            total += iters
+            assert b.info()["graph_replays"] >= 1
         for i, (s, d, h) in enumerate(shapes):
             with lb.LcsBound(s, d, h, check_every=20) as one:
-                one.iterate(iters)
+                one.iterate(total)
                 assert np.array_equal(b.export_fx(i, 0), one.export_fx(0)), i
                 assert b.read(i) == one.read(), i
 

@@ -308,18 +308,27 @@ def test_torch_allocator_and_stream(lb, torch_mod):
 
 
 def test_timing_stats(lb):
+    n = 4 ** 6 // 2
     with lb.LcsBound(2, 2, 6, timing=1, check_every=10) as hnd:
         hnd.iterate(30)
         st = hnd.stats()
-        assert st["sweep_launches"] == 30 and st["check_launches"] == 3
-        assert st["sweep_ms"] > 0 and st["check_ms"] > 0
         # at h >= 6 the zero start runs the kernel that also uses the string
-        # swap: 20 algorithmic bytes per stored state instead of 8 (d+1) = 24
-        assert st["sweep_bytes"] == 30 * 20 * (4 ** 6 // 2)
-        assert st["check_bytes"] == 3 * 8 * (4 ** 6 // 2)
-    with lb.LcsBound(2, 2, 5, timing=1) as hnd:
-        hnd.iterate(4)
-        assert hnd.stats()["sweep_bytes"] == 4 * 24 * (4 ** 5 // 2)
+        # swap: 20 algorithmic bytes per stored state instead of 8 (d+1) = 24.
+        # The checks of iterations 10 and 20 ran inside sweeps 11 and 21 (4
+        # more bytes per stored state each); the check of iteration 30 waits
+        # for the next sweep or for a call that reads results.
+        assert st["sweep_launches"] == 30 and st["check_launches"] == 0
+        assert st["sweep_ms"] > 0
+        assert st["sweep_bytes"] == 30 * 20 * n + 2 * 4 * n
+        hnd.read()
+        st = hnd.stats()
+        assert st["check_launches"] == 1 and st["check_ms"] > 0 and st["check_bytes"] == 8 * n
+    with lb.LcsBound(2, 2, 5, timing=1, check_every=10) as hnd:  # no fused kernel: every check on its own
+        hnd.iterate(30)
+        st = hnd.stats()
+        assert st["sweep_launches"] == 30 and st["check_launches"] == 3
+        assert st["sweep_bytes"] == 30 * 24 * (4 ** 5 // 2)
+        assert st["check_bytes"] == 3 * 8 * (4 ** 5 // 2)
 
 
 # ---------------------------------------------------------------------------

@@ -8,6 +8,8 @@ produces for one checked iteration -- the new iterate, R and its state -- on
 consecutive calls that share that array.  Results are integers: compared
 exactly.  This file is collected last.
 """
+import gc
+
 import numpy as np
 import pytest
 
@@ -91,12 +93,13 @@ def test_noalloc_allocates_nothing_and_runs_on_a_caller_stream(env):
     torch.cuda.synchronize()
     lb.lcs_sweep_incr_fx_noalloc(s, d, h, dev, out, R, arg, stream=stream.cuda_stream)  # warm-up
     stream.synchronize()
-    free0, _ = torch.cuda.mem_get_info()
-    alloc0 = torch.cuda.memory_allocated()
+    gc.collect()  # tensors of earlier tests are freed now, not in the middle of the checks
     for _ in range(3):
         out.fill_(0)
         R.fill_(-1)
         torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        alloc0 = torch.cuda.memory_allocated()
         lb.lcs_sweep_incr_fx_noalloc(s, d, h, dev, out, R, arg, stream=stream.cuda_stream)
         stream.synchronize()
         assert torch.cuda.mem_get_info()[0] == free0
