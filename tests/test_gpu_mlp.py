@@ -206,3 +206,44 @@ def test_stored_fixed_point_start_equals_the_double_start(lb):
         b.iterate(30)
         assert np.array_equal(a.export_fx(0), b.export_fx(0))
         assert a.read() == b.read()
+
+
+def _iterations_to(lb, H, target, start=None, limit=400):
+    """iterations of Algorithm 2 (a check after every one) until the bound reaches target"""
+    with lb.LcsBound(2, 2, H, check_every=1) as hnd:
+        if start is not None:
+            hnd.set_start(start)
+        for it in range(1, limit + 1):
+            hnd.iterate(1)
+            if hnd.read()[0] >= target:
+                return it
+    return None
+
+
+def test_learned_start_reaches_the_bound_in_fewer_iterations(lb):
+    """What the trained network gains: iterations until the bound comes within
+    1e-7 of the zero start's converged bound at h = 10, from the zero start
+    (the method), from the prefix-truncation lift of h = 8 (the non-learned
+    control) and from the network trained on the converged iterates of
+    h = 6, 7, 8.  The learned start must need fewer iterations than the zero
+    start; all three reach the same rigorous bound (Lemma 1: the check
+    decides it)."""
+    import torch
+
+    H, train_h = 10, (6, 7, 8)
+    ref = _converged(lb, H, iters=2000)[1][0]
+    target = ref - 1e-7
+    it_zero = _iterations_to(lb, H, target)
+    data = {h: _converged(lb, h, iters=1000) for h in train_h}
+    r_hat = data[max(train_h)][1][2]
+    newest = torch.empty(4 ** H, dtype=torch.float64, device="cuda")
+    older = torch.empty(4 ** H, dtype=torch.float64, device="cuda")
+    lb.lcs_lift_prefix(max(train_h), H, data[max(train_h)][0], r_hat, newest, older)
+    it_lift = _iterations_to(lb, H, target, [newest, older])
+    with lb.LcsMlp(seed=2024) as m:
+        m.train([data[h][0] for h in train_h], list(train_h), steps=1000, batch=4096, lr=1e-3)
+        m.start_vectors(H, r_hat, newest, older)
+    it_mlp = _iterations_to(lb, H, target, [newest, older])
+    print(f"h = {H}: iterations to the bound - 1e-7: zero start {it_zero}, prefix lift {it_lift}, learned {it_mlp}")
+    assert it_zero is not None and it_lift is not None and it_mlp is not None
+    assert it_mlp < it_zero
