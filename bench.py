@@ -622,8 +622,9 @@ def run_outofcore(args, cfg, world, rank, local_rank):
     t_create = time.perf_counter() - t0
     n_stored = hnd.n_stored
     it, bound, history, reached = 0, 0.0, [], None
+    max_iters = args.bound_iters if args.bound_iters is not None else cfg["max_iters"]
     with ClockSampler(local_rank) as clk:
-        while it < cfg["max_iters"]:
+        while it < max_iters:
             hnd.iterate(C)
             it += C
             bound = hnd.read()[0]
@@ -810,25 +811,30 @@ def main():
         except lb.LcsError:
             n_orb = None
         forms = {}
+        # the host vectors come from lcs_host_alloc (pinned, huge-page advised)
         if n_orb:
-            start_orb = hnd.export_orbit_fx(0, out=torch.empty(n_orb, dtype=torch.int64, pin_memory=True))
-            forms["orbit_form"] = entry(e2e_run(lambda: hnd.set_start_orbit_fx([start_orb] * d)), d * n_orb * 8,
-                                        "lcs_bound_set_start_orbit_fx from pinned host (d vectors in orbit form)"
-                                        + read_what, start_orb)
-            del start_orb
+            with lb.HostBuffer(n_orb) as buf:
+                start_orb = torch.from_numpy(hnd.export_orbit_fx(0, out=buf.array))
+                forms["orbit_form"] = entry(e2e_run(lambda: hnd.set_start_orbit_fx([start_orb] * d)), d * n_orb * 8,
+                                            "lcs_bound_set_start_orbit_fx from pinned host (d vectors in orbit form)"
+                                            + read_what, start_orb)
+                del start_orb
         n_st = hnd.n_stored
-        start_st = hnd.export_stored_fx(0, out=torch.empty(n_st, dtype=torch.int64, pin_memory=True))
-        forms["stored_form"] = entry(e2e_run(lambda: hnd.set_start_stored_fx([start_st] * d)), d * n_st * 8,
-                                     "lcs_bound_set_start_stored_fx from pinned host (d vectors in stored form)"
-                                     + read_what, start_st)
-        del start_st
-        start = hnd.export_fx(0, out=torch.empty(n, dtype=torch.int64, pin_memory=True))
-        forms["full_vectors"] = entry(e2e_run(lambda: hnd.set_start_fx([start] * d)), d * n * 8,
-                                      "lcs_bound_set_start_fx from pinned host (every state, symmetry verified on "
-                                      "the device)" + read_what, start)
-        del start
+        with lb.HostBuffer(n_st) as buf:
+            start_st = torch.from_numpy(hnd.export_stored_fx(0, out=buf.array))
+            forms["stored_form"] = entry(e2e_run(lambda: hnd.set_start_stored_fx([start_st] * d)), d * n_st * 8,
+                                         "lcs_bound_set_start_stored_fx from pinned host (d vectors in stored form)"
+                                         + read_what, start_st)
+            del start_st
+        with lb.HostBuffer(n) as buf:
+            start = torch.from_numpy(hnd.export_fx(0, out=buf.array))
+            forms["full_vectors"] = entry(e2e_run(lambda: hnd.set_start_fx([start] * d)), d * n * 8,
+                                          "lcs_bound_set_start_fx from pinned host (every state, symmetry verified "
+                                          "on the device)" + read_what, start)
+            del start
         head = "orbit_form" if n_orb else "stored_form"
-        e2e = {"unit": "state-updates/s", "d2h_bytes_per_step": 80, **forms.pop(head), "form": head, **forms}
+        e2e = {"unit": "state-updates/s", "d2h_bytes_per_step": 80, **forms.pop(head), "form": head,
+               "host_buffers": "lcs_host_alloc: pinned, mapped, advised for huge pages", **forms}
 
     # wall time to the rigorous bound: a fresh handle from the zero start,
     # create .. iterate(bound_iters) .. read, checks every 100 iterations

@@ -338,6 +338,18 @@ lcs_status lcs_bound_synchronize(lcs_bound_t* hnd);
  * NULL is ignored. */
 void lcs_bound_destroy(lcs_bound_t* hnd);
 
+/* Host buffers for transfers (no counterpart in the paper): bytes of host
+ * memory, pinned and mapped for the device, from an anonymous mapping aligned
+ * to 512 MiB and advised for transparent huge pages.  Any call that takes a
+ * host vector accepts them.  On this GB300's host link they keep the link's
+ * rate from their first use, where parts of ordinary pinned buffers were
+ * read at a fraction of it in processes that followed heavy use of the
+ * machine.  The memory is not initialised.  lcs_host_free releases a buffer
+ * of lcs_host_alloc (LCS_EINVAL for any other pointer; NULL is ignored).
+ * Synchronous. */
+lcs_status lcs_host_alloc(size_t bytes, void** out);
+lcs_status lcs_host_free(void* ptr);
+
 /* Static text of a status code. */
 const char* lcs_bound_errstr(lcs_status st);
 

@@ -165,6 +165,8 @@ def lib():
                 "lcs_lift_prefix": [i32, i32, vp, i32, dbl, vp, vp],
                 "lcs_fp32_experiment": [i32, i32, i32, i64, dbl, vp, P(dbl)],
                 "lcs_sweep_fx": [i32, i32, i32, i32, i32, vp, vp, vp],
+                "lcs_host_alloc": [ctypes.c_size_t, P(vp)],
+                "lcs_host_free": [vp],
                 "lcs_sweep_incr_fx_noalloc": [i32, i32, i32, i32, i32, vp, vp, vp, vp, vp],
             }
             for name, args in sig.items():
@@ -601,6 +603,39 @@ class LcsBatch:
     def set_mode(self, mode):
         """0: the persistent launch, 1: concurrent single-instance kernels (before the first iteration)."""
         lcs_bound_batch_set_mode(self.hnd, mode)
+
+
+class HostBuffer:
+    """n int64 values of host memory from lcs_host_alloc (pinned, mapped, huge-page advised) as a numpy array.
+
+    Keep this object alive while the array is in use; close() (or the end of
+    a with-block) frees the memory.
+    """
+
+    def __init__(self, n, dtype=np.int64):
+        self.ptr = ctypes.c_void_p()
+        nbytes = int(n) * np.dtype(dtype).itemsize
+        _check(lib().lcs_host_alloc(nbytes, ctypes.byref(self.ptr)), "lcs_host_alloc")
+        buf = (ctypes.c_char * nbytes).from_address(self.ptr.value)
+        self.array = np.frombuffer(buf, dtype=dtype, count=int(n))
+
+    def close(self):
+        if self.ptr:
+            self.array = None
+            _check(lib().lcs_host_free(self.ptr), "lcs_host_free")
+            self.ptr = ctypes.c_void_p()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def lcs_fp32_experiment(sigma, d, h, n_iters, rho, newest_dev):

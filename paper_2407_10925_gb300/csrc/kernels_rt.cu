@@ -12,9 +12,11 @@ const KernelSet* kernels_rt(int sigma) {
 }
 
 // threads' worth of work of one general sweep or check, for sizing its grid:
-// one CTA per tail tuple, or one warp per state (sigma = 2, d >= kRtWarpD)
+// one CTA per tail tuple, one warp per tail tuple (small tables, many
+// tuples), or one warp per state (sigma = 2, d >= kRtWarpD)
 unsigned long long rt_work_items(int sigma, int d, unsigned long long n_states, unsigned long long n_tail) {
-  return sigma == 2 && d >= kRtWarpD ? n_states * 32 : n_tail * kBlock;
+  if (sigma == 2 && d >= kRtWarpD) return n_states * 32;
+  return rt_warp_tails(sigma, d, n_tail) ? n_tail * 32 : n_tail * kBlock;
 }
 
 }  // namespace lcs

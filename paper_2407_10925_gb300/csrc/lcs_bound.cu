@@ -13,10 +13,13 @@
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <mutex>
 #include <new>
 #include <string>
 #include <vector>
+
+#include <sys/mman.h>
 
 #include "../../include/lcs_bound.h"
 #include "batch.h"
@@ -325,8 +328,11 @@ struct lcs_bound {
   size_t elem;
   long long* offs;
   // opts.host_slots: the ring rows placed in pinned host memory (read and
-  // written by the kernels over the host link); host_base = their allocations
+  // written by the kernels over the host link); host_base / host_len = their
+  // mappings
   void* host_base[kMaxD + 1];
+  size_t host_len[kMaxD + 1];
+  void* host_ptr[kMaxD + 1];  // the registered (aligned) start of each
   long long* ubuf;
   DevState* dstate;
   RedPartial* partials;
@@ -362,6 +368,35 @@ struct lcs_bound {
   int last_check_grid;
   int d_batch_worst;  // batch handles: d of the instance with the largest sigma^d
 };
+
+// Host memory for the device: an anonymous mapping aligned to 512 MiB,
+// advised for transparent huge pages, then pinned and mapped into the
+// device's address space (cudaHostRegister).  On this GB300's host link a
+// transfer from such memory keeps the link's rate from its first use: in
+// processes that followed heavy use of the machine, parts of ordinary pinned
+// buffers (cudaHostAlloc) were read at 16-40 GB/s the first time, and a
+// kernel gathering from 128 GiB of ordinary pages ran several times slower.
+// Returns the registered start; *base / *len describe the mapping.
+static void* host_map_alloc(size_t bytes, void** base, size_t* len) {
+  const size_t align = (size_t)512 << 20;
+  *len = bytes + align;
+  void* m = mmap(nullptr, *len, PROT_READ | PROT_WRITE, MAP_PRIVATE | MAP_ANONYMOUS, -1, 0);
+  if (m == MAP_FAILED) return nullptr;
+  char* hp = (char*)(((uintptr_t)m + align - 1) / align * align);
+  madvise(hp, bytes, MADV_HUGEPAGE);  // a hint: without huge pages the memory still works
+  if (cudaHostRegister(hp, bytes, cudaHostRegisterPortable | cudaHostRegisterMapped) != cudaSuccess) {
+    cudaGetLastError();
+    munmap(m, *len);
+    return nullptr;
+  }
+  *base = m;
+  return hp;
+}
+
+static void host_map_free(void* p, void* base, size_t len) {
+  cudaHostUnregister(p);
+  munmap(base, len);
+}
 
 static void* dev_alloc(lcs_bound* H, size_t bytes) {
   if (H->opts.alloc) return H->opts.alloc(bytes, H->opts.alloc_ctx);
@@ -449,6 +484,38 @@ const char* lcs_bound_errstr(lcs_status st) {
 
 const char* lcs_bound_last_error(void) { return g_last_error.c_str(); }
 
+// buffers of lcs_host_alloc: registered start -> (mapping, length)
+static std::mutex g_host_mutex;
+static std::map<void*, std::pair<void*, size_t>> g_host_maps;
+
+lcs_status lcs_host_alloc(size_t bytes, void** out) {
+  if (!out) return fail(LCS_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (bytes == 0) return fail(LCS_EINVAL, "0 bytes");
+  void* base = nullptr;
+  size_t len = 0;
+  void* p = host_map_alloc(bytes, &base, &len);
+  if (!p) return fail(LCS_ENOMEM, "%zu bytes of pinned host memory", bytes);
+  std::lock_guard<std::mutex> lock(g_host_mutex);
+  g_host_maps[p] = {base, len};
+  *out = p;
+  return LCS_OK;
+}
+
+lcs_status lcs_host_free(void* p) {
+  if (!p) return LCS_OK;
+  std::pair<void*, size_t> m;
+  {
+    std::lock_guard<std::mutex> lock(g_host_mutex);
+    auto it = g_host_maps.find(p);
+    if (it == g_host_maps.end()) return fail(LCS_EINVAL, "not a buffer of lcs_host_alloc");
+    m = it->second;
+    g_host_maps.erase(it);
+  }
+  host_map_free(p, m.first, m.second);
+  return LCS_OK;
+}
+
 lcs_status lcs_bound_synchronize(lcs_bound_t* H) {
   if (!H) return fail(LCS_EINVAL, "handle is NULL");
   LCS_CUDA(cudaStreamSynchronize(H->stream));
@@ -470,10 +537,11 @@ void lcs_bound_destroy(lcs_bound_t* H) {
   }
   if (H->batch) batch_destroy(H->batch);
   for (int k = 0; k <= H->d; ++k) {
-    if (H->host_base[k])
-      cudaFreeHost(H->host_base[k]);
-    else
+    if (H->host_base[k]) {
+      host_map_free(H->host_ptr[k], H->host_base[k], H->host_len[k]);
+    } else {
       dev_free(H, H->ring[k]);
+    }
   }
   dev_free(H, H->offs);
   dev_free(H, H->check_partials);
@@ -600,18 +668,26 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   const size_t vbytes = (size_t)H->n_stored * H->elem;
   for (int k = 0; k <= d; ++k) {
     if (k >= d + 1 - opts.host_slots) {
-      // a row in pinned host memory, mapped into the device's address space
-      void* hp = nullptr;
+      // A row in pinned host memory mapped into the device's address space
+      // (host_map_alloc: the kernels gather from all of it at once, and large
+      // pages keep the device's translations few -- a 128 GiB row of 64 KiB
+      // pages needs two million).
+      void* base = nullptr;
+      size_t len = 0;
+      void* hp = host_map_alloc(vbytes, &base, &len);
       void* dp = nullptr;
-      e = cudaHostAlloc(&hp, vbytes, cudaHostAllocPortable | cudaHostAllocMapped);
-      if (e == cudaSuccess) e = cudaHostGetDevicePointer(&dp, hp, 0);
-      if (e != cudaSuccess) {
+      if (hp && cudaHostGetDevicePointer(&dp, hp, 0) != cudaSuccess) {
         cudaGetLastError();
-        if (hp) cudaFreeHost(hp);
+        host_map_free(hp, base, len);
+        hp = nullptr;
+      }
+      if (!hp) {
         lcs_bound_destroy(H);
         return fail(LCS_ENOMEM, "iterate vector %d in pinned host memory (%zu bytes)", k, vbytes);
       }
-      H->host_base[k] = hp;
+      H->host_base[k] = base;
+      H->host_len[k] = len;
+      H->host_ptr[k] = hp;
       H->ring[k] = (long long*)dp;
       continue;
     }

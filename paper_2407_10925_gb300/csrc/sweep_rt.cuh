@@ -40,6 +40,15 @@ namespace lcs {
 
 constexpr int kRtTable = 6000;  // entries of the shared table (47 KiB; the static limit is 48 KiB)
 constexpr int kRtWarpD = 9;     // sigma = 2: one warp per state from this d on
+// one warp per tail tuple, each with a table of its own, when a table holds
+// at most this many entries and there are enough tuples to fill the GPU
+constexpr int kRtWarpTable = kRtTable / (kBlock / 32);
+constexpr unsigned long long kRtWarpTails = 1ull << 13;
+
+// one warp per tail tuple (host side: the same rule as the launch)
+inline bool rt_warp_tails(int sigma, int d, unsigned long long n_tail) {
+  return ((unsigned long long)sigma << d) <= (unsigned long long)kRtWarpTable && n_tail >= kRtWarpTails;
+}
 
 template <int SIG>
 struct RtGeo {
@@ -199,24 +208,26 @@ __device__ __forceinline__ long long rt_sum(const RtGeo<SIG>& g, const unsigned 
 // the table entry of (z, S): S = {} is shared by every z
 __device__ __forceinline__ int rt_entry(int z, unsigned S, int d) { return S ? (z << d) | (int)S : 0; }
 
-// the terms one of `parts` threads or lanes sums: a whole number of runs of
-// the lowest digit (terms = sigma^k is a multiple of sigma)
+// the terms one of `parts` threads or lanes sums: for sigma <= 8 a whole
+// number of runs of the lowest digit (terms = sigma^k is a multiple of sigma)
 template <int SIG>
 __device__ __forceinline__ unsigned long long rt_chunk(unsigned long long terms, unsigned parts) {
   const unsigned long long per = (terms + parts - 1) / parts;
-  return (per + SIG - 1) / SIG * SIG;
+  return SIG <= 8 ? (per + SIG - 1) / SIG * SIG : per;  // rt_sum_range unrolls the runs up to sigma = 8
 }
 
 constexpr unsigned long long kRtWarpTerms = 32;  // entries with this many terms or more: one warp each
-constexpr unsigned long long kRtCtaTerms = 512;  // entries with this many terms or more: the whole CTA
+constexpr unsigned long long kRtCtaTerms = 2048;  // entries with this many terms or more: the whole CTA
 
 // The table of one tail tuple.  An entry's terms are loads that mostly miss
 // the caches; the entry where every string advances has sigma^d of them.  So
 // the work is split by size: entries of fewer than 32 terms go to single
-// threads, those up to 512 to one warp each (lanes sum contiguous blocks),
+// threads, those up to 2048 to one warp each (lanes sum contiguous blocks),
 // and the largest to the whole CTA (every thread a contiguous block, the sums
-// meeting in the table through shared-memory atomics).  The caller
-// synchronises before and after.
+// meeting in the table through shared-memory atomics).  The CTA-wide entries
+// are enumerated directly (every S of d - k strings kept, by Gosper's
+// next-combination step), so no thread walks the whole table for them.  The
+// caller synchronises before and after.
 template <int SIG>
 __device__ __forceinline__ void rt_fill_table(const RtGeo<SIG>& g, const unsigned long long (&tp)[kMaxD],
                                               const long long* const* vs, long long* table) {
@@ -253,19 +264,54 @@ __device__ __forceinline__ void rt_fill_table(const RtGeo<SIG>& g, const unsigne
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
     if (lane == 0) table[e] = sum;
   }
-  for (int e = 0; cta_entries && e < entries; ++e) {  // uniform over the CTA
-    if (!used(e)) continue;
-    const int z = e >> g.d;
-    const unsigned S = (unsigned)e & g.full;
-    const int k = g.d - __popc(S);
+  // uniform over the CTA: k advanced strings, from every string down
+  for (int k = g.d; cta_entries && k >= 1 && g.pw[k] >= kRtCtaTerms; --k) {
     const unsigned long long terms = g.pw[k];
-    if (terms < kRtCtaTerms) continue;
     const unsigned long long per = rt_chunk<SIG>(terms, blockDim.x);
     const unsigned long long m0 = min(terms, (unsigned long long)threadIdx.x * per), m1 = min(terms, m0 + per);
+    unsigned S = (1u << (g.d - k)) - 1;  // the smallest set of d - k kept strings
+    while (S < g.full) {
+      for (int z = 0; z < (S ? SIG : 1); ++z) {  // S = {}: one entry for every z
+        long long sum = rt_sum_range<SIG>(g, tp, z, S, vs[k - 1], m0, m1);
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+        if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(table + rt_entry(z, S, g.d)), (unsigned long long)sum);
+      }
+      if (S == 0) break;
+      const unsigned c = S & (0u - S), r = S + c;
+      S = (((r ^ S) >> 2) / c) | r;  // the next set of the same size
+    }
+  }
+}
+
+// The table of one tail tuple filled by one warp (the warp-per-tuple form):
+// entries below 32 terms by single lanes, the others by the whole warp.  The
+// caller synchronises the warp before and after.
+template <int SIG>
+__device__ __forceinline__ void rt_fill_table_warp(const RtGeo<SIG>& g, const unsigned long long (&tp)[kMaxD],
+                                                   const long long* const* vs, long long* table) {
+  const int entries = SIG << g.d;
+  const int lane = threadIdx.x & 31;
+  for (int e = lane; e < entries; e += 32) {
+    const int z = e >> g.d;
+    const unsigned S = (unsigned)e & g.full;
+    if (S == g.full || (S == 0 && z > 0)) continue;
+    const int k = g.d - __popc(S);
+    if (g.pw[k] < kRtWarpTerms) table[e] = rt_sum<SIG>(g, tp, z, S, vs[k - 1]);
+  }
+  for (int e = 0; e < entries; ++e) {  // uniform over the warp
+    const int z = e >> g.d;
+    const unsigned S = (unsigned)e & g.full;
+    if (S == g.full || (S == 0 && z > 0)) continue;
+    const int k = g.d - __popc(S);
+    const unsigned long long terms = g.pw[k];
+    if (terms < kRtWarpTerms) continue;
+    const unsigned long long per = rt_chunk<SIG>(terms, 32);
+    const unsigned long long m0 = min(terms, (unsigned long long)lane * per), m1 = min(terms, m0 + per);
     long long sum = rt_sum_range<SIG>(g, tp, z, S, vs[k - 1], m0, m1);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    if (lane == 0) atomicAdd(reinterpret_cast<unsigned long long*>(table + e), (unsigned long long)sum);
+    if (lane == 0) table[e] = sum;
   }
 }
 
@@ -283,33 +329,55 @@ __device__ __forceinline__ void rt_head_sets(const RtGeo<SIG>& g, unsigned long 
   }
 }
 
-template <int SIG, bool INCR>
-__global__ void __launch_bounds__(kBlock) sweep_rt_kernel(SweepParams p) {
-  __shared__ long long table[kRtTable];
+// the value of head combination Hidx of tail tuple t from its table (or, for
+// tables too large for shared memory, from the sums themselves)
+template <int SIG>
+__device__ __forceinline__ long long rt_state_value(const RtGeo<SIG>& g, const unsigned long long (&tp)[kMaxD],
+                                                    unsigned long long Hidx, const long long* table,
+                                                    const long long* const* vs, long long one, long long R_shift) {
+  unsigned sets[SIG];
+  rt_head_sets<SIG>(g, Hidx, sets);
+  bool equal = false;
+  long long best = LLONG_MIN;
+#pragma unroll
+  for (int z = 0; z < SIG; ++z) {
+    if (sets[z] == g.full) {
+      equal = true;
+      continue;
+    }
+    const int k = g.d - __popc(sets[z]);
+    const long long M = g.table ? table[rt_entry(z, sets[z], g.d)] : rt_sum<SIG>(g, tp, z, sets[z], vs[k - 1]);
+    best = max(best, rt_floor_div(M, g.pw[k]) + (long long)(g.d - k) * R_shift);
+  }
+  return best + (equal ? one : 0);
+}
+
+// WARP: one warp per tail tuple with a table of its own (small tables, many
+// tuples), else one CTA per tail tuple
+template <int SIG, bool INCR, bool WARP>
+__global__ void __launch_bounds__(kBlock, 4) sweep_rt_kernel(SweepParams p) {
+  __shared__ long long table_all[kRtTable];
   const RtGeo<SIG> g = rt_geo<SIG>(p.n_stored, p.h, p.n_tail);
   long long best_v = p.r_mode ? LLONG_MIN : LLONG_MAX;
   unsigned long long best_x = ULLONG_MAX;
-  for (unsigned long long t = blockIdx.x; t < g.n_tail; t += gridDim.x) {
+  constexpr unsigned kUnits = WARP ? kBlock / 32 : 1;
+  const unsigned unit = WARP ? threadIdx.x >> 5 : 0;
+  const unsigned lane = WARP ? threadIdx.x & 31 : threadIdx.x;
+  constexpr unsigned kStride = WARP ? 32 : kBlock;
+  long long* table = table_all + (WARP ? unit * kRtWarpTable : 0);
+  for (unsigned long long t = (unsigned long long)blockIdx.x * kUnits + unit; t < g.n_tail;
+       t += (unsigned long long)gridDim.x * kUnits) {
     unsigned long long tp[kMaxD];
     rt_tail_parts<SIG>(g, p.h, t, tp);
-    if (g.table) rt_fill_table<SIG>(g, tp, p.prev, table);
-    __syncthreads();
-    for (unsigned long long Hidx = threadIdx.x; Hidx < g.sd; Hidx += blockDim.x) {
-      unsigned sets[SIG];
-      rt_head_sets<SIG>(g, Hidx, sets);
-      bool equal = false;
-      long long best = LLONG_MIN;
-#pragma unroll
-      for (int z = 0; z < SIG; ++z) {
-        if (sets[z] == g.full) {
-          equal = true;
-          continue;
-        }
-        const int k = g.d - __popc(sets[z]);
-        const long long M = g.table ? table[rt_entry(z, sets[z], g.d)] : rt_sum<SIG>(g, tp, z, sets[z], p.prev[k - 1]);
-        best = max(best, rt_floor_div(M, g.pw[k]));
-      }
-      const long long v = best + (equal ? p.one : 0);
+    if constexpr (WARP) {
+      rt_fill_table_warp<SIG>(g, tp, p.prev, table);
+      __syncwarp();
+    } else {
+      if (g.table) rt_fill_table<SIG>(g, tp, p.prev, table);
+      __syncthreads();
+    }
+    for (unsigned long long Hidx = lane; Hidx < g.sd; Hidx += kStride) {
+      const long long v = rt_state_value<SIG>(g, tp, Hidx, table, p.prev, p.one, 0);
       const unsigned long long x = Hidx * g.n_tail + t;
       p.out[x] = v;
       if constexpr (INCR) {
@@ -317,46 +385,49 @@ __global__ void __launch_bounds__(kBlock) sweep_rt_kernel(SweepParams p) {
         if (red_better(inc, x, best_v, best_x, p.r_mode)) best_v = inc, best_x = x;
       }
     }
-    __syncthreads();  // the table is rewritten for the next tuple
+    if constexpr (WARP)
+      __syncwarp();
+    else
+      __syncthreads();  // the table is rewritten for the next tuple
   }
   if constexpr (INCR) block_reduce_arg(best_v, best_x, p.r_mode, p.partials);
 }
 
 // W = u + dR - F(u + (d-1)R, .., u): a candidate advancing k strings reads
 // argument k = u + (d - k)R, whose mean is the mean of u plus (d - k)R
-template <int SIG>
-__global__ void __launch_bounds__(kBlock) check_rt_kernel(CheckParams q) {
-  __shared__ long long table[kRtTable];
+template <int SIG, bool WARP>
+__global__ void __launch_bounds__(kBlock, 4) check_rt_kernel(CheckParams q) {
+  __shared__ long long table_all[kRtTable];
   const RtGeo<SIG> g = rt_geo<SIG>(q.n_stored, q.h, q.n_tail);
   const long long R = q.R_from_state ? q.state->R : q.R;
   const long long* us[kMaxD];
   for (int k = 0; k < kMaxD; ++k) us[k] = q.u;
   long long best_w = LLONG_MIN;
-  for (unsigned long long t = blockIdx.x; t < g.n_tail; t += gridDim.x) {
+  constexpr unsigned kUnits = WARP ? kBlock / 32 : 1;
+  const unsigned unit = WARP ? threadIdx.x >> 5 : 0;
+  const unsigned lane = WARP ? threadIdx.x & 31 : threadIdx.x;
+  constexpr unsigned kStride = WARP ? 32 : kBlock;
+  long long* table = table_all + (WARP ? unit * kRtWarpTable : 0);
+  for (unsigned long long t = (unsigned long long)blockIdx.x * kUnits + unit; t < g.n_tail;
+       t += (unsigned long long)gridDim.x * kUnits) {
     unsigned long long tp[kMaxD];
     rt_tail_parts<SIG>(g, q.h, t, tp);
-    if (g.table) rt_fill_table<SIG>(g, tp, us, table);
-    __syncthreads();
-    for (unsigned long long Hidx = threadIdx.x; Hidx < g.sd; Hidx += blockDim.x) {
-      unsigned sets[SIG];
-      rt_head_sets<SIG>(g, Hidx, sets);
-      bool equal = false;
-      long long best = LLONG_MIN;
-#pragma unroll
-      for (int z = 0; z < SIG; ++z) {
-        if (sets[z] == g.full) {
-          equal = true;
-          continue;
-        }
-        const int k = g.d - __popc(sets[z]);
-        const long long M = g.table ? table[rt_entry(z, sets[z], g.d)] : rt_sum<SIG>(g, tp, z, sets[z], q.u);
-        best = max(best, rt_floor_div(M, g.pw[k]) + (long long)(g.d - k) * R);
-      }
+    if constexpr (WARP) {
+      rt_fill_table_warp<SIG>(g, tp, us, table);
+      __syncwarp();
+    } else {
+      if (g.table) rt_fill_table<SIG>(g, tp, us, table);
+      __syncthreads();
+    }
+    for (unsigned long long Hidx = lane; Hidx < g.sd; Hidx += kStride) {
       const unsigned long long x = Hidx * g.n_tail + t;
-      const long long F = best + (equal ? q.one : 0);
+      const long long F = rt_state_value<SIG>(g, tp, Hidx, table, us, q.one, R);
       best_w = max(best_w, ld_vec<false>(q.u + x) + (long long)g.d * R - F);
     }
-    __syncthreads();
+    if constexpr (WARP)
+      __syncwarp();
+    else
+      __syncthreads();
   }
   block_reduce_max(best_w, q.partials);
 }
@@ -484,26 +555,38 @@ inline int rt_d_of(unsigned long long n_stored, int h) {
 
 template <int SIG>
 void launch_sweep_rt(const SweepParams& p, int grid, cudaStream_t s) {
-  if (SIG == 2 && rt_d_of<SIG>(p.n_stored, p.h) >= kRtWarpD) {
+  const int d = rt_d_of<SIG>(p.n_stored, p.h);
+  if (SIG == 2 && d >= kRtWarpD) {
     if (p.incr)
       sweep_rt2_kernel<true><<<grid, kBlock, 0, s>>>(p);
     else
       sweep_rt2_kernel<false><<<grid, kBlock, 0, s>>>(p);
     return;
   }
+  if (rt_warp_tails(SIG, d, p.n_tail)) {
+    if (p.incr)
+      sweep_rt_kernel<SIG, true, true><<<grid, kBlock, 0, s>>>(p);
+    else
+      sweep_rt_kernel<SIG, false, true><<<grid, kBlock, 0, s>>>(p);
+    return;
+  }
   if (p.incr)
-    sweep_rt_kernel<SIG, true><<<grid, kBlock, 0, s>>>(p);
+    sweep_rt_kernel<SIG, true, false><<<grid, kBlock, 0, s>>>(p);
   else
-    sweep_rt_kernel<SIG, false><<<grid, kBlock, 0, s>>>(p);
+    sweep_rt_kernel<SIG, false, false><<<grid, kBlock, 0, s>>>(p);
 }
 
 template <int SIG>
 void launch_check_rt(const CheckParams& q, int grid, cudaStream_t s) {
-  if (SIG == 2 && rt_d_of<SIG>(q.n_stored, q.h) >= kRtWarpD) {
+  const int d = rt_d_of<SIG>(q.n_stored, q.h);
+  if (SIG == 2 && d >= kRtWarpD) {
     check_rt2_kernel<<<grid, kBlock, 0, s>>>(q);
     return;
   }
-  check_rt_kernel<SIG><<<grid, kBlock, 0, s>>>(q);
+  if (rt_warp_tails(SIG, d, q.n_tail))
+    check_rt_kernel<SIG, true><<<grid, kBlock, 0, s>>>(q);
+  else
+    check_rt_kernel<SIG, false><<<grid, kBlock, 0, s>>>(q);
 }
 
 // tails_per_thread = 0 marks a set that takes one tail tuple per CTA
@@ -516,8 +599,8 @@ KernelSet make_rt_set() {
   k.sym = 0;
   k.sweep = &launch_sweep_rt<SIG>;
   k.check = &launch_check_rt<SIG>;
-  k.sweep_fn = (const void*)&sweep_rt_kernel<SIG, true>;
-  k.check_fn = (const void*)&check_rt_kernel<SIG>;
+  k.sweep_fn = (const void*)&sweep_rt_kernel<SIG, true, false>;
+  k.check_fn = (const void*)&check_rt_kernel<SIG, false>;
   k.tails_per_thread = 0;
   k.sweep_algo_bytes = 0;  // set per handle: 8 (d + 1)
   k.check_algo_bytes = 8;

@@ -95,6 +95,9 @@ def test_null_handle_calls_fail_cleanly(L):
     assert L.lcs_bound_export_orbit_fx(None, 0, None, 0) == binding.LCS_EINVAL
     assert L.lcs_bound_read(None, None, None, None, None, None) == binding.LCS_EINVAL
     L.lcs_bound_destroy(None)
+    assert L.lcs_host_free(None) == binding.LCS_OK
+    assert L.lcs_host_free(12345) == binding.LCS_EINVAL  # not a buffer of lcs_host_alloc
+    assert L.lcs_host_alloc(0, None) == binding.LCS_EINVAL
 
 
 def test_missing_library_fails_loudly(monkeypatch):
@@ -152,7 +155,7 @@ def test_binding_signatures_match_the_header(L):
     decls = _declarations()
     assert len(decls) == len(declared_functions())
     scalars = {"int": ctypes.c_int, "int64_t": ctypes.c_int64, "uint64_t": ctypes.c_uint64, "double": ctypes.c_double,
-               "float": ctypes.c_float, "lcs_status": ctypes.c_int}
+               "float": ctypes.c_float, "lcs_status": ctypes.c_int, "size_t": ctypes.c_size_t}
     for ret, name, n, params in decls:
         fn = getattr(L, name)
         assert fn.argtypes is not None and len(fn.argtypes) == n, (name, n, fn.argtypes)

@@ -7,7 +7,7 @@ v_{t-k} over the states in which each string j with H_j = z (the set S) keeps
 z t_j and each other string (N, k = |N| of them) becomes t_j c_j, for every
 c in Sigma^k.  The kernels form those states' indices from the tail's digit
 parts: one range of terms per thread (or 32 contiguous chunks per warp, or
-256 per CTA for entries of 512 terms or more) for
+256 per CTA for entries of 2048 terms or more) for
 every sigma, and, for sigma = 2 from d = 9 on, lane bits deposited into the
 five lowest offset bits plus a submask walk over the rest.  Each must produce
 every term once (as a multiset), for every state and every letter.  The GPU
@@ -108,12 +108,12 @@ def sum_range_addresses(tp, z, S, s, d, n_tail, m0, m1):
     return out
 
 
-K_RT_CTA_TERMS, K_BLOCK = 512, 256
+K_RT_CTA_TERMS, K_BLOCK = 2048, 256
 
 
 def thread_or_warp_addresses(tp, z, S, s, d, n_tail):
     """A table entry's terms: one thread below 32 terms, 32 lanes with
-    contiguous chunks below 512, and from 512 on the CTA's 256 threads with
+    contiguous chunks below 2048, and from 2048 on the CTA's 256 threads with
     contiguous chunks, each a whole number of runs of the lowest digit
     (rt_fill_table, rt_chunk); without the table (sigma 2^d > 6000) one
     thread takes the whole range (rt_sum)."""
@@ -122,7 +122,8 @@ def thread_or_warp_addresses(tp, z, S, s, d, n_tail):
         return sum_range_addresses(tp, z, S, s, d, n_tail, 0, terms)
     parts = 32 if terms < K_RT_CTA_TERMS else K_BLOCK
     per = (terms + parts - 1) // parts
-    per = (per + s - 1) // s * s  # whole runs of the lowest digit (rt_chunk)
+    if s <= 8:
+        per = (per + s - 1) // s * s  # whole runs of the lowest digit (rt_chunk)
     out = []
     for lane in range(parts):
         m0 = min(terms, lane * per)

@@ -5,8 +5,9 @@ bit for bit: the stateless sweep on random arguments, whole runs of Algorithm
 start and from random starts, and the feasibility check of a given vector.
 
 The shapes cover every way the kernels form candidates: from the shared table
-of sums (sigma * 2^d <= 6000 entries) and, for sigma = 2 from d = 9 on, one
-warp per state.  A small number of fractional bits keeps the sums of
+of sums (sigma * 2^d <= 6000 entries) filled by one CTA per tail tuple, or by
+one warp per tuple for small tables and many tuples, and, for sigma = 2 from
+d = 9 on, one warp per state.  A small number of fractional bits keeps the sums of
 sigma^d terms inside int64 (the library checks that headroom for its handles).
 """
 import numpy as np
@@ -18,8 +19,10 @@ pytestmark = pytest.mark.gpu
 
 K = 30
 
+# (6, 2, 4) and (10, 2, 3) have small tables and at least 8192 tail tuples:
+# one warp per tuple instead of one CTA
 SWEEP_SHAPES = [(2, 6, 2), (2, 7, 1), (2, 9, 2), (2, 10, 1), (2, 12, 1), (2, 13, 1), (3, 4, 2), (3, 5, 1),
-                (4, 3, 2), (5, 3, 1), (6, 2, 2), (7, 3, 1), (8, 2, 3), (10, 2, 2), (9, 4, 1)]
+                (4, 3, 2), (5, 3, 1), (6, 2, 2), (7, 3, 1), (8, 2, 3), (10, 2, 2), (9, 4, 1), (6, 2, 4), (10, 2, 3)]
 
 
 @pytest.fixture(scope="module")
@@ -58,6 +61,7 @@ RUN_CASES = [
     (3, 5, 1, 20, 4, 0, True),
     (4, 3, 2, 12, 4, 0, False),
     (6, 2, 2, 20, 5, 1, False),
+    (10, 2, 3, 12, 4, 0, True),
     (10, 2, 2, 12, 0, 0, True),
     (5, 3, 1, 20, 1, 0, False),
 ]

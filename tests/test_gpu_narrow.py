@@ -177,3 +177,16 @@ def test_narrow_refusals(lb):
         with pytest.raises(lb.LcsError) as e:
             hnd.set_start_stored_fx([v[: v.size // 2]] * 2)
         assert e.value.status == lb.LCS_EINVAL
+
+
+def test_host_buffer_round_trip(lb):
+    """lcs_host_alloc's memory serves as a host vector for starts and exports."""
+    h = 8
+    with lb.LcsBound(2, 2, h, check_every=10) as a, lb.HostBuffer(4 ** h // 2) as buf:
+        a.iterate(30)
+        a.export_stored_fx(0, out=buf.array)
+        assert np.array_equal(buf.array, a.export_stored_fx(0))
+        with lb.LcsBound(2, 2, h, check_every=10) as b:
+            b.set_start_stored_fx([buf.array, buf.array])
+            b.iterate(5)
+            b.read()
