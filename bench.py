@@ -76,8 +76,9 @@ def parse():
     ap.add_argument("--bound-iters", type=int, default=None,
                     help="iterations of the wall-time-to-bound run (default: the config's, 2000 for h16; 0 skips)")
     ap.add_argument("--symmetry", type=int, default=1)
-    ap.add_argument("--batch-mode", choices=["auto", "0", "1"], default="auto",
-                    help="batch config: the autotuner's mode, or force 0 (persistent launch) / 1 (concurrent)")
+    ap.add_argument("--batch-mode", choices=["auto", "0", "1", "2"], default="auto",
+                    help="batch config: the autotuner's mode, or force 0 (persistent launch), 1 (concurrent, "
+                         "graph-captured), 2 (concurrent, enqueued call by call)")
     return ap.parse_args()
 
 
@@ -388,6 +389,32 @@ def run_batch(args, cfg, world, rank, local_rank):
     ms = reduce_max(ev0.elapsed_time(ev1), None)
     b.close()
 
+    # the concurrent mode with its calls captured in CUDA graphs (1) against
+    # the same mode enqueued call by call (2), in the same steady state.  A
+    # schedule (call length, check phase, every ring's newest slot) is
+    # captured the second time it comes; with 10-iteration calls the rings of
+    # 3, 4 and 5 slots repeat after 6 calls, so 24 warm-up calls capture all.
+    conc = {}
+    for mode in (1, 2):
+        bm = lb.LcsBatch(shapes, check_every=C, stream=stream.cuda_stream)
+        bm.set_mode(mode)
+        for _ in range(max(args.warmup, 24)):
+            bm.iterate(C)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            bm.iterate(C)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        mi = bm.info()
+        conc[f"mode{mode}"] = {"ms_per_step": reduce_max(e0.elapsed_time(e1), None) / args.steps,
+                               "graph_captured": mi["graph_captured"], "graph_replays": mi["graph_replays"],
+                               "bounds": [bm.read(i)[0] for i in range(len(shapes))]}
+        bm.close()
+    conc["captured_speedup"] = conc["mode2"]["ms_per_step"] / conc["mode1"]["ms_per_step"]
+    conc["bounds_equal"] = conc["mode1"].pop("bounds") == conc["mode2"].pop("bounds")
+
     # the plain path: each instance alone through the single-instance API
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -403,14 +430,15 @@ def run_batch(args, cfg, world, rank, local_rank):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "config": {"workload": "8 instances (sigma,d,h) " + str(shapes) + " in one batch handle ("
-                   + ("concurrent single-instance kernels" if info["mode"] == 1 else "one persistent launch")
+                   + ("concurrent single-instance kernels" if info["mode"] >= 1 else "one persistent launch")
                    + f", the autotuner's choice unless forced), {C} iterations per step",
                    "states": sum(n_states), "sweeps_per_step": C,
                    "l2": "working set of the batch (about 0.6 GB) is larger than L2"},
         "batch": {"time_to_bounds_s": t_batch, "create_and_tune_s": t_created - t0_batch,
                   "plain_sequential_time_to_bounds_s": t_plain, "speedup_vs_plain": t_plain / t_batch,
                   "iterations": total_iters, "bounds_equal_plain": bounds_batch == bounds_plain,
-                  "bounds": dict(zip([str(s) for s in shapes], bounds_batch)), "tuning": info},
+                  "bounds": dict(zip([str(s) for s in shapes], bounds_batch)), "tuning": info,
+                  "concurrent_modes": conc},
         "clocks": clk.summary(),
     }
     if rank == 0:

@@ -392,10 +392,10 @@ typedef struct {
   int graph;              /* 1: launches replay a captured CUDA graph */
   double tuned_ms_per_iter;
   int64_t launches;       /* persistent launches or graph replays so far (kernel launches in mode 1) */
-  int mode;               /* 0: one persistent launch; 1: concurrent single-instance kernels */
+  int mode;               /* 0: one persistent launch; 1: concurrent single-instance kernels; 2: 1 uncaptured */
   double persistent_ms_per_iter;  /* the autotuner's timings of both modes */
   double concurrent_ms_per_iter;
-  int graph_captured;     /* 1 once a persistent launch was captured in a CUDA graph and instantiated */
+  int graph_captured;     /* 1 once a call was captured in a CUDA graph and instantiated (either mode) */
   int min_ctas_per_sm;    /* the persistent kernel's register budget the autotuner chose: 2 (128
                            * registers a thread) or 4 (64, the heaviest bodies spill) CTAs per SM */
   int64_t graph_replays;  /* iterate calls that replayed a captured graph */
@@ -404,9 +404,13 @@ lcs_status lcs_bound_batch_info(lcs_bound_t* hnd, lcs_bound_batch_info_t* out);
 /* Force the execution mode of a batch before its first iteration (LCS_EINVAL
  * afterwards): 0 = the persistent launch with the autotuner's shape, 1 = each
  * instance's single-instance kernels on a stream of its own, forked from and
- * joined to the handle's stream, so the instances run concurrently.  Both
- * modes compute the same iterates and bounds bit for bit; the autotuner
- * times both at creation and keeps the faster. */
+ * joined to the handle's stream, so the instances run concurrently; a call
+ * whose schedule (length, check phase, every instance's ring slot) comes a
+ * second time is captured in a CUDA graph and replayed from then on (the
+ * iteration numbers the kernels record come from a device count, so a
+ * replay records the right ones); 2 = mode 1 never captured.  All modes
+ * compute the same iterates and bounds bit for bit; the autotuner times 0
+ * and 1 at creation and keeps the faster. */
 lcs_status lcs_bound_batch_set_mode(lcs_bound_t* hnd, int mode);
 
 /* Set the grid barrier's clock budget in cycles (testing the timeout path);

@@ -601,7 +601,9 @@ class LcsBatch:
         lcs_bound_batch_set_spin_budget(self.hnd, cycles)
 
     def set_mode(self, mode):
-        """0: the persistent launch, 1: concurrent single-instance kernels (before the first iteration)."""
+        """0: the persistent launch, 1: concurrent single-instance kernels with repeated call
+        schedules replayed from CUDA graphs, 2: the same kernels never captured (before the
+        first iteration)."""
         lcs_bound_batch_set_mode(self.hnd, mode)
 
 

@@ -410,7 +410,12 @@ struct BatchState {
   int tune_grid_choice, tune_units_choice;
   double tuned_ms;
   long long launches;
-  int mode;  // 0 persistent launch, 1 concurrent single-instance kernels
+  int mode;  // 0 persistent launch, 1 concurrent single-instance kernels, 2 the same never captured
+  // mode 1: graphs of whole iterate calls, keyed by the call's schedule
+  // (length, check phase, every instance's ring slot); a schedule is
+  // captured when it comes a second time, and replayed from then on
+  std::map<std::vector<long long>, cudaGraphExec_t> conc_graphs;
+  std::map<std::vector<long long>, int> conc_seen;
   double ms_persistent, ms_concurrent;
   ConcInst conc[kMaxBatch];
   cudaEvent_t fork;
@@ -439,6 +444,7 @@ void batch_destroy(BatchState* B) {
   }
   if (B->fork) cudaEventDestroy(B->fork);
   for (auto& g : B->graphs) cudaGraphExecDestroy(g.second);
+  for (auto& g : B->conc_graphs) cudaGraphExecDestroy(g.second);
   for (void* p : B->owned) {
     if (B->alloc) {
       if (B->free) B->free(p, B->ctx);
@@ -516,7 +522,7 @@ static const KernelSet* conc_kernels(int kind, int h) {
 // one iteration of instance r on its stream: the sweep, and on a checked
 // iteration the increment reduction, the check and the keep test -- the
 // sequence lcs_bound_iterate issues for a single instance
-static lcs_status conc_step(BatchState* B, int r, long long it, bool check) {
+static lcs_status conc_step(BatchState* B, int r, long long rel, bool check) {
   ConcInst& c = B->conc[r];
   const BatchInst& in = B->inst[r];
   const int rows = in.rows;
@@ -534,7 +540,7 @@ static lcs_status conc_step(BatchState* B, int r, long long it, bool check) {
   B_CUDA(cudaGetLastError());
   B->launches++;
   if (check) {
-    launch_finalize_incr(c.partials, c.grid_sweep, B->r_mode, in.state, it, c.stream);
+    launch_finalize_incr(c.partials, c.grid_sweep, B->r_mode, in.state, rel, c.stream, &B->d_ctl->iter_done);
     CheckParams q{};
     q.u = p.out;
     q.n_tail = in.n_tail;
@@ -546,7 +552,7 @@ static lcs_status conc_step(BatchState* B, int r, long long it, bool check) {
     q.R = 0;
     q.partials = c.partials;
     c.ks->check(q, c.grid_check, c.stream);
-    launch_finalize_check(c.partials, c.grid_check, in.state, it, c.stream);
+    launch_finalize_check(c.partials, c.grid_check, in.state, rel, c.stream, &B->d_ctl->iter_done);
     B_CUDA(cudaGetLastError());
     B->launches += 3;
   }
@@ -554,9 +560,14 @@ static lcs_status conc_step(BatchState* B, int r, long long it, bool check) {
   return LCS_OK;
 }
 
+__global__ void advance_count_kernel(long long* count, long long n) {
+  if (threadIdx.x == 0 && blockIdx.x == 0) *count += n;
+}
+
 // n_iters iterations of every instance, interleaved in rounds so that all
-// streams are fed while the host enqueues
-static lcs_status conc_iterate(BatchState* B, cudaStream_t s, long long n_iters) {
+// streams are fed while the host enqueues.  Iteration numbers are relative
+// to the device count ctl->iter_done, which the call advances at its end.
+static lcs_status conc_enqueue(BatchState* B, cudaStream_t s, long long n_iters) {
   const long long call_end = B->iter_done_host + n_iters;
   B_CUDA(cudaEventRecord(B->fork, s));
   for (int r = 0; r < B->n; ++r) B_CUDA(cudaStreamWaitEvent(B->conc[r].stream, B->fork, 0));
@@ -565,9 +576,10 @@ static lcs_status conc_iterate(BatchState* B, cudaStream_t s, long long n_iters)
     const long long m = std::min(round, n_iters - base);
     for (int r = 0; r < B->n; ++r) {
       for (long long j = 0; j < m; ++j) {
-        const long long it = B->iter_done_host + base + j + 1;
+        const long long rel = base + j + 1;
+        const long long it = B->iter_done_host + rel;
         const bool check = (B->check_every > 0 && it % B->check_every == 0) || it == call_end;
-        lcs_status st = conc_step(B, r, it, check);
+        lcs_status st = conc_step(B, r, rel, check);
         if (st) return st;
       }
     }
@@ -576,8 +588,54 @@ static lcs_status conc_iterate(BatchState* B, cudaStream_t s, long long n_iters)
     B_CUDA(cudaEventRecord(B->conc[r].join, B->conc[r].stream));
     B_CUDA(cudaStreamWaitEvent(s, B->conc[r].join, 0));
   }
+  advance_count_kernel<<<1, 32, 0, s>>>(&B->d_ctl->iter_done, n_iters);
+  B_CUDA(cudaGetLastError());
+  B->launches++;
   B->iter_done_host = call_end;
   return LCS_OK;
+}
+
+static lcs_status conc_iterate(BatchState* B, cudaStream_t s, long long n_iters) {
+  // what the enqueued work depends on besides the device state
+  std::vector<long long> key{n_iters, B->check_every > 0 ? B->iter_done_host % B->check_every : 0};
+  for (int r = 0; r < B->n; ++r) key.push_back(B->conc[r].newest);
+  if (B->mode == 1) {
+    auto it = B->conc_graphs.find(key);
+    if (it == B->conc_graphs.end() && ++B->conc_seen[key] >= 2) {
+      // the second call with this schedule: capture it (the host-side state
+      // the enqueue advances is restored if the capture fails)
+      int saved_newest[kMaxBatch];
+      for (int r = 0; r < B->n; ++r) saved_newest[r] = B->conc[r].newest;
+      const long long saved_iters = B->iter_done_host, saved_launches = B->launches;
+      cudaGraph_t g = nullptr;
+      cudaGraphExec_t ge = nullptr;
+      bool captured = false;
+      if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+        lcs_status st = conc_enqueue(B, s, n_iters);
+        cudaError_t e = cudaStreamEndCapture(s, &g);
+        captured = st == LCS_OK && e == cudaSuccess && cudaGraphInstantiate(&ge, g, 0) == cudaSuccess;
+        if (g) cudaGraphDestroy(g);
+      }
+      for (int r = 0; r < B->n; ++r) B->conc[r].newest = saved_newest[r];
+      B->iter_done_host = saved_iters;
+      B->launches = saved_launches;
+      if (captured) {
+        it = B->conc_graphs.emplace(key, ge).first;
+      } else {
+        cudaGetLastError();
+        B->mode = 2;  // capture is not available here: enqueue directly from now on
+      }
+    }
+    if (it != B->conc_graphs.end()) {
+      B_CUDA(cudaGraphLaunch(it->second, s));
+      B->launches++;
+      B->graph_replays++;
+      for (int r = 0; r < B->n; ++r) B->conc[r].newest = (B->conc[r].newest + (int)(n_iters % B->inst[r].rows)) % B->inst[r].rows;
+      B->iter_done_host += n_iters;
+      return LCS_OK;
+    }
+  }
+  return conc_enqueue(B, s, n_iters);
 }
 
 static lcs_status conc_setup(BatchState* B, int sms) {
@@ -631,7 +689,7 @@ static lcs_status enqueue_call(BatchState* B, cudaStream_t s, long long n_iters)
 
 lcs_status batch_iterate(BatchState* B, cudaStream_t s, long long n_iters) {
   if (n_iters <= 0) return LCS_OK;
-  if (B->mode == 1) return conc_iterate(B, s, n_iters);
+  if (B->mode >= 1) return conc_iterate(B, s, n_iters);
   *B->h_call_end = B->iter_done_host + n_iters;
   if (B->use_graph) {
     auto it = B->graphs.find(n_iters);
@@ -867,8 +925,8 @@ lcs_status batch_status(BatchState* B, cudaStream_t s, long long* status, long l
   B_CUDA(cudaMemcpyAsync(&c, B->d_ctl, sizeof c, cudaMemcpyDeviceToHost, s));
   B_CUDA(cudaStreamSynchronize(s));
   if (status) *status = c.status;
-  if (B->mode == 1) {
-    // the ring state lives on the host in this mode
+  if (B->mode >= 1) {
+    // the ring state lives on the host in the concurrent modes
     if (iter_done) *iter_done = B->iter_done_host;
     if (newest) *newest = B->conc[i].newest;
     return LCS_OK;
@@ -925,7 +983,7 @@ void batch_tuning(const BatchState* B, int* grid, int* units, double* ms, long l
   *ms = B->tuned_ms;
   *launches = B->launches;
   *graph = (B->mode == 0 && B->use_graph) ? 1 : 0;
-  *graph_captured = B->graphs.empty() ? 0 : 1;
+  *graph_captured = (B->graphs.empty() && B->conc_graphs.empty()) ? 0 : 1;
   *graph_replays = B->graph_replays;
   *min_ctas_per_sm = B->variant ? 4 : 2;
   *mode = B->mode;

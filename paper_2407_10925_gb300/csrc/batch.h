@@ -29,8 +29,11 @@ int batch_d(const BatchState* B, int i);
 void batch_destroy(BatchState* B);
 
 // provided by lcs_bound.cu for the concurrent mode (the single-instance kernels)
-void launch_finalize_incr(const RedPartial* parts, int n, int r_mode, DevState* st, long long iter, cudaStream_t s);
-void launch_finalize_check(const RedPartial* parts, int n, DevState* st, long long iter, cudaStream_t s);
+// iter_base (may be null): a device count the kernel adds to iter
+void launch_finalize_incr(const RedPartial* parts, int n, int r_mode, DevState* st, long long iter, cudaStream_t s,
+                          const long long* iter_base = nullptr);
+void launch_finalize_check(const RedPartial* parts, int n, DevState* st, long long iter, cudaStream_t s,
+                           const long long* iter_base = nullptr);
 int grid_for_work(const void* fn, int sms, unsigned long long work_items);
 
 // provided by kernels_d2s.cu (d = 2, sigma >= 3, swap-aware)

@@ -65,8 +65,11 @@ __device__ __forceinline__ bool better_arg(long long v, unsigned long long x, lo
 
 // R and its state from the per-CTA partials of a sweep (deterministic: fixed
 // assignment of partials to threads and a fixed reduction tree).
+// iter_base (may be null): a device count added to iter, so that a captured
+// graph records the right iteration each time it is replayed
 __global__ void __launch_bounds__(kFinalBlock) finalize_incr_kernel(const RedPartial* parts, int n, int r_mode,
-                                                                     DevState* st, long long iter) {
+                                                                     DevState* st, long long iter,
+                                                                     const long long* iter_base = nullptr) {
   long long v = r_mode ? LLONG_MIN : LLONG_MAX;
   unsigned long long x = ULLONG_MAX;
   for (int i = threadIdx.x; i < n; i += blockDim.x)
@@ -92,7 +95,7 @@ __global__ void __launch_bounds__(kFinalBlock) finalize_incr_kernel(const RedPar
     if (threadIdx.x == 0) {
       st->R = v;
       st->argmin = x;
-      st->R_iter = iter;
+      st->R_iter = iter + (iter_base ? *iter_base : 0);
     }
   }
 }
@@ -109,7 +112,8 @@ constexpr int kHistCap = 4096;  // records kept (a ring: the newest overwrite th
 // history buffer, the check's record is appended to it.
 __global__ void __launch_bounds__(kFinalBlock) finalize_check_kernel(const RedPartial* parts, int n, DevState* st,
                                                                       long long iter, CheckRecord* hist = nullptr,
-                                                                      unsigned long long* hist_count = nullptr) {
+                                                                      unsigned long long* hist_count = nullptr,
+                                                                      const long long* iter_base = nullptr) {
   long long v = 0;  // E = max(0, ...)
   for (int i = threadIdx.x; i < n; i += blockDim.x) v = max(v, parts[i].v);
   __shared__ long long sv[kFinalBlock / 32];
@@ -121,6 +125,7 @@ __global__ void __launch_bounds__(kFinalBlock) finalize_check_kernel(const RedPa
     v = threadIdx.x < nw ? sv[threadIdx.x] : 0;
     for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
     if (threadIdx.x == 0) {
+      if (iter_base) iter += *iter_base;
       const long long R = st->R, E = v;
       st->E = E;
       st->E_iter = iter;
@@ -433,12 +438,14 @@ namespace lcs {
 
 int grid_for_work(const void* fn, int sms, unsigned long long work_items) { return grid_for(fn, sms, work_items); }
 
-void launch_finalize_incr(const RedPartial* parts, int n, int r_mode, DevState* st, long long iter, cudaStream_t s) {
-  finalize_incr_kernel<<<1, kFinalBlock, 0, s>>>(parts, n, r_mode, st, iter);
+void launch_finalize_incr(const RedPartial* parts, int n, int r_mode, DevState* st, long long iter, cudaStream_t s,
+                          const long long* iter_base) {
+  finalize_incr_kernel<<<1, kFinalBlock, 0, s>>>(parts, n, r_mode, st, iter, iter_base);
 }
 
-void launch_finalize_check(const RedPartial* parts, int n, DevState* st, long long iter, cudaStream_t s) {
-  finalize_check_kernel<<<1, kFinalBlock, 0, s>>>(parts, n, st, iter);
+void launch_finalize_check(const RedPartial* parts, int n, DevState* st, long long iter, cudaStream_t s,
+                           const long long* iter_base) {
+  finalize_check_kernel<<<1, kFinalBlock, 0, s>>>(parts, n, st, iter, nullptr, nullptr, iter_base);
 }
 
 }  // namespace lcs
@@ -1875,7 +1882,8 @@ lcs_status lcs_bound_batch_info(lcs_bound_t* H, lcs_bound_batch_info_t* out) {
 lcs_status lcs_bound_batch_set_mode(lcs_bound_t* H, int mode) {
   if (!H) return fail(LCS_EINVAL, "NULL argument");
   if (!H->batch) return fail(LCS_EINVAL, "not a batch handle");
-  if (mode != 0 && mode != 1) return fail(LCS_EINVAL, "mode %d (0 persistent, 1 concurrent)", mode);
+  if (mode < 0 || mode > 2)
+    return fail(LCS_EINVAL, "mode %d (0 persistent, 1 concurrent, 2 concurrent without graph capture)", mode);
   if (H->iters_done != 0) return fail(LCS_EINVAL, "the mode can only be set before the first iteration");
   return batch_set_mode(H->batch, H->stream, mode);
 }

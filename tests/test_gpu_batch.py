@@ -29,8 +29,8 @@ def lb():
 MIXED = [(2, 2, 3), (2, 2, 6), (3, 2, 2), (4, 2, 2), (2, 3, 2), (2, 4, 2), (2, 2, 7), (3, 2, 3)]
 
 
-@pytest.mark.parametrize("mode", [0, 1])
-@pytest.mark.parametrize("check_every,pieces", [(0, [17]), (5, [7, 9, 1]), (1, [6])])
+@pytest.mark.parametrize("mode", [0, 1, 2])
+@pytest.mark.parametrize("check_every,pieces", [(0, [17]), (5, [7, 9, 1]), (1, [6]), (5, [5, 5, 5, 5, 5, 5])])
 def test_batch_matches_oracle(lb, orc, check_every, pieces, mode):
     iters = sum(pieces)
     with lb.LcsBatch(MIXED, check_every=check_every) as b:
@@ -76,7 +76,7 @@ def _oracle_in_pieces(orc, s, d, h, pieces, check_every):
     return out
 
 
-@pytest.mark.parametrize("mode", [None, 0, 1])
+@pytest.mark.parametrize("mode", [None, 0, 1, 2])
 def test_batch_config3_shapes_match_single_handles(lb, mode):
     """The eight-instance benchmark batch against the validated single-instance
     path, in the autotuner's mode and in each mode forced."""
@@ -93,11 +93,20 @@ def test_batch_config3_shapes_match_single_handles(lb, mode):
             assert info["mode"] == (1 if info["concurrent_ms_per_iter"] < info["persistent_ms_per_iter"] else 0)
         assert info["min_ctas_per_sm"] in (2, 4)
         total = iters
-        if mode == 0:  # the persistent launch was captured in a CUDA graph
-            assert info["graph_captured"] == 1 and info["graph"] == 1
-            b.iterate(iters)  # a call of the same length replays the captured graph
+        if mode in (0, 1, 2):
+            # a second call of the same length: mode 0 replays the graph of the
+            # persistent launch it captured; mode 1 captures this call's
+            # schedule (the ring slots and the check phase repeat after 60
+            # iterations) and replays it; mode 2 never captures
+            b.iterate(iters)
             total += iters
-            assert b.info()["graph_replays"] >= 1
+            info = b.info()
+            if mode == 0:
+                assert info["graph_captured"] == 1 and info["graph"] == 1 and info["graph_replays"] >= 1
+            elif mode == 1:
+                assert info["mode"] == 1 and info["graph_captured"] == 1 and info["graph_replays"] >= 1
+            else:
+                assert info["graph_captured"] == 0 and info["graph_replays"] == 0
         for i, (s, d, h) in enumerate(shapes):
             with lb.LcsBound(s, d, h, check_every=20) as one:
                 one.iterate(total)
