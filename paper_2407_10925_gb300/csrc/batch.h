@@ -47,7 +47,13 @@ const KernelSet* kernels_rt(int sigma);
 // provided by kernels_s2d2.cu: the sigma = d = 2 swap-aware sweep over
 // offset-normalised 32-bit storage
 const KernelSet* kernels_s2d2_narrow();
-unsigned long long rt_work_items(int sigma, int d, unsigned long long n_states, unsigned long long n_tail);
+// blocks: the block form (two phases, one thread per state in the second)
+unsigned long long rt_work_items(int sigma, int d, unsigned long long n_states, unsigned long long n_tail, bool blocks);
+// the block form of the general kernels: whether it serves (sigma, d, h), the
+// length of its term-offset table, and the launch that fills the table
+bool rt_blocks_apply(int sigma, int d, int h);
+size_t rt_offsets_len(int sigma, int d);
+void rt_offsets_fill(int sigma, int d, unsigned short* offs, unsigned* start, cudaStream_t s);
 
 // provided by kernels_orbit.cu (sigma = d = 2 orbit form)
 unsigned long long orbit_len(int h);

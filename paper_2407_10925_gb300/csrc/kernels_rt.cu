@@ -13,10 +13,36 @@ const KernelSet* kernels_rt(int sigma) {
 
 // threads' worth of work of one general sweep or check, for sizing its grid:
 // one CTA per tail tuple, one warp per tail tuple (small tables, many
-// tuples), or one warp per state (sigma = 2, d >= kRtWarpD)
-unsigned long long rt_work_items(int sigma, int d, unsigned long long n_states, unsigned long long n_tail) {
+// tuples), or one warp per state (sigma = 2, d >= kRtWarpD); in block form,
+// one thread per state (the second phase; the first sizes its own grid)
+unsigned long long rt_work_items(int sigma, int d, unsigned long long n_states, unsigned long long n_tail,
+                                 bool blocks) {
+  if (blocks) return n_states;
   if (sigma == 2 && d >= kRtWarpD) return n_states * 32;
   return rt_warp_tails(sigma, d, n_tail) ? n_tail * 32 : n_tail * kBlock;
+}
+
+bool rt_blocks_apply(int sigma, int d, int h) { return sigma <= 10 && rtb_applies(sigma, d, h); }
+
+size_t rt_offsets_len(int sigma, int d) {
+  size_t n = 1;
+  for (int i = 0; i < d; ++i) n *= (size_t)(sigma + 1);
+  return n;
+}
+
+void rt_offsets_fill(int sigma, int d, unsigned short* offs, unsigned* start, cudaStream_t s) {
+  switch (sigma) {
+    case 2: launch_rtb_offsets<2>(d, offs, start, s); break;
+    case 3: launch_rtb_offsets<3>(d, offs, start, s); break;
+    case 4: launch_rtb_offsets<4>(d, offs, start, s); break;
+    case 5: launch_rtb_offsets<5>(d, offs, start, s); break;
+    case 6: launch_rtb_offsets<6>(d, offs, start, s); break;
+    case 7: launch_rtb_offsets<7>(d, offs, start, s); break;
+    case 8: launch_rtb_offsets<8>(d, offs, start, s); break;
+    case 9: launch_rtb_offsets<9>(d, offs, start, s); break;
+    case 10: launch_rtb_offsets<10>(d, offs, start, s); break;
+    default: break;
+  }
 }
 
 }  // namespace lcs

@@ -372,6 +372,11 @@ struct lcs_bound {
   unsigned long long sweep_bytes, check_bytes;
   int last_check_grid;
   int d_batch_worst;  // batch handles: d of the instance with the largest sigma^d
+  // general kernels in block form: the means table (sigma 2^d rows of n_tail
+  // values) and the term offsets of every advance set
+  long long* rt_means;
+  unsigned short* rt_offs;
+  unsigned* rt_start;
 };
 
 // Host memory for the device: an anonymous mapping aligned to 512 MiB,
@@ -551,6 +556,9 @@ void lcs_bound_destroy(lcs_bound_t* H) {
     }
   }
   dev_free(H, H->offs);
+  dev_free(H, H->rt_means);
+  dev_free(H, H->rt_offs);
+  dev_free(H, H->rt_start);
   dev_free(H, H->check_partials);
   dev_free(H, H->ubuf);
   dev_free(H, H->dstate);
@@ -651,9 +659,11 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
   int sms = 0;
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, H->device);
   if (sms < 1) sms = 1;
-  // the general kernels take one tail tuple per CTA
+  // the general kernels: in block form where it applies (one thread per state
+  // in the second phase), else one tail tuple per CTA or warp
+  const bool rt_blocks = ks->tails_per_thread == 0 && rt_blocks_apply(sigma, d, h);
   const unsigned long long thread_items =
-      ks->tails_per_thread == 0 ? rt_work_items(sigma, d, n, H->n_tail) : (sym ? H->n_tail / 2 : H->n_tail);
+      ks->tails_per_thread == 0 ? rt_work_items(sigma, d, n, H->n_tail, rt_blocks) : (sym ? H->n_tail / 2 : H->n_tail);
   H->grid_sweep = grid_for(ks->sweep_fn, sms, thread_items);
   H->grid_check = grid_for(ks->check_fn, sms, thread_items);
   H->n_partials = std::max(H->grid_sweep, H->grid_check);
@@ -725,6 +735,18 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
       lcs_bound_destroy(H);
       return fail(LCS_ENOMEM, "partials of the fused check");
     }
+  }
+  if (rt_blocks) {
+    const size_t rows = (size_t)sigma << d;
+    H->rt_means = (long long*)dev_alloc(H, sizeof(long long) * rows * (size_t)H->n_tail);
+    H->rt_offs = (unsigned short*)dev_alloc(H, sizeof(unsigned short) * rt_offsets_len(sigma, d));
+    H->rt_start = (unsigned*)dev_alloc(H, sizeof(unsigned) << d);
+    if (!H->rt_means || !H->rt_offs || !H->rt_start) {
+      lcs_bound_destroy(H);
+      return fail(LCS_ENOMEM, "means table and term offsets of the general kernels (%zu bytes)",
+                  sizeof(long long) * rows * (size_t)H->n_tail);
+    }
+    rt_offsets_fill(sigma, d, H->rt_offs, H->rt_start, H->stream);
   }
   if (H->narrow) {
     H->offs = (long long*)dev_alloc(H, sizeof(long long) * (size_t)(kMaxD + 1));
@@ -865,6 +887,9 @@ static lcs_status run_check(lcs_bound* H, const long long* u, bool R_from_state,
   c.R_from_state = R_from_state ? 1 : 0;
   c.R = R;
   c.partials = H->partials;
+  c.rt_means = H->rt_means;
+  c.rt_offs = H->rt_offs;
+  c.rt_start = H->rt_start;
   cudaEvent_t a = nullptr;
   lcs_status st = timed_begin(H, &a);
   if (st) return st;
@@ -874,7 +899,7 @@ static lcs_status run_check(lcs_bound* H, const long long* u, bool R_from_state,
   if (st) return st;
   H->check_n++;
   H->check_bytes += (unsigned long long)K->check_algo_bytes * H->n_stored;
-  H->launches++;
+  H->launches += H->rt_means ? 2 : 1;
   H->last_check_grid = grid;
   if (finalize) {
     finalize_check_kernel<<<1, kFinalBlock, 0, H->stream>>>(H->partials, grid, H->dstate, iter, H->hist,
@@ -944,6 +969,9 @@ lcs_status lcs_bound_iterate(lcs_bound_t* H, int64_t n_iters) {
     p.one = H->one;
     p.partials = H->partials;
     p.state = H->dstate;
+    p.rt_means = H->rt_means;
+    p.rt_offs = H->rt_offs;
+    p.rt_start = H->rt_start;
     if (H->narrow) {
       p.offs = H->offs;
       p.slot_in0 = H->newest;
@@ -976,7 +1004,7 @@ lcs_status lcs_bound_iterate(lcs_bound_t* H, int64_t n_iters) {
     const int algo = K->tails_per_thread == 0 ? 8 * (H->d + 1) : K->sweep_algo_bytes;
     // a fused check adds one more read of the newest input's blocks: half of a check's bytes
     H->sweep_bytes += (unsigned long long)(algo + (fuse ? K->check_algo_bytes / 2 : 0)) * H->n_stored;
-    H->launches++;
+    H->launches += H->rt_means ? 2 : 1;  // the block form: the means table, then the states
     if (fuse) {  // the pending check's E and keep test, before this iteration's increment replaces R
       H->pending_check = false;
       if (lcs_status st2 = finish_check(H, H->check_partials, grid, p.prev[0], H->pending_iter)) return st2;
@@ -1928,7 +1956,7 @@ lcs_status lcs_sweep_fx(int sigma, int d, int h, int f_mode, int frac_bits, cons
   LCS_CUDA(cudaGetDevice(&dev));
   cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int grid =
-      grid_for(ks->sweep_fn, std::max(sms, 1), ks->tails_per_thread == 0 ? rt_work_items(sigma, d, n, p.n_tail) : p.n_tail);
+      grid_for(ks->sweep_fn, std::max(sms, 1), ks->tails_per_thread == 0 ? rt_work_items(sigma, d, n, p.n_tail, false) : p.n_tail);
   ks->sweep(p, grid, (cudaStream_t)stream);
   LCS_CUDA(cudaGetLastError());
   return LCS_OK;

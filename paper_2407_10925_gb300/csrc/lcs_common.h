@@ -60,6 +60,11 @@ struct SweepParams {
   // a sweep fused with the check of its newest input (KernelSet::sweep_check):
   // one max-W partial per CTA; R is read from state
   RedPartial* check_partials;
+  // general kernels in block form (sweep_rtb.cuh): the means table and the
+  // term offsets; null: the one-pass general kernels run instead
+  long long* rt_means;
+  const unsigned short* rt_offs;
+  const unsigned* rt_start;
 };
 
 // Arguments of one check launch: W = u + dR - F(u + (d-1)R, .., u).
@@ -73,6 +78,9 @@ struct CheckParams {
   int R_from_state;
   long long R;                   // used when !R_from_state
   RedPartial* partials;          // one per CTA
+  long long* rt_means;           // as in SweepParams
+  const unsigned short* rt_offs;
+  const unsigned* rt_start;
 };
 
 // Host-visible description of the kernels compiled for one (sigma, d).

@@ -35,6 +35,7 @@
 
 #include "lcs_common.h"
 #include "sweep_generic.cuh"
+#include "sweep_rtb.cuh"
 
 namespace lcs {
 
@@ -556,6 +557,10 @@ inline int rt_d_of(unsigned long long n_stored, int h) {
 template <int SIG>
 void launch_sweep_rt(const SweepParams& p, int grid, cudaStream_t s) {
   const int d = rt_d_of<SIG>(p.n_stored, p.h);
+  if (p.rt_means && rtb_applies(SIG, d, p.h)) {
+    launch_sweep_rtb<SIG>(p, d, grid, s);
+    return;
+  }
   if (SIG == 2 && d >= kRtWarpD) {
     if (p.incr)
       sweep_rt2_kernel<true><<<grid, kBlock, 0, s>>>(p);
@@ -579,6 +584,10 @@ void launch_sweep_rt(const SweepParams& p, int grid, cudaStream_t s) {
 template <int SIG>
 void launch_check_rt(const CheckParams& q, int grid, cudaStream_t s) {
   const int d = rt_d_of<SIG>(q.n_stored, q.h);
+  if (q.rt_means && rtb_applies(SIG, d, q.h)) {
+    launch_check_rtb<SIG>(q, d, grid, s);
+    return;
+  }
   if (SIG == 2 && d >= kRtWarpD) {
     check_rt2_kernel<<<grid, kBlock, 0, s>>>(q);
     return;

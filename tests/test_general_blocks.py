@@ -1,0 +1,208 @@
+"""The block form of the general kernels (sweep_rtb.cuh), restated with plain
+integers and checked against the terms that Algorithm 1 / Eq. ineq3 define,
+written from the STATE INDEX definition of include/lcs_bound.h alone.
+
+Phase 1 stages blocks of sigma^d consecutive values (the lowest d digits of
+the state index vary inside a block), lists for each block Y of v_k the
+advance sets N of k strings whose other strings S all carry one letter z in
+Y's top digit group, and forms for each such (Y, N) the sigma^|S| sums over
+the block's digits on N, one per choice of its digits on S.  It files each
+sum at row e(z, S), column t of the means table.  Phase 2 reads, for state
+(H, t), row e(z, S_z) at column t for every letter z.  Checked here, for
+every state of small shapes and every candidate: the entry phase 2 reads was
+produced by exactly one task, from the right argument, and its terms are the
+multiset Algorithm 1 defines.  Also: the term-offset table's start formula
+against a running sum, and that no task files two sums at one entry.
+"""
+import math
+
+import pytest
+
+from test_general_addressing import decode, defined_terms
+
+K_TILE_VALS, K_MAX_G, K_MAX_BLOCK = 2048, 64, 16384
+
+
+def blocks_per_tile(sd):
+    g = 1 if sd >= K_TILE_VALS else K_TILE_VALS // sd
+    return min(g, K_MAX_G)
+
+
+def top_sets(Y, topw, s, d):
+    top, Z = Y // topw, [0] * s
+    for j in range(d - 1, -1, -1):
+        Z[top % s] |= 1 << j
+        top //= s
+    return Z
+
+
+def count(Y, topw, s, d, ss):
+    if ss == 0:
+        return 1
+    return sum(math.comb(bin(m).count("1"), ss) for m in top_sets(Y, topw, s, d))
+
+
+def task(Y, topw, s, d, h, ss, r):
+    """(N, e, tail base) of task r of block Y with ss kept strings, as the kernel forms them."""
+    full, S, zsel = (1 << d) - 1, 0, 0
+    if ss > 0:
+        Z = top_sets(Y, topw, s, d)
+        for z in range(s):
+            c = math.comb(bin(Z[z]).count("1"), ss)
+            if r < c:
+                zsel, mask = z, Z[z]
+                break
+            r -= c
+        n, local, left = bin(mask).count("1"), 0, ss
+        for i in range(n - 1, -1, -1):
+            if left == 0:
+                break
+            c = math.comb(i, left)
+            if c <= r:
+                local |= 1 << i
+                r -= c
+                left -= 1
+        members = [b for b in range(d) if (mask >> b) & 1]
+        for i, b in enumerate(members):
+            if (local >> i) & 1:
+                S |= 1 << b
+    N = full ^ S
+    e = (zsel << d) | S if S else 0
+    tN = tS = 0
+    y, w = Y, 1
+    for i in range((h - 1) * d):
+        c = y % s
+        y //= s
+        j = d - 1 - i % d
+        if (N >> j) & 1:
+            tN += c * w
+        elif i < (h - 2) * d:
+            tS += c * w
+        w *= s
+    return N, e, tN + s ** d * tS
+
+
+def s_offset(S, d, lowS, s):
+    off, w = 0, 1
+    for j in range(d - 1, -1, -1):
+        if (S >> j) & 1:
+            off += (lowS % s) * w
+            lowS //= s
+        w *= s
+    return off
+
+
+def start_of(N, s, d):
+    """The kernel's closed form of the table position of set N."""
+    st, p1 = 0, 1
+    for b in range(d):
+        if (N >> b) & 1:
+            st += s ** bin(N >> (b + 1)).count("1") * p1
+        p1 *= s + 1
+    return st
+
+
+def offsets_table(s, d):
+    """start[N] by the closed form; offs[start[N] + m] by the kernel's digit deposit."""
+    start, offs = [], {}
+    for N in range(1 << d):
+        st = start_of(N, s, d)
+        start.append(st)
+        for m in range(s ** bin(N).count("1")):
+            off, w, mm = 0, 1, m
+            for j in range(d - 1, -1, -1):
+                if (N >> j) & 1:
+                    off += (mm % s) * w
+                    mm //= s
+                w *= s
+            offs[st + m] = off
+    return start, offs
+
+
+def phase1(s, d, h, check):
+    """{(e, t): (k, sorted term addresses)} as phase 1 files them (every tile)."""
+    sd, n_tail = s ** d, s ** (d * (h - 1))
+    topw = n_tail // sd
+    G = blocks_per_tile(sd)
+    start, offs = offsets_table(s, d)
+    full = (1 << d) - 1
+    filed = {}
+    n_ty = (n_tail + G - 1) // G
+    tiles = [(0, ty) for ty in range(n_ty)] if check else [(k, ty) for k in range(1, d + 1) for ty in range(n_ty)]
+    for kk, ty in tiles:
+        Y0 = ty * G
+        nb = min(G, n_tail - Y0)
+        for k in (range(1, d + 1) if check else [kk]):
+            ss = d - k
+            cnt = [0]
+            for b in range(nb):
+                cnt.append(cnt[-1] + count(Y0 + b, topw, s, d, ss))
+            T, O = s ** k, s ** ss
+            for i in range(cnt[nb]):
+                b = 0
+                while cnt[b + 1] <= i:
+                    b += 1
+                N, e, tb = task(Y0 + b, topw, s, d, h, ss, i - cnt[b])
+                assert bin(N).count("1") == k
+                for o in range(O):
+                    offS = s_offset(full ^ N, d, o, s)
+                    addrs = sorted((Y0 + b) * sd + offS + offs[start[N] + m] for m in range(T))
+                    key = (e, tb + offS)
+                    assert key not in filed, f"entry {key} filed twice"
+                    filed[key] = (k, addrs)
+    return filed
+
+
+# (7, 2, 2) and (6, 2, 2): several blocks to a tile with a partial last tile
+SHAPES = [(2, 6, 2), (3, 4, 2), (4, 3, 2), (7, 2, 2), (6, 2, 2), (2, 3, 3), (3, 3, 3), (2, 4, 3), (2, 2, 4)]
+
+
+@pytest.mark.parametrize("check", [False, True])
+@pytest.mark.parametrize("s,d,h", SHAPES)
+def test_every_state_reads_the_defined_sums(s, d, h, check):
+    filed = phase1(s, d, h, check)
+    n_tail = s ** (d * (h - 1))
+    full = (1 << d) - 1
+    used = set()
+    for x in range(s ** (d * h)):
+        Hidx, t = divmod(x, n_tail)
+        sets = [0] * s
+        hh = Hidx
+        for j in range(d - 1, -1, -1):
+            sets[hh % s] |= 1 << j
+            hh //= s
+        strings = decode(x, s, d, h)
+        for z in range(s):
+            if sets[z] == full:
+                continue
+            key = ((z << d) | sets[z] if sets[z] else 0, t)
+            assert key in filed, f"state {x} letter {z}: entry {key} never filed"
+            k, addrs = filed[key]
+            want, kk = defined_terms(strings, z, s)
+            assert k == kk and addrs == want, (x, z)
+            used.add(key)
+    assert used == set(filed), "phase 1 files entries no state reads"
+
+
+@pytest.mark.parametrize("s,d", [(2, 2), (2, 7), (3, 5), (5, 3), (10, 2), (2, 12)])
+def test_offset_table_start_is_the_running_sum(s, d):
+    total = 0
+    for N in range(1 << d):
+        assert start_of(N, s, d) == total
+        total += s ** bin(N).count("1")
+    assert total == (s + 1) ** d  # the table's length
+    if s ** d <= K_MAX_BLOCK:
+        assert s ** d - 1 < 2 ** 16  # every offset in a block fits the table's 16-bit entries
+
+
+def test_tiles_and_shared_memory_fit():
+    """Every block-form shape's tile fits the kernel's shared-memory opt-in (227 KiB)."""
+    for s in range(2, 11):
+        for d in range(2, 17):
+            sd = s ** d
+            if sd > K_MAX_BLOCK:
+                continue
+            G = blocks_per_tile(sd)
+            smem = G * sd * 8 + 256 * 20 + (K_MAX_G + 2) * 4 + 64
+            assert smem <= 227 * 1024
+            assert G <= K_MAX_G and (G == 1 or G * sd <= K_TILE_VALS)

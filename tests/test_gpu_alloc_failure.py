@@ -53,7 +53,7 @@ def _opts(lb, a, **kw):
 
 
 CASES = [((2, 2, 8), {}), ((2, 2, 8), {"keep_u": 1}), ((3, 2, 4), {}), ((2, 3, 4), {"symmetry": 0}),
-         ((3, 8, 1), {"frac_bits": 30})]
+         ((3, 8, 1), {"frac_bits": 30}), ((3, 4, 2), {"frac_bits": 36})]
 
 
 @pytest.mark.parametrize("shape,kw", CASES, ids=lambda v: str(v))

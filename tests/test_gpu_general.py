@@ -4,10 +4,16 @@ bit for bit: the stateless sweep on random arguments, whole runs of Algorithm
 2 (iterates, R and its state, E, the kept triplet, the bound) from the zero
 start and from random starts, and the feasibility check of a given vector.
 
-The shapes cover every way the kernels form candidates: from the shared table
-of sums (sigma * 2^d <= 6000 entries) filled by one CTA per tail tuple, or by
-one warp per tuple for small tables and many tuples, and, for sigma = 2 from
-d = 9 on, one warp per state.  A small number of fractional bits keeps the sums of
+The shapes cover every way the kernels form candidates.  Handles with h >= 2
+and sigma^d <= 16384 run the block form (a means table filled from blocks of
+sigma^d consecutive values staged in shared memory, then one thread per
+state).  The stateless sweep and h = 1 run the one-pass kernels: the shared
+table of sums (sigma * 2^d <= 6000 entries) filled by one CTA per tail tuple,
+or by one warp per tuple for small tables and many tuples, and, for sigma = 2
+from d = 9 on, one warp per state.  At the benchmark shapes (3, 8, 2) and
+(2, 12, 2) the oracle's plain F (2631 and 259 terms per state) is too slow for
+every state, so windows of states are compared, and the increment reduction
+against the exported iterate.  A small number of fractional bits keeps the sums of
 sigma^d terms inside int64 (the library checks that headroom for its handles).
 """
 import numpy as np
@@ -64,6 +70,17 @@ RUN_CASES = [
     (10, 2, 3, 12, 4, 0, True),
     (10, 2, 2, 12, 0, 0, True),
     (5, 3, 1, 20, 1, 0, False),
+    # the block form (h >= 2): one block per tile, several (sigma^d < 2048)
+    # with a partial last tile, sigma = 2 with large d
+    (2, 10, 2, 2, 1, 0, True),
+    (3, 6, 2, 3, 2, 1, True),
+    (2, 8, 2, 5, 5, 0, True),
+    (6, 2, 3, 6, 3, 0, True),
+    (7, 2, 2, 5, 5, 1, True),
+    (4, 4, 2, 4, 2, 0, True),
+    (5, 3, 2, 6, 3, 0, True),
+    (9, 3, 2, 2, 1, 0, True),
+    (2, 6, 3, 4, 2, 0, True),
 ]
 
 
@@ -90,7 +107,7 @@ def test_general_run_bit_exact(lb, orc, case):
         assert hnd.read()[0] == want["bound_rd"]
 
 
-@pytest.mark.parametrize("s,d,h", [(3, 4, 2), (2, 12, 1), (2, 9, 2), (10, 2, 2), (7, 3, 1)])
+@pytest.mark.parametrize("s,d,h", [(3, 4, 2), (2, 12, 1), (2, 9, 2), (10, 2, 2), (7, 3, 1), (6, 2, 3), (2, 10, 2)])
 def test_general_check_vector_matches_oracle(lb, orc, s, d, h):
     import torch
 
@@ -113,3 +130,27 @@ def test_all_advance_sets_stay_unsupported_without_a_kernel(lb):
     with pytest.raises(lb.LcsError) as e:
         lb.LcsBound(3, 4, 2, f_mode=1)
     assert e.value.status == lb.LCS_EUNSUPPORTED
+
+
+@pytest.mark.parametrize("s,d,h", [(3, 8, 2), (2, 12, 2)])
+def test_block_form_sampled_at_benchmark_shapes(lb, orc, s, d, h):
+    kb = 36  # the benchmark's fractional bits for these shapes
+    hist = inputs.random_history(s, d, h, seed=4242 + s + d, frac_bits=kb)  # newest first
+    n = hist[0].size
+    with lb.LcsBound(s, d, h, check_every=1, frac_bits=kb) as hnd:
+        hnd.set_start_fx(hist)
+        hnd.iterate(1)
+        rep = hnd.report()
+        got = hnd.export_fx(0)
+    assert rep["status"] == 0
+    rng = np.random.default_rng(17)
+    sd = s ** d
+    # windows: the first and last states, and random ones across head and tail digits
+    starts = [0, n - 2 * sd] + [int(x) for x in rng.integers(0, n - 2 * sd, size=4)]
+    for x0 in starts:
+        want = orc.F(s, d, h, hist, arith="fx", frac_bits=kb, x0=x0, x1=x0 + 2 * sd)
+        part = got[x0:x0 + 2 * sd]
+        assert np.array_equal(part, want), (x0, np.flatnonzero(part != want)[:10])
+    inc = got - hist[0]
+    assert rep["R"] == int(inc.min())
+    assert inc[rep["argmin"]] == rep["R"]
