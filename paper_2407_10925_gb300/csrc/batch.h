@@ -2,6 +2,8 @@
 // batched persistent launch (batch.cu).
 #pragma once
 
+#include <vector>
+
 #include <cuda_runtime.h>
 
 #include "../../include/lcs_bound.h"
@@ -54,6 +56,7 @@ unsigned long long rt_work_items(int sigma, int d, unsigned long long n_states, 
 bool rt_blocks_apply(int sigma, int d, int h);
 size_t rt_offsets_len(int sigma, int d);
 void rt_offsets_fill(int sigma, int d, unsigned short* offs, unsigned* start, cudaStream_t s);
+std::vector<unsigned long long> rt_tile_list(int sigma, int d, int h);
 
 // provided by kernels_orbit.cu (sigma = d = 2 orbit form)
 unsigned long long orbit_len(int h);

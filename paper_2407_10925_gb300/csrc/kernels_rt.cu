@@ -1,5 +1,7 @@
 // Instantiation of the general sweep and check (any d up to kMaxD, full
 // storage, f_mode 0) for sigma = 2 .. 10.
+#include <vector>
+
 #include "sweep_rt.cuh"
 
 namespace lcs {
@@ -43,6 +45,40 @@ void rt_offsets_fill(int sigma, int d, unsigned short* offs, unsigned* start, cu
     case 10: launch_rtb_offsets<10>(d, offs, start, s); break;
     default: break;
   }
+}
+
+// The first phase's tiles that hold a task, as (k << 48) | run index: a run
+// of G blocks of v_k has one when some block's top digits carry one letter
+// on at least d - k strings (every run for k = d).
+std::vector<unsigned long long> rt_tile_list(int sigma, int d, int h) {
+  std::vector<unsigned long long> out;
+  unsigned long long sd = 1, n_tail = 1;
+  for (int i = 0; i < d; ++i) sd *= (unsigned long long)sigma;
+  for (int i = 0; i < d * (h - 1); ++i) n_tail *= (unsigned long long)sigma;
+  const unsigned long long topw = n_tail / sd;
+  const unsigned G = rtb_blocks_per_tile((unsigned)sd);
+  // the most strings sharing one top letter, for each top group
+  std::vector<unsigned char> most(sd);
+  for (unsigned long long top = 0; top < sd; ++top) {
+    int c[16] = {0};
+    unsigned long long x = top;
+    int m = 0;
+    for (int j = 0; j < d; ++j) {
+      m = std::max(m, ++c[x % (unsigned long long)sigma]);
+      x /= (unsigned long long)sigma;
+    }
+    most[top] = (unsigned char)m;
+  }
+  const unsigned long long runs = (n_tail + G - 1) / G;
+  std::vector<unsigned char> run_most(runs, 0);
+  for (unsigned long long Y = 0; Y < n_tail; ++Y) {
+    unsigned char& r = run_most[Y / G];
+    r = std::max(r, most[Y / topw]);
+  }
+  for (int k = 1; k <= d; ++k)
+    for (unsigned long long ty = 0; ty < runs; ++ty)
+      if (k == d || run_most[ty] >= d - k) out.push_back(((unsigned long long)k << 48) | ty);
+  return out;
 }
 
 }  // namespace lcs

@@ -377,6 +377,8 @@ struct lcs_bound {
   long long* rt_means;
   unsigned short* rt_offs;
   unsigned* rt_start;
+  unsigned long long* rt_tiles;  // the first phase's tiles with a task
+  unsigned long long rt_n_tiles;
 };
 
 // Host memory for the device: an anonymous mapping aligned to 512 MiB,
@@ -559,6 +561,7 @@ void lcs_bound_destroy(lcs_bound_t* H) {
   dev_free(H, H->rt_means);
   dev_free(H, H->rt_offs);
   dev_free(H, H->rt_start);
+  dev_free(H, H->rt_tiles);
   dev_free(H, H->check_partials);
   dev_free(H, H->ubuf);
   dev_free(H, H->dstate);
@@ -666,6 +669,12 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
       ks->tails_per_thread == 0 ? rt_work_items(sigma, d, n, H->n_tail, rt_blocks) : (sym ? H->n_tail / 2 : H->n_tail);
   H->grid_sweep = grid_for(ks->sweep_fn, sms, thread_items);
   H->grid_check = grid_for(ks->check_fn, sms, thread_items);
+  if (rt_blocks) {
+    // the block form's second phase (one thread per state, few registers,
+    // bound by the latency of its table reads): six CTAs per SM
+    const unsigned long long need = std::max(1ull, (n + kBlock - 1) / kBlock);
+    H->grid_sweep = H->grid_check = (int)std::min((unsigned long long)sms * 6, need);
+  }
   H->n_partials = std::max(H->grid_sweep, H->grid_check);
   if (ks_swap) {
     // sigma = d = 2: one CTA per 16 x 16 tile of orbit representatives;
@@ -747,6 +756,20 @@ lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts_
                   sizeof(long long) * rows * (size_t)H->n_tail);
     }
     rt_offsets_fill(sigma, d, H->rt_offs, H->rt_start, H->stream);
+    const std::vector<unsigned long long> tiles = rt_tile_list(sigma, d, h);
+    H->rt_n_tiles = tiles.size();
+    H->rt_tiles = (unsigned long long*)dev_alloc(H, sizeof(unsigned long long) * std::max<size_t>(1, tiles.size()));
+    if (!H->rt_tiles) {
+      lcs_bound_destroy(H);
+      return fail(LCS_ENOMEM, "tile list of the general kernels");
+    }
+    e = cudaMemcpyAsync(H->rt_tiles, tiles.data(), sizeof(unsigned long long) * tiles.size(), cudaMemcpyHostToDevice,
+                        H->stream);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(H->stream);  // the host list is freed on return
+    if (e != cudaSuccess) {
+      lcs_bound_destroy(H);
+      return fail(LCS_ECUDA, "tile list: %s", cudaGetErrorString(e));
+    }
   }
   if (H->narrow) {
     H->offs = (long long*)dev_alloc(H, sizeof(long long) * (size_t)(kMaxD + 1));
@@ -972,6 +995,8 @@ lcs_status lcs_bound_iterate(lcs_bound_t* H, int64_t n_iters) {
     p.rt_means = H->rt_means;
     p.rt_offs = H->rt_offs;
     p.rt_start = H->rt_start;
+    p.rt_tiles = H->rt_tiles;
+    p.rt_n_tiles = H->rt_n_tiles;
     if (H->narrow) {
       p.offs = H->offs;
       p.slot_in0 = H->newest;

@@ -65,6 +65,8 @@ struct SweepParams {
   long long* rt_means;
   const unsigned short* rt_offs;
   const unsigned* rt_start;
+  const unsigned long long* rt_tiles;  // the first phase's tiles with a task: (k << 48) | run index
+  unsigned long long rt_n_tiles;
 };
 
 // Arguments of one check launch: W = u + dR - F(u + (d-1)R, .., u).

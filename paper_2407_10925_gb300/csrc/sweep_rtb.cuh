@@ -44,6 +44,7 @@
 
 #include <climits>
 
+#include "../../include/lcs_bound.h"
 #include "lcs_common.h"
 #include "sweep_generic.cuh"
 
@@ -70,11 +71,26 @@ __host__ __device__ inline unsigned rtb_blocks_per_tile(unsigned sd) {
   return g < kRtbMaxG ? g : kRtbMaxG;
 }
 
-// shared memory of a phase-1 CTA: the tile, then the task list (N, block
-// offset, entry, tail base), the per-block task counts, the cross-warp sums
-__host__ __device__ inline size_t rtb_smem_bytes(unsigned sd) {
-  return (size_t)rtb_blocks_per_tile(sd) * sd * 8 + (size_t)kRtbTasks * (4 + 4 + 4 + 8) + (kRtbMaxG + 2) * 4 + 8 * 8;
+constexpr unsigned kRtbAcc = kBlock / 2;  // outputs split over several threads in one pass at most
+
+// one staging buffer: a tile plus one element of slack (the bulk copy starts
+// at an even element), a multiple of 16 bytes
+__host__ __device__ inline unsigned rtb_stage_bytes(unsigned sd) {
+  return (rtb_blocks_per_tile(sd) * sd * 8 + 8 + 15) / 16 * 16;
 }
+
+// shared memory of a phase-1 CTA: the stages, then the task list (N, block
+// offset, entry, tail base), the per-block task counts, the parts' sums, two
+// mbarriers and a flag
+__host__ __device__ inline size_t rtb_smem_bytes(unsigned sd, int nstage) {
+  return (size_t)nstage * rtb_stage_bytes(sd) + (size_t)kRtbTasks * (4 + 4 + 4 + 8) + (kRtbMaxG + 2) * 4 +
+         kRtbAcc * 8 + 2 * 8 + 16;
+}
+
+// two stages when three CTAs with two stages each still fit an SM (the
+// kernel is bound by its summation more than by its staging, so occupancy
+// comes first), else one
+__host__ __device__ inline int rtb_stages(unsigned sd) { return rtb_smem_bytes(sd, 2) <= 74u * 1024 ? 2 : 1; }
 
 // arguments of phase 1
 struct RtbArgs {
@@ -88,6 +104,10 @@ struct RtbArgs {
   const DevState* state;      // check: R from state->R when R_from_state, else R
   int R_from_state;
   long long R;
+  DevState* state_out;        // status: LCS_ETIMEOUT if a staging wait gives up
+  const unsigned long long* tiles;  // sweep: the tiles with a task, (k << 48) | run index
+  unsigned long long n_tiles;
+  int nstage;
 };
 
 // arguments of phase 2
@@ -235,135 +255,311 @@ __device__ __forceinline__ long long rtb_floor_mean(long long sum, unsigned T, i
   }
 }
 
-// Phase 1.  Tiles: (k, run of G blocks) for the sweep (v_k's blocks), runs of
-// G blocks for the check (u's, every k from one staging).
+// ---------------------------------------------------------------------------
+// staging: bulk copies (TMA) into shared memory, completed on an mbarrier
+
+__device__ __forceinline__ uint32_t rtb_smem_addr(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void rtb_bulk_load(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+               "l"(src), "r"(bytes), "r"(bar)
+               : "memory");
+}
+
+// bounded wait on an mbarrier phase; false when the budget (in clock cycles) runs out
+__device__ __forceinline__ bool rtb_wait(uint32_t bar, uint32_t parity, long long budget) {
+  const long long t0 = clock64();
+  for (;;) {
+    uint32_t done;
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\tselp.u32 %0, 1, 0, p;\n\t}"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    if (done) return true;
+    if (clock64() - t0 > budget) return false;
+  }
+}
+
+constexpr long long kRtbWaitBudget = 1ll << 31;  // clock cycles (about a second)
+
+// One tile: nb blocks of sigma^d values from element e0 of vector v.  A bulk
+// copy wants 16-byte aligned ends, so it covers [e0 rounded down to an even
+// element, end rounded up to one) and the tile starts `shift` elements in; it
+// is used only when that range lies inside the vector (else plain loads).
+struct RtbTile {
+  const long long* v;
+  unsigned long long e0;
+  unsigned vals;      // nb sigma^d
+  unsigned shift;     // 0 or 1
+  unsigned bytes;     // of the copy
+  bool bulk;
+};
+
+__device__ __forceinline__ RtbTile rtb_tile(const long long* v, unsigned long long n_stored, unsigned long long e0,
+                                            unsigned vals) {
+  RtbTile t;
+  t.v = v;
+  t.e0 = e0;
+  t.vals = vals;
+  t.shift = (unsigned)(e0 & 1);
+  const unsigned long long a0 = e0 - t.shift, a1 = (e0 + vals + 1) & ~1ull;
+  t.bytes = (unsigned)((a1 - a0) * 8);
+  t.bulk = ((reinterpret_cast<uintptr_t>(v) & 15) == 0) && a1 <= n_stored;
+  return t;
+}
+
+// The inner digits of a part's sum: the U lowest-weight strings of N left
+// after the part's own digits are walked in registers, so one lookup in the
+// offset table serves sigma^U loads.
+template <int SIG>
+struct RtbInner {
+  static constexpr int U = SIG == 2 ? 3 : SIG == 3 ? 2 : 1;
+  static constexpr int IN = SIG == 2 ? 8 : SIG == 3 ? 9 : SIG;
+};
+
+// Part `part` (of sigma^a) of one output: the terms whose a lowest N digits
+// are part's digits.  bb points at the output's block position (its S digits
+// included).  offs/start: the term-offset table.
+template <int SIG>
+__device__ __forceinline__ long long rtb_part_sum(const long long* bb, unsigned N, int d, int k, int a, unsigned part,
+                                                  const unsigned short* __restrict__ offs,
+                                                  const unsigned* __restrict__ start) {
+  constexpr int U = RtbInner<SIG>::U, IN = RtbInner<SIG>::IN;
+  unsigned low = 0, rest = N, partset = 0, w = 1, w0 = 0, w1 = 0, w2 = 0;
+  int i = 0;
+  for (int j = d - 1; j >= 0; --j, w *= SIG) {
+    if (!((N >> j) & 1u)) continue;
+    if (i < a) {
+      low += (part % SIG) * w;
+      part /= SIG;
+      rest &= ~(1u << j);
+      partset |= 1u << j;
+    } else if (i < a + U) {
+      if (i == a) w0 = w;
+      else if (i == a + 1) w1 = w;
+      else w2 = w;
+      rest &= ~(1u << j);
+    }
+    ++i;
+  }
+  const long long* b = bb + low;
+  long long acc[IN];
+#pragma unroll
+  for (int c = 0; c < IN; ++c) acc[c] = 0;
+  if (k - a >= U) {
+    // inner offsets: the U digits, least significant first
+    unsigned in[IN];
+#pragma unroll
+    for (int c = 0; c < IN; ++c) {
+      unsigned q = c, o = 0;
+      o += (q % SIG) * w0;
+      q /= SIG;
+      if (U > 1) {
+        o += (q % SIG) * w1;
+        q /= SIG;
+      }
+      if (U > 2) o += (q % SIG) * w2;
+      in[c] = o;
+    }
+    unsigned J = 1;
+    for (int q = a + U; q < k; ++q) J *= SIG;
+    const unsigned short* on = offs + start[rest];
+    for (unsigned jj = 0; jj < J; ++jj) {
+      const long long* bj = b + __ldg(on + jj);
+#pragma unroll
+      for (int c = 0; c < IN; ++c) acc[c] += bj[in[c]];
+    }
+  } else {
+    // fewer than U digits left: one lookup per term, over every N string but the part's
+    unsigned J = 1;
+    for (int q = a; q < k; ++q) J *= SIG;
+    const unsigned short* on = offs + start[N & ~partset];
+    for (unsigned jj = 0; jj < J; ++jj) acc[0] += b[__ldg(on + jj)];
+  }
+  long long sum = 0;
+#pragma unroll
+  for (int c = 0; c < IN; ++c) sum += acc[c];
+  return sum;
+}
+
+// Phase 1.  Tiles: the listed (k, run of G blocks) for the sweep (v_k's
+// blocks; runs without a task are not listed), every run of G blocks for the
+// check (u's, all k from one staging).  Two stages when they fit: the copy of
+// the tile after next is issued as soon as a tile is done.
 template <int SIG, bool CHECK>
-__global__ void __launch_bounds__(kBlock) rtb_means_kernel(RtbArgs a) {
+__global__ void __launch_bounds__(kBlock, 4) rtb_means_kernel(RtbArgs a) {
   extern __shared__ __align__(16) unsigned char rtb_smem[];
   const unsigned sd = a.sd;
   const int d = a.d;
   const unsigned G = rtb_blocks_per_tile(sd);
-  long long* blk = reinterpret_cast<long long*>(rtb_smem);
-  unsigned* t_N = reinterpret_cast<unsigned*>(rtb_smem + (size_t)G * sd * 8);
+  const unsigned stage_bytes = rtb_stage_bytes(sd);
+  const int nstage = a.nstage;
+  unsigned char* stage0 = rtb_smem;
+  unsigned* t_N = reinterpret_cast<unsigned*>(rtb_smem + (size_t)nstage * stage_bytes);
   unsigned* t_boff = t_N + kRtbTasks;
   unsigned* t_e = t_boff + kRtbTasks;
   unsigned long long* t_base = reinterpret_cast<unsigned long long*>(t_e + kRtbTasks);
   unsigned* cnt = reinterpret_cast<unsigned*>(t_base + kRtbTasks);
   long long* acc = reinterpret_cast<long long*>(cnt + kRtbMaxG + 2);
+  unsigned long long* bars = reinterpret_cast<unsigned long long*>(acc + kRtbAcc);
+  int* flag = reinterpret_cast<int*>(bars + 2);
 
   const unsigned long long n_tail = a.n_tail;
   const unsigned long long topw = n_tail / sd;  // sigma^((h-2) d): weight of Y's top group
   const unsigned long long n_ty = (n_tail + G - 1) / G;
+  const unsigned long long n_stored = n_tail * sd;
   const unsigned full = (1u << d) - 1;
   const long long R = CHECK ? (a.R_from_state ? a.state->R : a.R) : 0;
-  const unsigned long long n_tiles = (CHECK ? 1ull : (unsigned long long)d) * n_ty;
-  const int tid = threadIdx.x;
+  const unsigned long long n_tiles = CHECK ? n_ty : a.n_tiles;
+  const int tid = threadIdx.x, lane = tid & 31;
 
-  for (unsigned long long tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-    const int k_first = CHECK ? 1 : (int)(tile / n_ty) + 1;
+  // tile i of this CTA: its first k and run of blocks
+  auto tile_of = [&](unsigned long long it, int& k, unsigned long long& Y0, unsigned& nb) {
+    unsigned long long ty;
+    if (CHECK) {
+      k = 1;
+      ty = it;
+    } else {
+      const unsigned long long e = a.tiles[it];
+      k = (int)(e >> 48);
+      ty = e & ((1ull << 48) - 1);
+    }
+    Y0 = ty * G;
+    nb = (unsigned)min((unsigned long long)G, n_tail - Y0);
+  };
+  auto tile_desc = [&](unsigned long long it) {
+    int k;
+    unsigned long long Y0;
+    unsigned nb;
+    tile_of(it, k, Y0, nb);
+    return rtb_tile(a.v[k - 1], n_stored, Y0 * sd, nb * sd);
+  };
+  auto issue = [&](unsigned long long it, int st) {  // one thread
+    const RtbTile t = tile_desc(it);
+    if (!t.bulk) return;
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    rtb_bulk_load(rtb_smem_addr(stage0 + (size_t)st * stage_bytes), t.v + (t.e0 - t.shift), t.bytes,
+                  rtb_smem_addr(bars + st));
+  };
+
+  if (tid == 0) {
+    for (int st = 0; st < nstage; ++st)
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(rtb_smem_addr(bars + st)), "r"(1u) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int st = 0; st < nstage; ++st) {
+      const unsigned long long it = blockIdx.x + (unsigned long long)st * gridDim.x;
+      if (it < n_tiles) issue(it, st);
+    }
+  }
+  __syncthreads();
+  unsigned phase = 0;  // bit st: the parity the next bulk copy into stage st completes
+  unsigned long long i = 0;
+  for (unsigned long long it = blockIdx.x; it < n_tiles; it += gridDim.x, ++i) {
+    const int st = nstage == 2 ? (int)(i & 1) : 0;
+    int k_first;
+    unsigned long long Y0;
+    unsigned nb;
+    tile_of(it, k_first, Y0, nb);
+    const RtbTile tile = rtb_tile(a.v[k_first - 1], n_stored, Y0 * sd, nb * sd);
+    long long* blk = reinterpret_cast<long long*>(stage0 + (size_t)st * stage_bytes) + tile.shift;
+    if (tile.bulk) {
+      if (tid == 0) {
+        const bool ok = rtb_wait(rtb_smem_addr(bars + st), (phase >> st) & 1u, kRtbWaitBudget);
+        *flag = ok ? 1 : 0;
+        if (!ok) {
+          atomicExch(reinterpret_cast<unsigned long long*>(&a.state_out->status), (unsigned long long)LCS_ETIMEOUT);
+          // the other stage's copy may still be in flight: wait for it (bounded) before leaving
+          const unsigned long long nxt = it + gridDim.x;
+          if (nstage == 2 && nxt < n_tiles && tile_desc(nxt).bulk)
+            rtb_wait(rtb_smem_addr(bars + (st ^ 1)), (phase >> (st ^ 1)) & 1u, kRtbWaitBudget);
+        }
+      }
+      __syncthreads();
+      if (!*flag) return;  // uniform
+      phase ^= 1u << st;
+    } else {
+      for (unsigned q = tid; q < tile.vals; q += kBlock) blk[q] = __ldcs(tile.v + tile.e0 + q);
+      __syncthreads();
+    }
     const int k_last = CHECK ? d : k_first;
-    const unsigned long long Y0 = (tile % n_ty) * G;
-    const unsigned nb = (unsigned)min((unsigned long long)G, n_tail - Y0);
-    const long long* __restrict__ src = a.v[k_first - 1] + Y0 * sd;
-    bool staged = false;
     for (int k = k_first; k <= k_last; ++k) {
       const int s = d - k;
-      __syncthreads();  // the previous pass is done with cnt and the task list
-      if (tid < (int)nb) cnt[tid + 1] = rtb_count<SIG>(Y0 + tid, topw, d, s);
-      if (tid == 0) cnt[0] = 0;
-      __syncthreads();
-      if (tid == 0)
-        for (unsigned b = 1; b <= nb; ++b) cnt[b] += cnt[b - 1];
-      __syncthreads();
-      const unsigned total = cnt[nb];
-      if (total == 0) continue;  // uniform
-      if (!staged) {
-        // one contiguous read of nb sigma^d values, four loads in flight per thread
-        const unsigned vals = nb * sd;
-        for (unsigned i = tid; i < vals; i += 4 * kBlock) {
-          long long x[4];
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const unsigned ii = i + q * kBlock;
-            x[q] = ii < vals ? __ldcs(src + ii) : 0;
-          }
-#pragma unroll
-          for (int q = 0; q < 4; ++q) {
-            const unsigned ii = i + q * kBlock;
-            if (ii < vals) blk[ii] = x[q];
-          }
-        }
-        staged = true;
+      unsigned total;
+      if (nb == 1) {  // one block: every thread counts its tasks, no barrier
+        total = rtb_count<SIG>(Y0, topw, d, s);
+      } else {
+        if (tid < (int)nb) cnt[tid + 1] = rtb_count<SIG>(Y0 + tid, topw, d, s);
+        if (tid == 0) cnt[0] = 0;
+        __syncthreads();
+        if (tid == 0)
+          for (unsigned b = 1; b <= nb; ++b) cnt[b] += cnt[b - 1];
+        __syncthreads();
+        total = cnt[nb];
       }
       unsigned T = 1, O = 1;  // terms per output (sigma^k), outputs per task (sigma^s)
-      for (int i = 0; i < k; ++i) T *= SIG;
-      for (int i = 0; i < s; ++i) O *= SIG;
+      for (int q = 0; q < k; ++q) T *= SIG;
+      for (int q = 0; q < s; ++q) O *= SIG;
       for (unsigned i0 = 0; i0 < total; i0 += kRtbTasks) {
         const unsigned nbatch = min(kRtbTasks, total - i0);
         if (tid < (int)nbatch) {
-          const unsigned i = i0 + tid;
-          unsigned b = 0;
-          while (cnt[b + 1] <= i) ++b;
+          const unsigned ti = i0 + tid;
+          unsigned b = 0, first = 0;
+          if (nb > 1) {
+            while (cnt[b + 1] <= ti) ++b;
+            first = cnt[b];
+          }
           unsigned N, e;
           unsigned long long tb;
-          rtb_task<SIG>(Y0 + b, topw, d, a.h, s, i - cnt[b], N, e, tb);
+          rtb_task<SIG>(Y0 + b, topw, d, a.h, s, ti - first, N, e, tb);
           t_N[tid] = N;
           t_boff[tid] = b * sd;
           t_e[tid] = e;
           t_base[tid] = tb;
         }
-        __syncthreads();  // also: the staged tile is visible
-        // outputs: nbatch * O, each the sum of T terms split over P threads
+        // outputs: nbatch * O, each the sum of T terms split over P = sigma^a
+        // threads (the part is the a lowest N digits); parts meet in acc
         const unsigned nOut = nbatch * O;
+        int a_lo = 0;
         unsigned P = 1;
-        if (nOut < (unsigned)kBlock) {
-          while (P * 2 * nOut <= (unsigned)kBlock && P * 2 <= T) P *= 2;
+        while (a_lo < k - RtbInner<SIG>::U && nOut * P * SIG <= (unsigned)kBlock) {
+          P *= SIG;
+          ++a_lo;
         }
-        const int lgP = __ffs(P) - 1;
-        const unsigned slots = nOut << lgP;
-        if (P > 32) {
-          if (tid < (int)nOut) acc[tid] = 0;
-          __syncthreads();
-        }
+        const unsigned slots = nOut * P;
+        if (P > 1 && tid < (int)nOut) acc[tid] = 0;
+        __syncthreads();  // the task list (and acc) are ready
         for (unsigned base = 0; base < slots; base += kBlock) {  // uniform trip count
           const unsigned slot = base + tid;
           const bool act = slot < slots;
-          const unsigned o = slot >> lgP, part = slot & (P - 1);
+          const unsigned o = slot / P, part = slot - o * P;
           long long sum = 0;
           unsigned task = 0, offS = 0;
           if (act) {
             task = o / O;
             const unsigned N = t_N[task];
             offS = rtb_s_offset<SIG>(full ^ N, d, o - task * O);
-            const unsigned short* __restrict__ on = a.offs + a.start[N];
-            const long long* bb = blk + t_boff[task] + offS;
-            long long s0 = 0, s1 = 0, s2 = 0, s3 = 0;
-            unsigned m = part;
-            for (; m + 3 * P < T; m += 4 * P) {
-              const unsigned o0 = __ldg(on + m), o1 = __ldg(on + m + P), o2 = __ldg(on + m + 2 * P),
-                             o3 = __ldg(on + m + 3 * P);
-              s0 += bb[o0];
-              s1 += bb[o1];
-              s2 += bb[o2];
-              s3 += bb[o3];
-            }
-            for (; m < T; m += P) s0 += bb[__ldg(on + m)];
-            sum = (s0 + s1) + (s2 + s3);
+            sum = rtb_part_sum<SIG>(blk + t_boff[task] + offS, N, d, k, a_lo, part, a.offs, a.start);
           }
           if (P > 1) {
-            const unsigned width = P < 32 ? P : 32;
-            for (unsigned w = width >> 1; w; w >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, w);
-          }
-          if (P > 32) {
-            if (act && (tid & 31) == 0)
+            // segmented sum over the lanes of one output within this warp
+#pragma unroll
+            for (unsigned w = 1; w < 32; w <<= 1) {
+              const long long up = __shfl_down_sync(0xffffffffu, sum, w);
+              if (lane + w < 32 && part + w < P) sum += up;
+            }
+            if (act && (part == 0 || lane == 0))
               atomicAdd(reinterpret_cast<unsigned long long*>(acc + o), (unsigned long long)sum);
-          } else if (act && part == 0) {
+          } else if (act) {
             long long mean = rtb_floor_mean<SIG>(sum, T, k);
             if (CHECK) mean += (long long)(d - k) * R;
             a.means[(unsigned long long)t_e[task] * n_tail + t_base[task] + offS] = mean;
           }
         }
-        if (P > 32) {
+        if (P > 1) {
           __syncthreads();
           if (tid < (int)nOut) {
             const unsigned task = tid / O;
@@ -373,66 +569,95 @@ __global__ void __launch_bounds__(kBlock) rtb_means_kernel(RtbArgs a) {
             a.means[(unsigned long long)t_e[task] * n_tail + t_base[task] + offS] = mean;
           }
         }
-        __syncthreads();  // the task list is rewritten by the next batch
+        __syncthreads();  // the task list and acc are rewritten by the next batch
       }
+      __syncthreads();  // cnt is rewritten by the next k
+    }
+    // every thread is done with this stage: refill it with the tile after next
+    if (tid == 0) {
+      const unsigned long long nxt = it + (unsigned long long)nstage * gridDim.x;
+      if (nxt < n_tiles) issue(nxt, st);
     }
   }
 }
 
-// Phase 2: v (sweep) or W (check) of every state from the means table
+// Phase 2: v (sweep) or W (check) of every state from the means table.  A
+// unit is one head combination and a span of kRtbSpan consecutive tail
+// tuples (chunk-major: the CTAs in flight share the table's columns); its
+// candidate rows are formed once, then each thread takes kRtbPer states,
+// issuing all their loads before it uses one.
+constexpr int kRtbPer = 8;
+constexpr unsigned kRtbSpan = kRtbPer * kBlock;
+
 template <int SIG, bool INCR, bool CHECK>
 __global__ void __launch_bounds__(kBlock) rtb_state_kernel(RtbStateArgs a) {
   const unsigned long long n_tail = a.n_tail;
   const int d = a.d;
   const unsigned full = (1u << d) - 1;
-  const unsigned long long stride = (unsigned long long)gridDim.x * blockDim.x;
-  const unsigned long long sq = stride / n_tail, sr = stride % n_tail;
-  unsigned long long x = (unsigned long long)blockIdx.x * blockDim.x + threadIdx.x;
-  unsigned long long Hidx = x / n_tail, t = x % n_tail;
+  const unsigned long long chunks = (n_tail + kRtbSpan - 1) / kRtbSpan;
+  const unsigned long long units = chunks * a.sd;
   const long long R = CHECK ? (a.R_from_state ? a.state->R : a.R) : 0;
   long long best_v = a.r_mode ? LLONG_MIN : LLONG_MAX;
   unsigned long long best_x = ULLONG_MAX;
   long long best_w = LLONG_MIN;
-  for (; x < a.n_stored; x += stride) {
+  for (unsigned long long u = blockIdx.x; u < units; u += gridDim.x) {
+    const unsigned long long c = u / a.sd;
+    const unsigned Hidx = (unsigned)(u - c * a.sd);
     unsigned sets[SIG];
 #pragma unroll
     for (int z = 0; z < SIG; ++z) sets[z] = 0;
-    unsigned hh = (unsigned)Hidx;
+    unsigned hh = Hidx;
     for (int j = d - 1; j >= 0; --j) {
-      const unsigned c = hh % SIG;
+      const unsigned cz = hh % SIG;
       hh /= SIG;
 #pragma unroll
       for (int z = 0; z < SIG; ++z)
-        if (c == (unsigned)z) sets[z] |= 1u << j;
+        if (cz == (unsigned)z) sets[z] |= 1u << j;
     }
+    // candidate rows: one per letter on some but not all heads, and row 0
+    // (every string advances) for the first letter on no head
+    unsigned long long rows[SIG];
+    bool use[SIG];
     bool equal = false, absent = false;
-    long long best = LLONG_MIN;
 #pragma unroll
     for (int z = 0; z < SIG; ++z) {
-      if (sets[z] == full) {
-        equal = true;
-      } else if (sets[z] == 0) {
-        absent = true;  // every string advances: the shared entry 0
+      use[z] = sets[z] != full && (sets[z] != 0 || !absent);
+      rows[z] = sets[z] ? (unsigned long long)(((unsigned)z << d) | sets[z]) * n_tail : 0ull;
+      equal |= sets[z] == full;
+      absent |= sets[z] == 0;
+    }
+    const long long bonus = equal ? a.one : 0;
+    const unsigned long long x0 = (unsigned long long)Hidx * n_tail;
+    const unsigned long long t0 = c * kRtbSpan + threadIdx.x;
+    long long best[kRtbPer], other[kRtbPer];
+#pragma unroll
+    for (int q = 0; q < kRtbPer; ++q) {
+      const unsigned long long t = t0 + (unsigned)(q * kBlock);
+      best[q] = LLONG_MIN;
+      other[q] = 0;
+      if (t < n_tail) {
+#pragma unroll
+        for (int z = 0; z < SIG; ++z)
+          if (use[z]) best[q] = max(best[q], __ldg(a.means + rows[z] + t));
+        if (CHECK) other[q] = __ldcs(a.u + x0 + t);
+        else if (INCR) other[q] = __ldcs(a.prev0 + x0 + t);
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < kRtbPer; ++q) {
+      const unsigned long long t = t0 + (unsigned)(q * kBlock);
+      if (t >= n_tail) continue;
+      const long long v = best[q] + bonus;
+      const unsigned long long x = x0 + t;
+      if constexpr (CHECK) {
+        best_w = max(best_w, other[q] + (long long)d * R - v);
       } else {
-        best = max(best, __ldg(a.means + ((unsigned long long)(((unsigned)z << d) | sets[z])) * n_tail + t));
+        __stcs(a.out + x, v);
+        if constexpr (INCR) {
+          const long long inc = v - other[q];
+          if (red_better(inc, x, best_v, best_x, a.r_mode)) best_v = inc, best_x = x;
+        }
       }
-    }
-    if (absent) best = max(best, __ldg(a.means + t));
-    const long long v = best + (equal ? a.one : 0);
-    if constexpr (CHECK) {
-      best_w = max(best_w, __ldcs(a.u + x) + (long long)d * R - v);
-    } else {
-      __stcs(a.out + x, v);
-      if constexpr (INCR) {
-        const long long inc = v - __ldcs(a.prev0 + x);
-        if (red_better(inc, x, best_v, best_x, a.r_mode)) best_v = inc, best_x = x;
-      }
-    }
-    t += sr;
-    Hidx += sq;
-    if (t >= n_tail) {
-      t -= n_tail;
-      ++Hidx;
     }
   }
   if constexpr (CHECK)
@@ -482,8 +707,7 @@ inline int rtb_means_grid(size_t smem, unsigned long long tiles) {
   static int sms = 0;
   static bool attr = false;
   if (!attr) {
-    cudaFuncSetAttribute(rtb_means_kernel<SIG, CHECK>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                         (int)rtb_smem_bytes(kRtbMaxBlock));
+    cudaFuncSetAttribute(rtb_means_kernel<SIG, CHECK>, cudaFuncAttributeMaxDynamicSharedMemorySize, 227 * 1024);
     attr = true;
   }
   if (sms == 0) {
@@ -499,7 +723,7 @@ inline int rtb_means_grid(size_t smem, unsigned long long tiles) {
     cudaGetLastError();
     per_sm = 1;
   }
-  return (int)min((unsigned long long)sms * per_sm, tiles);
+  return (int)min((unsigned long long)sms * per_sm, tiles > 0 ? tiles : 1ull);
 }
 
 template <int SIG>
@@ -513,10 +737,13 @@ void launch_sweep_rtb(const SweepParams& p, int d, int grid, cudaStream_t s) {
   a.sd = (unsigned)(p.n_stored / p.n_tail);
   a.d = d;
   a.h = p.h;
-  const size_t smem = rtb_smem_bytes(a.sd);
-  const unsigned G = rtb_blocks_per_tile(a.sd);
-  const unsigned long long tiles = (unsigned long long)d * ((p.n_tail + G - 1) / G);
-  rtb_means_kernel<SIG, false><<<rtb_means_grid<SIG, false>(smem, tiles), kBlock, smem, s>>>(a);
+  a.state_out = p.state;
+  a.tiles = p.rt_tiles;
+  a.n_tiles = p.rt_n_tiles;
+  a.nstage = rtb_stages(a.sd);
+  const size_t smem = rtb_smem_bytes(a.sd, a.nstage);
+  if (a.n_tiles > 0)
+    rtb_means_kernel<SIG, false><<<rtb_means_grid<SIG, false>(smem, a.n_tiles), kBlock, smem, s>>>(a);
   RtbStateArgs b{};
   b.means = p.rt_means;
   b.out = p.out;
@@ -548,7 +775,9 @@ void launch_check_rtb(const CheckParams& q, int d, int grid, cudaStream_t s) {
   a.state = q.state;
   a.R_from_state = q.R_from_state;
   a.R = q.R;
-  const size_t smem = rtb_smem_bytes(a.sd);
+  a.state_out = const_cast<DevState*>(q.state);  // the handle's state: its status is writable
+  a.nstage = rtb_stages(a.sd);
+  const size_t smem = rtb_smem_bytes(a.sd, a.nstage);
   const unsigned G = rtb_blocks_per_tile(a.sd);
   const unsigned long long tiles = (q.n_tail + G - 1) / G;
   rtb_means_kernel<SIG, true><<<rtb_means_grid<SIG, true>(smem, tiles), kBlock, smem, s>>>(a);

@@ -138,6 +138,9 @@ def phase1(s, d, h, check):
             for b in range(nb):
                 cnt.append(cnt[-1] + count(Y0 + b, topw, s, d, ss))
             T, O = s ** k, s ** ss
+            if not check:  # the listed tiles (rt_tile_list) are exactly those with a task
+                most = max(max(bin(m).count("1") for m in top_sets(Y0 + b, topw, s, d)) for b in range(nb))
+                assert (k == d or most >= d - k) == (cnt[nb] > 0)
             for i in range(cnt[nb]):
                 b = 0
                 while cnt[b + 1] <= i:
@@ -203,6 +206,36 @@ def test_tiles_and_shared_memory_fit():
             if sd > K_MAX_BLOCK:
                 continue
             G = blocks_per_tile(sd)
-            smem = G * sd * 8 + 256 * 20 + (K_MAX_G + 2) * 4 + 64
-            assert smem <= 227 * 1024
+
+            def smem(nstage):
+                return nstage * stage_bytes(sd) + 256 * 20 + (K_MAX_G + 2) * 4 + 128 * 8 + 2 * 8 + 16
+
+            nstage = 2 if smem(2) <= 200 * 1024 else 1
+            assert smem(nstage) <= 227 * 1024
             assert G <= K_MAX_G and (G == 1 or G * sd <= K_TILE_VALS)
+
+
+def stage_bytes(sd):
+    return (blocks_per_tile(sd) * sd * 8 + 8 + 15) // 16 * 16
+
+
+@pytest.mark.parametrize("sd", [36, 49, 64, 81, 100, 125, 243, 729, 2048, 2187, 6561, 10000, 15625, 16384])
+def test_bulk_copies_stay_inside_their_stage_and_vector(sd):
+    """The staging copy of a tile of nb blocks at element e0 covers the even-aligned
+    range around it: it must fit its stage buffer (with the tile starting at the
+    shift), be a whole number of 16-byte units, and is used only inside the vector."""
+    G = blocks_per_tile(sd)
+    for n_tail in (G, 3 * G + 1, 7 * G - 1):
+        n = n_tail * sd
+        for ty in range((n_tail + G - 1) // G):
+            nb = min(G, n_tail - ty * G)
+            e0, vals = ty * G * sd, nb * sd
+            shift = e0 & 1
+            a0, a1 = e0 - shift, (e0 + vals + 1) & ~1
+            nbytes = (a1 - a0) * 8
+            assert nbytes % 16 == 0 and a0 % 2 == 0
+            assert nbytes <= stage_bytes(sd)
+            assert (shift + vals) * 8 <= stage_bytes(sd)
+            bulk = a1 <= n
+            if not bulk:  # only a last, misaligned tile falls back to plain loads
+                assert ty == (n_tail + G - 1) // G - 1 and (e0 + vals) % 2 == 1
