@@ -119,8 +119,39 @@ def offsets_table(s, d):
     return start, offs
 
 
-def phase1(s, d, h, check):
-    """{(e, t): (k, sorted term addresses)} as phase 1 files them (every tile)."""
+LANES = {2: (5, 32), 3: (3, 27), 4: (2, 16), 5: (2, 25)}  # (lane digits A, live lanes L)
+
+
+def lane_outputs(s, d, N, start, offs):
+    """The lane-digit form (the kernel uses it for sigma = 2; restated for sigma <= 5):
+    [(offset of the output's S digits, sorted term offsets)],
+    as the writer lanes of a warp file them after the shuffle sum over the advanced lane digits."""
+    A, L = LANES[s]
+    full, hi = (1 << d) - 1, (1 << (d - A)) - 1
+    S = full ^ N
+    nlo = sum(1 << p for p in range(A) if (N >> (d - 1 - p)) & 1)
+    J, Q = s ** bin(N & hi).count("1"), s ** bin(S & hi).count("1")
+
+    def digits(lane):
+        return [(lane // s ** p) % s for p in range(A)]
+
+    out = []
+    for q in range(Q):
+        offSh = offs[start[S & hi] + q]
+        for lane in range(L):
+            dl = digits(lane)
+            if any(dl[p] for p in range(A) if (nlo >> p) & 1):
+                continue  # not a writer
+            # the lanes summed into this writer: same digits outside nlo
+            group = [l2 for l2 in range(L) if all(digits(l2)[p] == dl[p] for p in range(A) if not (nlo >> p) & 1)]
+            terms = sorted(offSh + offs[start[N & hi] + n] + l2 for n in range(J) for l2 in group)
+            out.append((offSh + lane, terms))
+    return out
+
+
+def phase1(s, d, h, check, lanes=False):
+    """{(e, t): (k, sorted term addresses)} as phase 1 files them (every tile);
+    lanes: the lane-digit form of the sums instead of the per-output one."""
     sd, n_tail = s ** d, s ** (d * (h - 1))
     topw = n_tail // sd
     G = blocks_per_tile(sd)
@@ -147,6 +178,12 @@ def phase1(s, d, h, check):
                     b += 1
                 N, e, tb = task(Y0 + b, topw, s, d, h, ss, i - cnt[b])
                 assert bin(N).count("1") == k
+                if lanes:
+                    for offS, terms in lane_outputs(s, d, N, start, offs):
+                        key = (e, tb + offS)
+                        assert key not in filed, f"entry {key} filed twice"
+                        filed[key] = (k, [(Y0 + b) * sd + x for x in terms])
+                    continue
                 for o in range(O):
                     offS = s_offset(full ^ N, d, o, s)
                     addrs = sorted((Y0 + b) * sd + offS + offs[start[N] + m] for m in range(T))
@@ -157,13 +194,17 @@ def phase1(s, d, h, check):
 
 
 # (7, 2, 2) and (6, 2, 2): several blocks to a tile with a partial last tile
-SHAPES = [(2, 6, 2), (3, 4, 2), (4, 3, 2), (7, 2, 2), (6, 2, 2), (2, 3, 3), (3, 3, 3), (2, 4, 3), (2, 2, 4)]
+SHAPES = [(2, 6, 2), (3, 4, 2), (4, 3, 2), (7, 2, 2), (6, 2, 2), (2, 3, 3), (3, 3, 3), (2, 4, 3), (2, 2, 4),
+          (5, 2, 2)]
 
 
+@pytest.mark.parametrize("form", ["outputs", "lanes"])
 @pytest.mark.parametrize("check", [False, True])
 @pytest.mark.parametrize("s,d,h", SHAPES)
-def test_every_state_reads_the_defined_sums(s, d, h, check):
-    filed = phase1(s, d, h, check)
+def test_every_state_reads_the_defined_sums(s, d, h, check, form):
+    if form == "lanes" and (s not in LANES or d < LANES[s][0]):
+        pytest.skip("the lane-digit form serves sigma <= 5 with d >= its lane digits")
+    filed = phase1(s, d, h, check, lanes=form == "lanes")
     n_tail = s ** (d * (h - 1))
     full = (1 << d) - 1
     used = set()
