@@ -755,6 +755,21 @@ __global__ void __launch_bounds__(kBlock) rtb_state_kernel(RtbStateArgs a) {
       absent |= sets[z] == 0;
     }
     const long long bonus = equal ? a.one : 0;
+    // the rows used, packed: at most min(sigma, d + 1) of them, and d + 1 <= 5
+    // for sigma >= 7 (sigma^d <= 16384)
+    constexpr int CM = SIG <= 6 ? SIG : 5;
+    unsigned long long crow[CM];
+    int ncr = 0;
+#pragma unroll
+    for (int j = 0; j < CM; ++j) crow[j] = 0;
+#pragma unroll
+    for (int z = 0; z < SIG; ++z) {
+      if (!use[z]) continue;
+#pragma unroll
+      for (int j = 0; j < CM; ++j)
+        if (j == ncr) crow[j] = rows[z];
+      ++ncr;
+    }
     const unsigned long long x0 = (unsigned long long)Hidx * n_tail;
     const unsigned long long t0 = c * kRtbSpan + threadIdx.x;
     long long best[kRtbPer], other[kRtbPer];
@@ -765,8 +780,8 @@ __global__ void __launch_bounds__(kBlock) rtb_state_kernel(RtbStateArgs a) {
       other[q] = 0;
       if (t < n_tail) {
 #pragma unroll
-        for (int z = 0; z < SIG; ++z)
-          if (use[z]) best[q] = max(best[q], __ldg(a.means + rows[z] + t));
+        for (int j = 0; j < CM; ++j)
+          if (j < ncr) best[q] = max(best[q], __ldg(a.means + crow[j] + t));
         if (CHECK) other[q] = __ldcs(a.u + x0 + t);
         else if (INCR) other[q] = __ldcs(a.prev0 + x0 + t);
       }
