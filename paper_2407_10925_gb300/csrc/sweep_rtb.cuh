@@ -51,7 +51,7 @@
 namespace lcs {
 
 constexpr unsigned kRtbMaxBlock = 16384;  // sigma^d values of one block at most (128 KiB of shared memory)
-constexpr unsigned kRtbTileVals = 2048;   // smaller blocks are staged several to a tile
+constexpr unsigned kRtbTileVals = 8192;   // blocks below 2048 values are staged several to a tile of up to this many
 constexpr unsigned kRtbMaxG = 64;         // blocks of one tile at most
 constexpr unsigned kRtbTasks = kBlock;    // tasks listed at once: one per thread
 
@@ -67,7 +67,7 @@ inline bool rtb_applies(int sigma, int d, int h) {
 }
 
 __host__ __device__ inline unsigned rtb_blocks_per_tile(unsigned sd) {
-  const unsigned g = sd >= kRtbTileVals ? 1u : kRtbTileVals / sd;
+  const unsigned g = sd >= 2048 ? 1u : kRtbTileVals / sd;
   return g < kRtbMaxG ? g : kRtbMaxG;
 }
 

@@ -20,11 +20,11 @@ import pytest
 
 from test_general_addressing import decode, defined_terms
 
-K_TILE_VALS, K_MAX_G, K_MAX_BLOCK = 2048, 64, 16384
+K_TILE_VALS, K_MAX_G, K_MAX_BLOCK = 8192, 64, 16384
 
 
 def blocks_per_tile(sd):
-    g = 1 if sd >= K_TILE_VALS else K_TILE_VALS // sd
+    g = 1 if sd >= 2048 else K_TILE_VALS // sd
     return min(g, K_MAX_G)
 
 
@@ -254,6 +254,7 @@ def test_tiles_and_shared_memory_fit():
             nstage = 2 if smem(2) <= 200 * 1024 else 1
             assert smem(nstage) <= 227 * 1024
             assert G <= K_MAX_G and (G == 1 or G * sd <= K_TILE_VALS)
+            assert G == 1 or sd < 2048
 
 
 def stage_bytes(sd):
