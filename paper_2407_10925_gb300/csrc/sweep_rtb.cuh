@@ -591,7 +591,9 @@ __global__ void __launch_bounds__(kBlock, 4) rtb_means_kernel(RtbArgs a) {
         *flag = ok ? 1 : 0;
         if (!ok) {
           atomicExch(reinterpret_cast<unsigned long long*>(&a.state_out->status), (unsigned long long)LCS_ETIMEOUT);
-          // the other stage's copy may still be in flight: wait for it (bounded) before leaving
+          // copies may still be in flight into this stage and the other one:
+          // wait for each again (bounded) before the CTA leaves
+          rtb_wait(rtb_smem_addr(bars + st), (phase >> st) & 1u, kRtbWaitBudget);
           const unsigned long long nxt = it + gridDim.x;
           if (nstage == 2 && nxt < n_tiles && tile_desc(nxt).bulk)
             rtb_wait(rtb_smem_addr(bars + (st ^ 1)), (phase >> (st ^ 1)) & 1u, kRtbWaitBudget);
