@@ -54,9 +54,9 @@ CONFIGS = {
     "h17n": dict(sigma=2, d=2, h=17, frac_bits=26, storage=1, bound_iters=400),
     # shapes of the general kernels (every shape without a specialised kernel)
     # (sums of sigma^d values need fewer fractional bits than the default 44)
-    "s3d8h2": dict(sigma=3, d=8, h=2, frac_bits=36),  # 3^16 states
-    "s10d2h4": dict(sigma=10, d=2, h=4),  # 10^8 states
-    "s2d12h2": dict(sigma=2, d=12, h=2, frac_bits=36),  # 2^24 states, one warp per state
+    "s3d8h2": dict(sigma=3, d=8, h=2, frac_bits=36, general=True),  # 3^16 states
+    "s10d2h4": dict(sigma=10, d=2, h=4, general=True),  # 10^8 states
+    "s2d12h2": dict(sigma=2, d=12, h=2, frac_bits=36, general=True),  # 2^24 states, one warp per state
 }
 METRIC = "state-updates/s"
 FALLBACK_HBM_GBS = 6800.0
@@ -340,6 +340,17 @@ def run_reference(args, cfg, rank):
         "e2e": {"value": value, "unit": "state-updates/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def general_terms_per_state(sigma, d):
+    """Mean terms of F per state (every candidate's sum over sigma^|N| values),
+    counting each sum once per tail tuple: the block form forms each once."""
+    import math
+
+    # a sum M(z, S) for every letter z and every proper S whose complement is
+    # not empty, sigma^|N| terms each, shared by the sigma^d head combinations
+    tot = sum(math.comb(d, k) * sigma ** k for k in range(1, d)) * sigma + sigma ** d
+    return tot / sigma ** d
 
 
 def workload_name(cfg, args):
@@ -921,6 +932,10 @@ def main():
                 "check": ("each check runs inside the next sweep (the first of the next step), which reads "
                           "4 more bytes per stored state; those bytes count in the sweep's"
                           if st["check_launches"] == 0 else "a kernel of its own per check"),
+                **({"note": "general kernels in block form: two launches per sweep, bound by the sums of "
+                            "Algorithm 1 formed in shared memory (%.1f terms per state), not by DRAM"
+                            % general_terms_per_state(sigma, d)}
+                   if cfg.get("general") else {}),
             },
             "cpu_baseline": cpu,
             "e2e": e2e,
