@@ -121,7 +121,8 @@ typedef struct {
    * check_vector return LCS_EUNSUPPORTED.  The start must be swap-symmetric. */
   int storage;
   /* 0 (default) or 1: the number of the d + 1 iterate vectors placed in
-   * pinned host memory (cudaHostAlloc, mapped) instead of device memory --
+   * pinned, mapped host memory (an anonymous mapping advised for huge pages,
+   * then registered) instead of device memory --
    * the sweeps read and write that vector over the host link, so a shape
    * whose vectors do not all fit in HBM runs out of core.  The host vector
    * does not come from `alloc`.  Results are bit for bit those of an all-HBM
@@ -139,10 +140,16 @@ lcs_status lcs_bound_default_opts(lcs_bound_opts* opts);
  * failure *out is NULL.  Synchronous.
  * Kernels: specialised ones for sigma = 2 (d = 2..5), sigma = 3 (d = 2, 3)
  * and sigma = 4, 5 (d = 2); every other shape with sigma <= 10 runs the
- * general kernels (f_mode 0 only, full storage whatever opts.symmetry says,
- * one CTA per tail tuple).  Larger sigma, or f_mode 1 without a specialised
- * kernel: LCS_EUNSUPPORTED.  Sums of sigma^d values must stay inside int64:
- * large sigma^d needs fewer fractional bits (LCS_EOVERFLOW otherwise). */
+ * general kernels (f_mode 0 only, full storage whatever opts.symmetry says).
+ * For h >= 2 and sigma^d <= 16384 they run in block form (Algorithm 1's sums
+ * formed once per tail tuple from blocks of sigma^d consecutive values, then
+ * one pass over the states); the handle then also allocates a table of
+ * sigma 2^d means per tail tuple (8 sigma 2^d sigma^(d (h-1)) bytes), the
+ * term offsets ((1 + sigma)^d 16-bit values) and a list of the blocks that
+ * hold sums, all through `alloc` when given.  Larger sigma, or f_mode 1
+ * without a specialised kernel: LCS_EUNSUPPORTED.  Sums of sigma^d values
+ * must stay inside int64: large sigma^d needs fewer fractional bits
+ * (LCS_EOVERFLOW otherwise). */
 lcs_status lcs_bound_create(int sigma, int d, int h, const lcs_bound_opts* opts, lcs_bound_t** out);
 
 /* Number of states sigma^(d h) of the handle's shape, and the number the
