@@ -284,3 +284,18 @@ def test_bulk_copies_stay_inside_their_stage_and_vector(sd):
             bulk = a1 <= n
             if not bulk:  # only a last, misaligned tile falls back to plain loads
                 assert ty == (n_tail + G - 1) // G - 1 and (e0 + vals) % 2 == 1
+
+
+@pytest.mark.parametrize("s,d,h", [(2, 6, 2), (3, 4, 2), (7, 2, 2), (2, 3, 3)])
+def test_terms_per_state_the_bench_reports(s, d, h):
+    """bench.py's note on the general configs states the terms of F per state
+    that the first phase sums; it must be the count of the terms it files."""
+    import os
+    import sys
+
+    sys.path.insert(0, os.path.dirname(os.path.dirname(os.path.abspath(__file__))))
+    import bench
+
+    filed = phase1(s, d, h, False)
+    terms = sum(len(addrs) for _, addrs in filed.values())
+    assert terms / s ** (d * h) == pytest.approx(bench.general_terms_per_state(s, d), rel=1e-12)
