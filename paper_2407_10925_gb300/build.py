@@ -27,6 +27,10 @@ SOURCES = [
     "kernels_s2d2.cu",
     "kernels_orbit.cu",
     "kernels_rt.cu",
+    "kernels_rt_s2_4.cu",
+    "kernels_rt_s5_6.cu",
+    "kernels_rt_s7_8.cu",
+    "kernels_rt_s9_10.cu",
     "kernels_d2s.cu",
     "kernels_d3s.cu",
     "batch.cu",

@@ -1,16 +1,27 @@
-// Instantiation of the general sweep and check (any d up to kMaxD, full
-// storage, f_mode 0) for sigma = 2 .. 10.
+// The general sweep and check (any d up to kMaxD, full storage, f_mode 0)
+// for sigma = 2 .. 10: dispatch over the translation units that instantiate
+// them (kernels_rt_s*.cu), and the host-side helpers.
 #include <vector>
 
 #include "sweep_rt.cuh"
 
 namespace lcs {
 
+const KernelSet* kernels_rt_s2_4(int sigma);
+const KernelSet* kernels_rt_s5_6(int sigma);
+const KernelSet* kernels_rt_s7_8(int sigma);
+const KernelSet* kernels_rt_s9_10(int sigma);
+bool rt_offsets_fill_s2_4(int sigma, int d, unsigned short* offs, unsigned* start, cudaStream_t s);
+bool rt_offsets_fill_s5_6(int sigma, int d, unsigned short* offs, unsigned* start, cudaStream_t s);
+bool rt_offsets_fill_s7_8(int sigma, int d, unsigned short* offs, unsigned* start, cudaStream_t s);
+bool rt_offsets_fill_s9_10(int sigma, int d, unsigned short* offs, unsigned* start, cudaStream_t s);
+
 const KernelSet* kernels_rt(int sigma) {
-  static const KernelSet k[] = {make_rt_set<2>(), make_rt_set<3>(), make_rt_set<4>(), make_rt_set<5>(),
-                                make_rt_set<6>(), make_rt_set<7>(), make_rt_set<8>(), make_rt_set<9>(),
-                                make_rt_set<10>()};
-  return sigma >= 2 && sigma <= 10 ? &k[sigma - 2] : nullptr;
+  if (sigma >= 2 && sigma <= 4) return kernels_rt_s2_4(sigma);
+  if (sigma >= 5 && sigma <= 6) return kernels_rt_s5_6(sigma);
+  if (sigma >= 7 && sigma <= 8) return kernels_rt_s7_8(sigma);
+  if (sigma >= 9 && sigma <= 10) return kernels_rt_s9_10(sigma);
+  return nullptr;
 }
 
 // threads' worth of work of one general sweep or check, for sizing its grid:
@@ -33,18 +44,9 @@ size_t rt_offsets_len(int sigma, int d) {
 }
 
 void rt_offsets_fill(int sigma, int d, unsigned short* offs, unsigned* start, cudaStream_t s) {
-  switch (sigma) {
-    case 2: launch_rtb_offsets<2>(d, offs, start, s); break;
-    case 3: launch_rtb_offsets<3>(d, offs, start, s); break;
-    case 4: launch_rtb_offsets<4>(d, offs, start, s); break;
-    case 5: launch_rtb_offsets<5>(d, offs, start, s); break;
-    case 6: launch_rtb_offsets<6>(d, offs, start, s); break;
-    case 7: launch_rtb_offsets<7>(d, offs, start, s); break;
-    case 8: launch_rtb_offsets<8>(d, offs, start, s); break;
-    case 9: launch_rtb_offsets<9>(d, offs, start, s); break;
-    case 10: launch_rtb_offsets<10>(d, offs, start, s); break;
-    default: break;
-  }
+  if (!rt_offsets_fill_s2_4(sigma, d, offs, start, s) && !rt_offsets_fill_s5_6(sigma, d, offs, start, s) &&
+      !rt_offsets_fill_s7_8(sigma, d, offs, start, s))
+    rt_offsets_fill_s9_10(sigma, d, offs, start, s);
 }
 
 // The first phase's tiles that hold a task, as (k << 48) | run index: a run

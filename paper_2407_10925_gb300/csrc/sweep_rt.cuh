@@ -516,6 +516,9 @@ __global__ void __launch_bounds__(kBlock) sweep_rt2_kernel(SweepParams p) {
   if constexpr (INCR) block_reduce_arg(best_v, best_x, p.r_mode, p.partials);
 }
 
+// (a template, so that the translation units that include this header share
+// one definition)
+template <int SIG2 = 2>
 __global__ void __launch_bounds__(kBlock) check_rt2_kernel(CheckParams q) {
   const RtGeo<2> g = rt_geo<2>(q.n_stored, q.h, q.n_tail);
   const long long R = q.R_from_state ? q.state->R : q.R;
@@ -589,7 +592,7 @@ void launch_check_rt(const CheckParams& q, int grid, cudaStream_t s) {
     return;
   }
   if (SIG == 2 && d >= kRtWarpD) {
-    check_rt2_kernel<<<grid, kBlock, 0, s>>>(q);
+    check_rt2_kernel<2><<<grid, kBlock, 0, s>>>(q);
     return;
   }
   if (rt_warp_tails(SIG, d, q.n_tail))
