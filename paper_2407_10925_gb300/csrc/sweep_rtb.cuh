@@ -19,15 +19,20 @@
 // block's values over the digits on N.  Every M needed by some state arises
 // from exactly one task.
 //
-// Phase 1 (rtb_means_kernel): a CTA stages a tile of consecutive blocks of one
-// vector in shared memory with one contiguous read, lists the valid tasks,
-// and sums each M over shared memory, reading the offsets of its terms from a
-// table built once (rtb_offsets_kernel).  It stores the floored mean (plus
+// Phase 1 (rtb_means_kernel): a persistent CTA walks the tiles that hold a
+// task (listed once per handle), stages each -- consecutive blocks of one
+// vector -- in shared memory with one bulk copy (TMA) completed on an
+// mbarrier, lists the tile's tasks, and sums each M over shared memory,
+// reading the offsets of its terms from a table built once
+// (rtb_offsets_kernel): per output, split over the threads on the lowest
+// advanced digits (sigma >= 3), or per task by a warp whose lanes are the
+// block's five lowest digits (sigma = 2).  It stores the floored mean (plus
 // (d - k) R for the check, whose k-th argument is u + (d - k) R) at
 // means[e(z, S) n_tail + t], e(z, S) = the entry index of sweep_rt.cuh.
-// Phase 2 (rtb_state_kernel): one thread per state reads its candidates from
-// rows e(z, S_z) at column t -- consecutive states, consecutive t -- and
-// writes v with the fused increment reduction, or reduces the check's max W.
+// Phase 2 (rtb_state_kernel): for one head combination and a span of tail
+// tuples, the candidate rows e(z, S_z) are formed once; each thread reads
+// them at its columns t -- consecutive states, consecutive t -- and writes v
+// with the fused increment reduction, or reduces the check's max W.
 //
 // Reads: each block of each argument once per sweep (algorithmic), plus the
 // means table (sigma 2^d values per tail tuple, against sigma^d states).
