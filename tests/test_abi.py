@@ -263,3 +263,17 @@ def test_binding_checks_vector_sizes_before_the_call(L):
     for call in cases:
         with pytest.raises(ValueError):
             call()
+
+
+def test_build_compiles_every_cuda_source():
+    """build.py's list of translation units holds every .cu file of csrc/ once
+    (a source left out would leave its kernels unlinked; the general kernels
+    are spread over several units)."""
+    import os
+
+    from paper_2407_10925_gb300 import build
+
+    csrc = os.path.join(os.path.dirname(os.path.abspath(build.__file__)), "csrc")
+    on_disk = sorted(f for f in os.listdir(csrc) if f.endswith(".cu"))
+    assert sorted(build.SOURCES) == on_disk
+    assert len(set(build.SOURCES)) == len(build.SOURCES)
