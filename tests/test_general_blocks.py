@@ -299,3 +299,39 @@ def test_terms_per_state_the_bench_reports(s, d, h):
     filed = phase1(s, d, h, False)
     terms = sum(len(addrs) for _, addrs in filed.values())
     assert terms / s ** (d * h) == pytest.approx(bench.general_terms_per_state(s, d), rel=1e-12)
+
+
+@pytest.mark.parametrize("s", [2, 3, 4, 5])
+def test_lane_shuffle_reduction(s):
+    """rtb_lane_reduce restated lane by lane: for sigma = 2 an xor shuffle per
+    advanced lane digit, else a sum of the sigma lanes that differ in that digit
+    (source lanes taken mod 32, as the shuffle does).  Every writer lane (live,
+    advanced digits 0) must end with the sum over the live lanes that agree
+    with it on the kept digits."""
+    A, L = LANES[s]
+    for nlo in range(1 << A):
+        vals = [(lane * 7919 + 13) % 1009 if lane < L else 0 for lane in range(32)]
+        acc = list(vals)
+        w = 1
+        for p in range(A):
+            if (nlo >> p) & 1:
+                if s == 2:
+                    acc = [acc[lane] + acc[lane ^ w] for lane in range(32)]
+                else:
+                    new = []
+                    for lane in range(32):
+                        b0 = lane - ((lane // w) % s) * w
+                        new.append(sum(acc[(b0 + c * w) & 31] for c in range(s)))
+                    acc = new
+            w *= s
+
+        def digits(lane):
+            return [(lane // s ** p) % s for p in range(A)]
+
+        for lane in range(L):
+            dl = digits(lane)
+            if any(dl[p] for p in range(A) if (nlo >> p) & 1):
+                continue
+            want = sum(vals[l2] for l2 in range(L)
+                       if all(digits(l2)[p] == dl[p] for p in range(A) if not (nlo >> p) & 1))
+            assert acc[lane] == want, (s, nlo, lane)
